@@ -1,0 +1,99 @@
+"""Geometric multigrid V-cycle preconditioner (Sec. 3.2-3.3).
+
+On every level l >= 1 the smoother is damped Richardson preconditioned by the
+field-split additive Schwarz method; level 0 is solved directly (Sec. 3.2,
+"at the coarse level (l=0) a direct solver is employed").  Level operators
+are rediscretised on each level; transfers are P2 and R2 of Sec. 3.3.
+
+Mixed mode (extension, not in the paper): level operators, transfers,
+Schwarz factors and V-cycle vectors are rounded to float32 and the cycle's
+arithmetic runs in float32; the coarse direct solve stays float64.
+
+The transposed cycle (adjoint extension) applies the transposed operators in
+reverse order: transposed post-smoothing first, restriction by P^T,
+transposed coarse solve, prolongation by R^T, transposed pre-smoothing.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as la
+
+from .assemble import assemble
+from .fem import Reference
+from .fsasm import FSASM
+from .mesh import build_levels
+from .transfer import prolongation, restriction
+
+
+class Hierarchy:
+    def __init__(self, prob, *, mixed: bool = False, omega: float = 1.0, nu_pre: int = 1,
+                 nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
+                 weighted: bool = True):
+        self.prob = prob
+        self.mixed = mixed
+        self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
+        self.wdtype = np.float32 if mixed else np.float64
+        self.levels = build_levels(prob)
+        ref = Reference(prob.dim)
+        self.A = [assemble(prob, lev, ref) for lev in self.levels]
+        nl = len(self.levels)
+        self.P = [None] + [prolongation(self.levels[l], self.levels[l - 1]) for l in range(1, nl)]
+        self.R = [None] + [restriction(self.P[l], self.levels[l], self.levels[l - 1],
+                                       classical=classical_restriction) for l in range(1, nl)]
+        b = prob.patch if patch is None else patch
+        self.smoothers = [None] + [FSASM(self.A[l], self.levels[l], b, dtype=self.wdtype,
+                                         weighted=weighted) for l in range(1, nl)]
+        self.coarse_lu = la.lu_factor(self.A[0].toarray())
+        wd = self.wdtype
+        self.Aw = [A.astype(wd) for A in self.A]
+        self.Pw = [None] + [P.astype(wd) for P in self.P[1:]]
+        self.Rw = [None] + [R.astype(wd) for R in self.R[1:]]
+        self.AwT = [A.T.tocsr() for A in self.Aw]
+
+    @property
+    def fine(self):
+        return self.A[-1]
+
+    def _smooth(self, l, x, b, transpose=False):
+        A = self.AwT[l] if transpose else self.Aw[l]
+        S = self.smoothers[l]
+        r = b - A @ x
+        y = S.apply_transpose(r) if transpose else S.apply(r)
+        return (x + self.wdtype(self.omega) * y).astype(self.wdtype)
+
+    def vcycle_level(self, l: int, b: np.ndarray) -> np.ndarray:
+        wd = self.wdtype
+        b = b.astype(wd)
+        if l == 0:
+            return la.lu_solve(self.coarse_lu, b.astype(np.float64)).astype(wd)
+        x = np.zeros_like(b)
+        for _ in range(self.nu_pre):
+            x = self._smooth(l, x, b)
+        r = (b - self.Aw[l] @ x).astype(wd)
+        xc = self.vcycle_level(l - 1, (self.Rw[l] @ r).astype(wd))
+        x = (x + self.Pw[l] @ xc).astype(wd)
+        for _ in range(self.nu_post):
+            x = self._smooth(l, x, b)
+        return x
+
+    def vcycle_transpose_level(self, l: int, b: np.ndarray) -> np.ndarray:
+        wd = self.wdtype
+        b = b.astype(wd)
+        if l == 0:
+            return la.lu_solve(self.coarse_lu, b.astype(np.float64), trans=1).astype(wd)
+        x = np.zeros_like(b)
+        for _ in range(self.nu_post):
+            x = self._smooth(l, x, b, transpose=True)
+        r = (b - self.AwT[l] @ x).astype(wd)
+        xc = self.vcycle_transpose_level(l - 1, (self.Pw[l].T @ r).astype(wd))
+        x = (x + self.Rw[l].T @ xc).astype(wd)
+        for _ in range(self.nu_pre):
+            x = self._smooth(l, x, b, transpose=True)
+        return x
+
+    def vcycle(self, b: np.ndarray) -> np.ndarray:
+        """One V-cycle from a zero guess on the fine level: M^{-1} b (float64 out)."""
+        return self.vcycle_level(len(self.levels) - 1, b).astype(np.float64)
+
+    def vcycle_transpose(self, b: np.ndarray) -> np.ndarray:
+        return self.vcycle_transpose_level(len(self.levels) - 1, b).astype(np.float64)
