@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the FSI solve: fine DOF/s to reach a 1e-8 relative residual.
+
+Workload: the 2D channel with an aneurysm-like wall pocket, 256 x 256 fine
+elements, 7 GMG levels, 1.12 M unknowns (seeded synthetic stand-in for the
+paper's 2D aneurysm meshes).  One step = one complete FGMRES(30) solve from
+x0 = 0 to a float64 true relative residual <= 1e-8 (V-cycle with FS-ASM
+smoothing, Arnoldi, refinement): every step of the solve path.  Set-up
+(hierarchy, assembly, block factorisation) is timed separately.
+
+  value      mixed precision (float32 cycle, float64 Krylov), device-resident
+             right-hand side, CUDA events on the solver's stream;
+  fp64       the all-float64 path on the same system (mixed/fp64 speed-up);
+  e2e        mixed precision through the public call with host buffers
+             (pinned H2D of b, solve, D2H of x inside the timed region);
+  roofline   the fine-level FS-ASM smoother apply, the dominant kernel:
+             algorithmic bytes / its mean launch time from CUDA events,
+             against the measured HBM copy bandwidth;
+  cpu_baseline  the FP64 oracle on this host, bounded sample (see "sample").
+
+--impl reference runs the oracle itself as the reference arm.  With
+torchrun, every rank solves its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fine DOF/s to 1e-8 rel residual (mixed vs FP64 GPU); smoother % HBM peak"
+UNIT = "DOF/s"
+RTOL = 1e-8
+# FGMRES iterations the oracle's algorithm needs on each seeded workload to
+# reach RTOL (oracle.fgmres.solve on the same right-hand side); used to
+# project the oracle's per-iteration time to the metric.
+ORACLE_ITERATIONS = {1: 40}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--sample-iters", type=int, default=3, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_rhs(p):
+    from oracle import mesh
+    from paper_1909_13201_gb300 import inputs as I
+    lev = mesh.build_levels(p)[-1]
+    return I.gather_natural(I.natural_vector(p, 1), lev.dof_field, lev.dof_comp, lev.dof_node)
+
+
+def oracle_sample(cfg: int, iters: int, steps: int = 1, warmup: int = 0):
+    """Time the FP64 oracle: set-up untimed, then `steps` samples of `iters`
+    FGMRES iterations each.  Returns per-iteration seconds of every sample."""
+    from oracle import fgmres, gmg
+    from paper_1909_13201_gb300 import inputs as I
+    p = I.make_config(cfg)
+    t0 = time.time()
+    H = gmg.Hierarchy(p)
+    setup_s = time.time() - t0
+    b = oracle_rhs(p)
+    per_it = []
+    for k in range(warmup + steps):
+        t = time.time()
+        _, st = fgmres.solve(H, b, rtol=RTOL, maxit=iters)
+        dt = (time.time() - t) / max(st["iterations"], 1)
+        if k >= warmup:
+            per_it.append(dt)
+    return {"n": int(H.fine.shape[0]), "setup_s": setup_s, "per_iteration_s": per_it}
+
+
+def cpu_baseline(cfg: int):
+    """Run the oracle sample in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--config", str(cfg)],
+                         capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "oracle run failed: " + out.stderr.strip().splitlines()[-1][:200]}
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    t_it = statistics.median(res["per_iteration_s"])
+    n_it = ORACLE_ITERATIONS.get(cfg)
+    value = res["n"] / (t_it * n_it)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (numpy/scipy, 1 thread) on the same workload: hierarchy set-up "
+                       f"{res['setup_s']:.0f} s untimed, {len(res['per_iteration_s'])} FGMRES iteration(s) "
+                       f"timed ({t_it:.2f} s each), projected to the {n_it} iterations the oracle needs "
+                       f"to reach {RTOL:g}")}
+
+
+# ------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the fine smoother apply from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "block_apply_c1_mixed.md")
+    src = os.path.join(ROOT, "paper_1909_13201_gb300", "csrc", "kernels_block.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().split()[0]
+    if vals.get("kernels_block.cu sha256[:16]") != sha:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1909_13201_gb300 import inputs as I
+    from paper_1909_13201_gb300.binding import FSI_FP64, FSI_MIXED, FSISolver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = I.make_config(args.config)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    s = FSISolver(p, stream=stream)
+    torch.cuda.synchronize()
+    setup_hier_s = time.time() - t0
+    n = s.sizes(p.n_levels - 1)["n"]
+    f, c, nd = s.dof_map(p.n_levels - 1)
+    b_host = I.gather_natural(I.natural_vector(p, 1), f.astype(np.int64), c.astype(np.int64), nd.astype(np.int64))
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.empty_like(b)
+
+    def timed(k, fn):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / k)
+
+    stats = {}
+
+    def solve_dev():
+        _, st = s.solve(b, x, rtol=RTOL)
+        stats.update(st)
+
+    # ---- mixed precision (headline)
+    t0 = time.time()
+    s.setup_smoothers(precision=FSI_MIXED)
+    torch.cuda.synchronize()
+    setup_mixed_s = time.time() - t0
+    for _ in range(args.warmup):
+        solve_dev()
+    props = torch.cuda.get_device_properties(local)
+    smi_id = str(local)
+    if all(hasattr(props, a) for a in ("pci_domain_id", "pci_bus_id", "pci_device_id")):
+        smi_id = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    clocks = Clocks(smi_id)
+    clocks.start()
+    ms = timed(args.steps, solve_dev)
+    clk = clocks.stop()
+    st_mixed = dict(stats)
+    # roofline of the fine smoother and launch count, from profiled solves
+    s.profile(1)
+    for _ in range(2):
+        solve_dev()
+    prof = s.profile(0)
+    launches_per_step = prof["kernel_launches"] / 2.0
+    sm_ms = prof["smoother_ms"] / max(prof["smoother_launches"], 1)
+    achieved = prof["smoother_bytes"] / (sm_ms * 1e-3) / 1e9
+    spmv_ms = prof["spmv_ms"] / max(prof["spmv_launches"], 1)
+    spmv_gbs = prof["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    # ---- end to end through the public call with host buffers (mixed)
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty_like(b_pin).pin_memory()
+
+    def solve_e2e():
+        b.copy_(b_pin, non_blocking=True)
+        s.solve(b, x, rtol=RTOL)
+        x_pin.copy_(x, non_blocking=True)
+
+    solve_e2e()
+    ms_e2e = timed(max(2, args.steps // 2), solve_e2e)
+    # ---- all-float64 path on the same system
+    t0 = time.time()
+    s.setup_smoothers(precision=FSI_FP64)
+    torch.cuda.synchronize()
+    setup_fp64_s = time.time() - t0
+    solve_dev()
+    ms64 = timed(max(2, args.steps // 3), solve_dev)
+    st64 = dict(stats)
+
+    value = world * n / (ms * 1e-3)
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args.config) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 cycle / f64 Krylov", "data": "synthetic (seeded, no dataset)",
+        "config": {"workload": p.name, "fine_elements": f"{p.n_fine}x{p.n_fine}", "levels": p.n_levels,
+                   "unknowns": n, "vanka_group": p.patch, "restart": 30, "rtol": RTOL,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set (~2.6 GB of block inverses and operators) larger than L2; no flush"},
+        "iterations": st_mixed.get("iterations"), "rho": st_mixed.get("rho"),
+        "rel_residual": st_mixed.get("rel_residual"),
+        "fp64": {"value": world * n / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": st64.get("iterations"),
+                 "speedup_mixed_over_fp64": ms64 / ms},
+        "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed": setup_mixed_s, "smoothers_fp64": setup_fp64_s},
+        "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
+        "roofline": {"bound": "hbm", "kernel": "block_apply_kernel<float> (fine level)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": ncu_traffic(),
+                     "algorithmic_bytes_per_launch": prof["smoother_bytes"], "mean_launch_ms": sm_ms,
+                     "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms}},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "gpu_launches_per_step": launches_per_step,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1909_13201_gb300 import inputs as I
+    p = I.make_config(args.config)
+    res = oracle_sample(args.config, iters=1, steps=args.steps, warmup=args.warmup)
+    n_it = ORACLE_ITERATIONS[args.config]
+    t_it = statistics.mean(res["per_iteration_s"])
+    value = res["n"] / (t_it * n_it)
+    sample = (f"FP64 oracle (numpy/scipy, 1 thread); each step = 1 FGMRES iteration (one V-cycle + "
+              f"Arnoldi) of the same workload after an untimed {res['setup_s']:.0f} s set-up, projected to the "
+              f"{n_it} iterations needed to reach {RTOL:g}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * n_it * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded, no dataset)",
+        "config": {"workload": p.name, "fine_elements": f"{p.n_fine}x{p.n_fine}", "levels": p.n_levels,
+                   "unknowns": res["n"], "vanka_group": p.patch, "restart": 30, "rtol": RTOL,
+                   "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(oracle_sample(args.config, args.sample_iters)), flush=True)
+        return
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(k, "1")
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * fsi.h -- C ABI of the GB300 (sm_103a) field-split GMG-preconditioned FGMRES
+ * solver for the linearised monolithic FSI system of Calandrini, Aulisa and
+ * Ke, "A field-split preconditioning technique for fluid-structure
+ * interaction problems with applications in biomechanics" (arXiv:1909.13201).
+ *
+ * The operation: solve J2 x = f (Sec. 3.2, Eq. matrix_J2: unknowns ordered
+ * d^s, d^f, p^s, u^s, u^f, p^f) by flexible GMRES, right-preconditioned by one
+ * geometric-multigrid V-cycle (Sec. 3.2-3.3: damped Richardson smoothing on
+ * levels l >= 1, direct solve on level 0; prolongation P2 and equation-aware
+ * restriction R2 of Sec. 3.3) whose smoother preconditioner is the additive
+ * field-split Schwarz method FS = blockdiag(AS1, AS2) of Sec. 3.2 (Vanka
+ * blocks solved by LU, Jacobi on the lumped mass K_u^s).
+ *
+ * Conventions shared by every call:
+ *   - all compute runs on the CUDA stream given at set-up, on the device that
+ *     was current then; every call returns after its stream work completed;
+ *   - vectors b, x, w, lambda are float64 arrays of the level-(L-1) dof count
+ *     in J2 order (fsi_get_dof_map gives field/component/node of each entry);
+ *     "device" pointers are cudaMalloc'd (or torch) memory of that device;
+ *   - the caller owns every buffer it passes; the context owns (and frees in
+ *     fsi_destroy) all device memory it allocates itself;
+ *   - no call aborts, traps or throws: each returns an fsi_status, and
+ *     fsi_last_error() gives a one-line message for the last failing call
+ *     of the calling thread.
+ */
+#ifndef FSI_H
+#define FSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsi_ctx fsi_ctx;
+
+typedef enum {
+    FSI_OK = 0,
+    FSI_ERR_ARG = 1,            /* invalid argument (null, size, option range) */
+    FSI_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    FSI_ERR_ALLOC = 3,          /* device or host allocation failed */
+    FSI_ERR_ZERO_PIVOT = 4,     /* a Schwarz block or the coarse matrix is singular */
+    FSI_ERR_NOT_CONVERGED = 5,  /* max_iters reached; x holds the last iterate */
+    FSI_ERR_BREAKDOWN = 6,      /* Arnoldi breakdown without convergence */
+    FSI_ERR_NONFINITE = 7,      /* NaN/Inf in a norm (input or arithmetic) */
+    FSI_ERR_STATE = 8           /* call out of order (e.g. solve before smoothers) */
+} fsi_status;
+
+enum { FSI_BC_CHANNEL_2D = 0, FSI_BC_BOX_3D = 1 };
+enum { FSI_FP64 = 0, FSI_MIXED = 1 };
+
+/* One linearised FSI problem on the unit square/cube (Sec. 2.2 weak form,
+ * linearised at d = 0 with a frozen advection field; linear-elastic solid
+ * with penalty pressure).  Host pointers, read during fsi_setup_hierarchy only. */
+typedef struct {
+    int dim;                    /* 2 or 3 */
+    int n_fine;                 /* fine elements per direction, divisible by 2^(n_levels-1) */
+    int n_levels;               /* GMG levels L >= 1 */
+    const uint8_t *material;    /* n_fine^dim, lexicographic x fastest; 1 solid, 0 fluid */
+    const double *advection;    /* dim x (2 n_fine + 1)^dim: w at the fine Q2 nodes, comp-major */
+    double mu_s, lambda_s, rho_s, rho_f, mu_f, dt;
+    int bc_preset;              /* FSI_BC_CHANNEL_2D or FSI_BC_BOX_3D */
+} fsi_problem;
+
+typedef struct {
+    int restriction;            /* 0: equation-aware R2 of Sec. 3.3 (default); 1: classical P^T */
+} fsi_hier_opts;
+
+typedef struct {
+    int precision;              /* FSI_FP64 or FSI_MIXED (float32 cycle, float64 Krylov) */
+    int patch;                  /* Vanka group edge b >= 1: b^dim pressure vertices per block */
+    double omega;               /* Richardson damping (Sec. 3.2), > 0 */
+    int nu_pre, nu_post;        /* smoothing steps, >= 1 */
+} fsi_smoother_opts;
+
+typedef struct {
+    double rtol;                /* stop when ||f - J2 x||_2 <= rtol ||f||_2 (float64 true residual) */
+    int restart;                /* FGMRES restart length m, 1..64 */
+    int max_iters;              /* total inner iterations */
+    int use_x0;                 /* 1: x holds the initial guess; 0: start from zero */
+} fsi_solve_opts;
+
+typedef struct {
+    int iterations;             /* N of Sec. 4: total FGMRES iterations */
+    int cycles;                 /* restart cycles run */
+    int converged;
+    int status;                 /* fsi_status of this solve */
+    double r0, rN;              /* initial and final true residual norms */
+    double rel_residual;        /* rN / ||f|| */
+    double rho;                 /* average convergence rate (rN / r0)^(1/N), Sec. 4 */
+    double solve_ms;            /* wall time of the call, host clock */
+} fsi_solve_stats;
+
+/* ---------------------------------------------------------------------------
+ * fsi_setup_hierarchy -- Sec. 3.3: levels by midpoint refinement (coarse
+ * element solid when any descendant is), J2 numbering per level (Eq.
+ * matrix_J2), level operators by rediscretisation (Sec. 2.2 weak form),
+ * transfers P2 and R2, and the coarse-level direct factorisation.
+ * probs: host array of n_probs problems (n_probs > 1 only for
+ * fsi_solve_batched).  cuda_stream: a cudaStream_t (NULL = legacy stream).
+ * On success *out owns all device memory it allocated. */
+fsi_status fsi_setup_hierarchy(const fsi_problem *probs, int n_probs, const fsi_hier_opts *opts,
+                               void *cuda_stream, fsi_ctx **out);
+
+/* fsi_setup_smoothers -- Sec. 3.2: Vanka index sets of AS1 (solid [d^s,p^s]
+ * and fluid [d^f] blocks) and AS2 (fluid [u^f,p^f] blocks) on every level
+ * l >= 1, gather of the dense blocks and their batched factorisation
+ * (inverted, stored float64 or float32 per opts->precision).  Returns
+ * FSI_ERR_ZERO_PIVOT if a block is singular.  May be called again to change
+ * the options. */
+fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts);
+
+/* fsi_solve -- FGMRES(restart) on J2 x = f with one V-cycle per iteration
+ * (Sec. 3.2).  b: device, f (J2 order, length fsi_get_sizes n_dofs of the
+ * fine level).  x: device, in: initial guess if opts->use_x0, out: solution.
+ * Problem 0 of the context.  Non-convergence returns FSI_ERR_NOT_CONVERGED
+ * with x holding the last iterate and st filled. */
+fsi_status fsi_solve(fsi_ctx *ctx, const double *b, double *x, const fsi_solve_opts *opts,
+                     fsi_solve_stats *st);
+
+/* fsi_solve_batched -- every problem of the context, b[i] and x[i] device
+ * vectors of problem i; st: host array of n_probs stats. */
+fsi_status fsi_solve_batched(fsi_ctx *ctx, const double *const *b, double *const *x,
+                             const fsi_solve_opts *opts, fsi_solve_stats *st);
+
+/* fsi_adjoint -- for J = w^T x with J2 x = f: solves J2^T lambda = w by
+ * FGMRES with the transposed V-cycle (transposed smoothers, restriction P^T,
+ * prolongation R^T), then dJ/df = lambda, dJ/dA_ij = -lambda_i x_j on the
+ * fine operator's CSR pattern (fsi_get_matrix order) and dJ/dmu_s =
+ * -lambda^T (dA/dmu_s) x at fixed lambda_s.  w, x, lambda, dA_vals: device;
+ * dA_vals (nnz) and dmu_s (host scalar) may be NULL.  Problem 0. */
+fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *lambda,
+                       double *dA_vals, double *dmu_s, const fsi_solve_opts *opts,
+                       fsi_solve_stats *st);
+
+/* ----------------------------- accessors --------------------------------- */
+
+/* Sizes of level `level` (0 = coarse .. L-1 = fine) of problem `prob`:
+ * out[0] n_dofs, out[1] nnz of A_l, out[2] number of Schwarz blocks,
+ * out[3] largest block, out[4..10] J2 group offsets (7 entries). */
+fsi_status fsi_get_sizes(const fsi_ctx *ctx, int prob, int level, int64_t *out);
+
+/* Host copies (n_dofs each) of the J2 dof map: field (0 d, 1 u, 2 p),
+ * component (pressure: 0 solid copy, 1 fluid copy) and Q2/Q1 node index. */
+fsi_status fsi_get_dof_map(const fsi_ctx *ctx, int prob, int level, int32_t *field,
+                           int32_t *comp, int32_t *node);
+
+/* Host copy of the float64 CSR of A_l: row_ptr (n+1), col (nnz), val (nnz). */
+fsi_status fsi_get_matrix(const fsi_ctx *ctx, int prob, int level, int64_t *row_ptr,
+                          int32_t *col, double *val);
+
+/* Host copy of the transfer between level l and l-1 (l >= 1): which = 0 P_l
+ * (n_l x n_{l-1}), 1 R_l (n_{l-1} x n_l).  Call with col/val NULL to get
+ * row_ptr only (row_ptr[n_rows] = nnz). */
+fsi_status fsi_get_transfer(const fsi_ctx *ctx, int prob, int level, int which, int64_t *row_ptr,
+                            int32_t *col, double *val);
+
+/* Host copy of the Schwarz block index sets of level l >= 1: blk_ptr
+ * (n_blocks+1), idx (blk_ptr[n_blocks]).  idx NULL: blk_ptr only. */
+fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_ptr, int32_t *idx);
+
+/* ------------------- single-operation entry points ------------------------
+ * Device-vector calls of one piece of the path, in the level's working
+ * precision converted from/to float64 at the boundary; used to check each
+ * piece against the oracle.  All vectors device float64. */
+
+/* y = A_l x (float64 operator). */
+fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x, double *y);
+
+/* y = P2^{-1} r on level l >= 1 (transpose != 0: P2^{-T} r), Sec. 3.2. */
+fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
+                              int transpose);
+
+/* z = M^{-1} v: one V-cycle from zero on the fine level (transpose != 0: the
+ * transposed cycle). */
+fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, int transpose);
+
+/* Kernel profiling (no counterpart in the paper; measurement support).
+ * mode 1: reset the counters and start recording CUDA events around the
+ * fine-level smoother apply and fine-level residual SpMV launches of the
+ * following solves; mode 0: stop recording; mode 2: read only.
+ * out (host, 8 doubles): [0] smoother launches timed, [1] their total ms,
+ * [2] algorithmic bytes per smoother launch (block inverses, index, weight,
+ * gather and scatter traffic), [3] SpMV launches timed, [4] their total ms,
+ * [5] algorithmic bytes per SpMV launch, [6] kernels launched by the library
+ * since the last reset, [7] reserved.  Problem 0. */
+fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
+
+/* Host-only inspection context: builds the levels, numbering, operator
+ * sparsity patterns, transfers and (for patch >= 1) the Schwarz block index
+ * sets on the host without touching a GPU, so that fsi_get_sizes,
+ * fsi_get_dof_map, fsi_get_pattern, fsi_get_transfer and fsi_get_blocks can
+ * be called on machines without CUDA devices.  Every other call on such a
+ * context returns FSI_ERR_STATE.  Release with fsi_destroy. */
+fsi_status fsi_setup_host_only(const fsi_problem *prob, const fsi_hier_opts *opts, int patch,
+                               fsi_ctx **out);
+
+/* Host copy of the sparsity pattern of A_l: row_ptr (n+1), col (nnz). */
+fsi_status fsi_get_pattern(const fsi_ctx *ctx, int prob, int level, int64_t *row_ptr, int32_t *col);
+
+/* Release everything the context owns.  NULL is a no-op. */
+void fsi_destroy(fsi_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *fsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_H */

@@ -38,7 +38,7 @@ import numpy as np
 import scipy.linalg as la
 import scipy.sparse as sp
 
-from .mesh import Level, lex
+from .mesh import Level, flat, lex
 from .transfer import G_US
 
 
@@ -46,21 +46,21 @@ def vertex_groups(lev: Level, b: int) -> list[np.ndarray]:
     """Q1 vertices of the b^dim tiles of the vertex lattice, tiles in lex order."""
     m1 = lev.n + 1
     npd = -(-m1 // b)
-    c1 = lex(lev.dim, m1)
-    out = []
-    for tc in lex(lev.dim, npd):
-        lo = tc * b
-        sel = np.all((c1 >= lo) & (c1 < lo + b), 1)
-        out.append(np.flatnonzero(sel))
-    return out
+    tile = flat(lex(lev.dim, m1) // b, npd)           # tile of every vertex
+    order = np.argsort(tile, kind="stable")            # vertices in lex order inside a tile
+    bounds = np.searchsorted(tile[order], np.arange(npd ** lev.dim + 1))
+    return [order[bounds[t]:bounds[t + 1]] for t in range(npd ** lev.dim)]
 
 
-def vertex_elements(lev: Level) -> list[list[int]]:
-    """Elements touching each Q1 vertex."""
-    out = [[] for _ in range(lev.nq1)]
-    for e in range(lev.material.size):
-        for z in lev.elem_q1[e]:
-            out[z].append(e)
+def vertex_elements(lev: Level) -> np.ndarray:
+    """(nq1, 2^dim) elements touching each Q1 vertex, -1 where absent."""
+    nv = 2 ** lev.dim
+    out = np.full((lev.nq1, nv), -1, np.int64)
+    fill = np.zeros(lev.nq1, np.int64)
+    for al in range(nv):                      # each element touches its 2^dim vertices once
+        z = lev.elem_q1[:, al]
+        out[z, fill[z]] = np.arange(lev.material.size)
+        fill[z] += 1
     return out
 
 
@@ -70,14 +70,18 @@ def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
     blocks = []
     for grp in vertex_groups(lev, b):
         cand = []
-        zs = [z for z in grp if lev.ps_dof[z] >= 0]
-        els = sorted({e for z in zs for e in touch[z] if lev.material[e] == 1})
-        if els:
+        zs = grp[lev.ps_dof[grp] >= 0]
+        els = touch[zs].ravel()
+        els = np.unique(els[(els >= 0)])
+        els = els[lev.material[els] == 1]
+        if els.size:
             q2 = np.unique(lev.elem_q2[els])
             cand.append(np.concatenate([lev.d_dof[q2].ravel(), lev.ps_dof[zs]]))
-        zf = [z for z in grp if lev.pf_dof[z] >= 0]
-        els = sorted({e for z in zf for e in touch[z] if lev.material[e] == 0})
-        if els:
+        zf = grp[lev.pf_dof[grp] >= 0]
+        els = touch[zf].ravel()
+        els = np.unique(els[(els >= 0)])
+        els = els[lev.material[els] == 0]
+        if els.size:
             q2 = np.unique(lev.elem_q2[els])
             q2 = q2[~lev.q2_solid[q2]]
             cand.append(lev.d_dof[q2].ravel())
@@ -106,9 +110,18 @@ class FSASM:
             else (mult > 0).astype(np.float64)
         Ad = A.tocsr()
         self.lu = []
+        local = np.full(self.n, -1, np.int64)         # global dof -> position in the block
         for idx in self.blocks:
-            blk = Ad[idx][:, idx].toarray().astype(dtype)
-            self.lu.append(la.lu_factor(blk, check_finite=True))
+            # A_jj = A[I_j, I_j]: the block's rows, columns mapped into the block
+            sub = Ad[idx]
+            local[idx] = np.arange(idx.size)
+            cols = local[sub.indices]
+            keep = cols >= 0
+            rows = np.repeat(np.arange(idx.size), np.diff(sub.indptr))
+            blk = np.zeros((idx.size, idx.size))
+            blk[rows[keep], cols[keep]] = sub.data[keep]
+            local[idx] = -1
+            self.lu.append(la.lu_factor(blk.astype(dtype), check_finite=True))
         self.jacobi = np.flatnonzero((lev.group == G_US) | lev.fixed)
         self.inv_diag = 1.0 / Ad.diagonal()[self.jacobi]
 

@@ -31,64 +31,55 @@ from .fem import q1_1d, q2_1d
 from .mesh import Level, flat, lex
 
 
-def _weights_1d(basis, frac: float) -> np.ndarray:
-    return basis(frac)[0]
-
-
 def prolongation(fine: Level, coarse: Level) -> sp.csr_matrix:
+    """Nodal interpolation, vectorised over the fine nodes."""
     dim = fine.dim
     nc = coarse.n
     rows, cols, vals = [], [], []
-    # --- Q2 fields (d and u), node by node ---
-    c2 = lex(dim, 2 * fine.n + 1)
-    for y in range(fine.nq2):
-        pos = c2[y]                       # fine Q2 index; coarse element spans 4 fine Q2 steps
-        el = np.minimum(pos // 4, nc - 1)
-        frac = (pos - 4 * el) / 4.0
-        w1 = [_weights_1d(q2_1d, frac[k]) for k in range(dim)]
-        for a in itertools.product(range(3), repeat=dim):
-            a = a[::-1]
-            wt = 1.0
-            for k in range(dim):
-                wt *= w1[k][a[k]]
-            if wt == 0.0:
-                continue
-            Y = flat(2 * el + np.array(a), 2 * nc + 1)
-            for comp in range(dim):
-                for tab_f, tab_c in ((fine.d_dof, coarse.d_dof), (fine.v_dof, coarse.v_dof)):
-                    r, c = tab_f[y, comp], tab_c[Y, comp]
-                    if fine.fixed[r] or coarse.fixed[c]:
-                        continue
-                    rows.append(r); cols.append(c); vals.append(wt)
+    # --- Q2 fields (d and u) ---
+    pos = lex(dim, 2 * fine.n + 1)                     # fine Q2 lattice indices
+    el = np.minimum(pos // 4, nc - 1)                  # coarse element spans 4 fine Q2 steps
+    frac = (pos - 4 * el) / 4.0
+    w1 = [q2_1d(frac[:, k])[0] for k in range(dim)]    # (3, nq2) per direction
+    for a in itertools.product(range(3), repeat=dim):
+        a = np.array(a[::-1])                          # local coarse node, x fastest
+        wt = np.ones(fine.nq2)
+        for k in range(dim):
+            wt = wt * w1[k][a[k]]
+        Y = flat(2 * el + a, 2 * nc + 1)
+        for comp in range(dim):
+            for tab_f, tab_c in ((fine.d_dof, coarse.d_dof), (fine.v_dof, coarse.v_dof)):
+                r, c = tab_f[:, comp], tab_c[Y, comp]
+                keep = (wt != 0.0) & ~fine.fixed[r] & ~coarse.fixed[c]
+                rows.append(r[keep]); cols.append(c[keep]); vals.append(wt[keep])
     # --- Q1 pressure copies ---
-    c1 = lex(dim, fine.n + 1)
-    for z in range(fine.nq1):
-        pos = c1[z]                       # fine Q1 index; coarse element spans 2 steps
-        cands = []                        # containing coarse elements
-        for off in itertools.product(*[sorted({min(p // 2, nc - 1), max((p - 1) // 2, 0)})
-                                       for p in pos[::-1]]):
-            el = np.array(off[::-1])
-            if np.all(2 * el <= pos) and np.all(pos <= 2 * el + 2):
-                cands.append(el)
-        for copy, has_f, dof_f, dof_c, mat in ((0, fine.q1_has_s, fine.ps_dof, coarse.ps_dof, 1),
-                                               (1, fine.q1_has_f, fine.pf_dof, coarse.pf_dof, 0)):
-            if not has_f[z]:
-                continue
-            el = next((e for e in cands if coarse.material[flat(e, nc)] == mat), None)
-            if el is None:
-                continue                  # p^f with no coarse fluid parent: zero row
-            frac = (pos - 2 * el) / 2.0
-            w1 = [_weights_1d(q1_1d, frac[k]) for k in range(dim)]
-            for a in itertools.product(range(2), repeat=dim):
-                a = a[::-1]
-                wt = 1.0
-                for k in range(dim):
-                    wt *= w1[k][a[k]]
-                if wt == 0.0:
-                    continue
-                Z = flat(el + np.array(a), nc + 1)
-                rows.append(dof_f[z]); cols.append(dof_c[Z]); vals.append(wt)
-    P = sp.coo_matrix((vals, (rows, cols)), shape=(fine.n_dofs, coarse.n_dofs)).tocsr()
+    pos = lex(dim, fine.n + 1)                         # fine Q1 lattice; coarse element spans 2 steps
+    lo = np.maximum((pos - 1) // 2, 0)
+    hi = np.minimum(pos // 2, nc - 1)
+    # candidate containing coarse elements, x fastest; both choices contain the vertex
+    cand = []
+    for t in range(2 ** dim):
+        e = np.where(np.array([(t >> k) & 1 for k in range(dim)])[None, :] == 1, hi, lo)
+        cand.append(e)
+    cand = np.stack(cand, 1)                           # (nq1, 2^dim, dim)
+    cmat = coarse.material[flat(cand, nc)]             # (nq1, 2^dim)
+    for has_f, dof_f, dof_c, mat in ((fine.q1_has_s, fine.ps_dof, coarse.ps_dof, 1),
+                                     (fine.q1_has_f, fine.pf_dof, coarse.pf_dof, 0)):
+        match = cmat == mat
+        ok = has_f & match.any(1)                      # p^f with no coarse fluid parent: zero row
+        first = np.argmax(match, 1)
+        E = cand[np.arange(pos.shape[0]), first]       # chosen coarse element
+        fr = (pos - 2 * E) / 2.0
+        for a in itertools.product(range(2), repeat=dim):
+            a = np.array(a[::-1])
+            wt = np.ones(pos.shape[0])
+            for k in range(dim):
+                wt = wt * (fr[:, k] if a[k] else 1.0 - fr[:, k])
+            keep = ok & (wt != 0.0)
+            Z = flat(E + a, nc + 1)
+            rows.append(dof_f[keep]); cols.append(dof_c[Z[keep]]); vals.append(wt[keep])
+    P = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(fine.n_dofs, coarse.n_dofs)).tocsr()
     P.sum_duplicates()
     P.sort_indices()
     return P

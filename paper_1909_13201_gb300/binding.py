@@ -1,0 +1,344 @@
+"""Thin Python binding of the C ABI in include/fsi.h (ctypes).
+
+Argument marshalling only: every step of set-up and solve runs inside
+libfsi.so (host set-up code and CUDA kernels).  PyTorch supplies device
+memory and the CUDA stream.  There is no fallback: if the library is missing
+or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FSI_OK, FSI_ERR_ARG, FSI_ERR_CUDA, FSI_ERR_ALLOC, FSI_ERR_ZERO_PIVOT, FSI_ERR_NOT_CONVERGED, \
+    FSI_ERR_BREAKDOWN, FSI_ERR_NONFINITE, FSI_ERR_STATE = range(9)
+FSI_FP64, FSI_MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_ALLOC", 4: "ERR_ZERO_PIVOT",
+                5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_NONFINITE", 8: "ERR_STATE"}
+
+EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solve_batched",
+            "fsi_adjoint", "fsi_get_sizes", "fsi_get_dof_map", "fsi_get_matrix", "fsi_get_transfer",
+            "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
+            "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_destroy", "fsi_last_error"]
+
+
+class FSIError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem_t(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_fine", C.c_int), ("n_levels", C.c_int),
+                ("material", C.POINTER(C.c_uint8)), ("advection", C.POINTER(C.c_double)),
+                ("mu_s", C.c_double), ("lambda_s", C.c_double), ("rho_s", C.c_double),
+                ("rho_f", C.c_double), ("mu_f", C.c_double), ("dt", C.c_double),
+                ("bc_preset", C.c_int)]
+
+
+class HierOpts_t(C.Structure):
+    _fields_ = [("restriction", C.c_int)]
+
+
+class SmootherOpts_t(C.Structure):
+    _fields_ = [("precision", C.c_int), ("patch", C.c_int), ("omega", C.c_double),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int)]
+
+
+class SolveOpts_t(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("max_iters", C.c_int),
+                ("use_x0", C.c_int)]
+
+
+class SolveStats_t(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("cycles", C.c_int), ("converged", C.c_int),
+                ("status", C.c_int), ("r0", C.c_double), ("rN", C.c_double),
+                ("rel_residual", C.c_double), ("rho", C.c_double), ("solve_ms", C.c_double)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False) -> C.CDLL:
+    """Load libfsi.so (optionally building it first).  Raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build() first")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I, I64, I32, D, U8 = C.c_void_p, C.c_int, C.c_int64, C.c_int32, C.c_double, C.c_uint8
+    lib.fsi_setup_hierarchy.argtypes = [C.POINTER(Problem_t), I, C.POINTER(HierOpts_t), P, C.POINTER(P)]
+    lib.fsi_setup_smoothers.argtypes = [P, C.POINTER(SmootherOpts_t)]
+    lib.fsi_solve.argtypes = [P, P, P, C.POINTER(SolveOpts_t), C.POINTER(SolveStats_t)]
+    lib.fsi_solve_batched.argtypes = [P, C.POINTER(P), C.POINTER(P), C.POINTER(SolveOpts_t),
+                                      C.POINTER(SolveStats_t)]
+    lib.fsi_adjoint.argtypes = [P, P, P, P, P, C.POINTER(D), C.POINTER(SolveOpts_t), C.POINTER(SolveStats_t)]
+    lib.fsi_get_sizes.argtypes = [P, I, I, C.POINTER(I64)]
+    lib.fsi_get_dof_map.argtypes = [P, I, I, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]
+    lib.fsi_get_matrix.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32), C.POINTER(D)]
+    lib.fsi_get_transfer.argtypes = [P, I, I, I, C.POINTER(I64), C.POINTER(I32), C.POINTER(D)]
+    lib.fsi_get_blocks.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
+    lib.fsi_apply_operator.argtypes = [P, I, I, P, P]
+    lib.fsi_apply_smoother.argtypes = [P, I, I, P, P, I]
+    lib.fsi_apply_vcycle.argtypes = [P, I, P, P, I]
+    lib.fsi_setup_host_only.argtypes = [C.POINTER(Problem_t), C.POINTER(HierOpts_t), I, C.POINTER(P)]
+    lib.fsi_get_pattern.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
+    lib.fsi_profile.argtypes = [P, I, C.POINTER(D)]
+    lib.fsi_destroy.argtypes = [P]
+    lib.fsi_destroy.restype = None
+    lib.fsi_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("fsi_destroy", "fsi_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status != FSI_OK and status not in allow:
+        raise FSIError(status, load_library().fsi_last_error().decode())
+    return status
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous CUDA float64 tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+class FSISolver:
+    """Handle on one fsi_ctx (one or many problems, same device and stream).
+
+    host_only=True builds only the host-side structure (no GPU needed) for
+    inspection: sizes, dof maps, patterns, transfers and block sets."""
+
+    def __init__(self, problems, restriction: int = 0, stream=None, host_only=False, patch=None):
+        lib = load_library()
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.problems = list(problems)
+        self._keep = []
+        arr = (Problem_t * len(problems))()
+        for i, p in enumerate(problems):
+            mat = np.ascontiguousarray(p.material, dtype=np.uint8)
+            adv = np.ascontiguousarray(p.advection, dtype=np.float64)
+            self._keep += [mat, adv]
+            arr[i] = Problem_t(p.dim, p.n_fine, p.n_levels, _ptr(mat, C.c_uint8), _ptr(adv, C.c_double),
+                               p.mu_s, p.lambda_s, p.rho_s, p.rho_f, p.mu_f, p.dt, p.bc_preset)
+        self.ctx = C.c_void_p()
+        ho = HierOpts_t(restriction)
+        if host_only:
+            if len(problems) != 1:
+                raise ValueError("host-only inspection takes one problem")
+            b = problems[0].patch if patch is None else patch
+            _check(lib.fsi_setup_host_only(arr, C.byref(ho), b, C.byref(self.ctx)))
+            self.stream = None
+        else:
+            import torch
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            _check(lib.fsi_setup_hierarchy(arr, len(problems), C.byref(ho), C.c_void_p(self.stream.cuda_stream),
+                                           C.byref(self.ctx)))
+        self._keep = []
+        self.precision = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) and self.ctx.value:
+                load_library().fsi_destroy(self.ctx)
+                self.ctx = C.c_void_p()
+        except Exception:
+            pass
+
+    def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=1.0, nu_pre=1, nu_post=1):
+        if patch is None:
+            patch = self.problems[0].patch
+        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post)
+        _check(load_library().fsi_setup_smoothers(self.ctx, C.byref(so)))
+        self.precision = precision
+
+    @staticmethod
+    def _opts(rtol, restart, max_iters, use_x0):
+        return SolveOpts_t(rtol, restart, max_iters, 1 if use_x0 else 0)
+
+    def solve(self, b, x=None, rtol=1e-8, restart=30, max_iters=1000, check=True):
+        """Solve J2 x = b on problem 0.  b: CUDA float64 tensor (host tensors
+        are copied in and the result copied back)."""
+        import torch
+        host = not b.is_cuda
+        bd = b.to("cuda", non_blocking=True) if host else b
+        use_x0 = x is not None
+        xd = (x.to("cuda") if (x is not None and not x.is_cuda) else x) if use_x0 else torch.empty_like(bd)
+        st = SolveStats_t()
+        opts = self._opts(rtol, restart, max_iters, use_x0)
+        s = load_library().fsi_solve(self.ctx, _dptr(bd), _dptr(xd), C.byref(opts), C.byref(st))
+        if check:
+            _check(s)
+        out = xd.to("cpu") if host else xd
+        return out, st.to_dict()
+
+    def solve_batched(self, bs, xs=None, rtol=1e-8, restart=30, max_iters=1000, check=True):
+        import torch
+        n = len(self.problems)
+        xs = xs if xs is not None else [torch.empty_like(b) for b in bs]
+        bp = (C.c_void_p * n)(*[_dptr(b) for b in bs])
+        xp = (C.c_void_p * n)(*[_dptr(x) for x in xs])
+        st = (SolveStats_t * n)()
+        opts = self._opts(rtol, restart, max_iters, False)
+        s = load_library().fsi_solve_batched(self.ctx, bp, xp, C.byref(opts), st)
+        if check:
+            _check(s)
+        return xs, [st[i].to_dict() for i in range(n)]
+
+    def adjoint(self, w, x, rtol=1e-8, restart=30, max_iters=1000, want_dA=True, want_dmu=True, check=True):
+        import torch
+        lam = torch.empty_like(w)
+        nnz = self.sizes(self.n_levels - 1)["nnz"]
+        dA = torch.empty(nnz, dtype=torch.float64, device=w.device) if want_dA else None
+        dmu = C.c_double(0.0)
+        st = SolveStats_t()
+        opts = self._opts(rtol, restart, max_iters, False)
+        s = load_library().fsi_adjoint(self.ctx, _dptr(w), _dptr(x), _dptr(lam),
+                                       _dptr(dA) if want_dA else None,
+                                       C.byref(dmu) if want_dmu else None, C.byref(opts), C.byref(st))
+        if check:
+            _check(s)
+        return lam, dA, (dmu.value if want_dmu else None), st.to_dict()
+
+    def profile(self, mode):
+        """mode 1 start (reset), 0 stop, 2 read.  Returns the counters of
+        fsi_profile as a dict."""
+        out = np.zeros(8, np.float64)
+        _check(load_library().fsi_profile(self.ctx, mode, _ptr(out, C.c_double)))
+        return {"smoother_launches": int(out[0]), "smoother_ms": out[1], "smoother_bytes": out[2],
+                "spmv_launches": int(out[3]), "spmv_ms": out[4], "spmv_bytes": out[5],
+                "kernel_launches": int(out[6])}
+
+    # ------------------------------------------------------------ accessors
+    @property
+    def n_levels(self):
+        return self.problems[0].n_levels
+
+    def sizes(self, level, prob=0):
+        out = np.zeros(11, np.int64)
+        _check(load_library().fsi_get_sizes(self.ctx, prob, level, _ptr(out, C.c_int64)))
+        return {"n": int(out[0]), "nnz": int(out[1]), "n_blocks": int(out[2]), "max_block": int(out[3]),
+                "offsets": out[4:11].copy()}
+
+    def dof_map(self, level, prob=0):
+        n = self.sizes(level, prob)["n"]
+        f, c, nd = (np.zeros(n, np.int32) for _ in range(3))
+        _check(load_library().fsi_get_dof_map(self.ctx, prob, level, _ptr(f, C.c_int32), _ptr(c, C.c_int32),
+                                              _ptr(nd, C.c_int32)))
+        return f, c, nd
+
+    def matrix(self, level, prob=0):
+        sz = self.sizes(level, prob)
+        ptr = np.zeros(sz["n"] + 1, np.int64)
+        col = np.zeros(sz["nnz"], np.int32)
+        val = np.zeros(sz["nnz"], np.float64)
+        _check(load_library().fsi_get_matrix(self.ctx, prob, level, _ptr(ptr, C.c_int64), _ptr(col, C.c_int32),
+                                             _ptr(val, C.c_double)))
+        return ptr, col, val
+
+    def pattern(self, level, prob=0):
+        sz = self.sizes(level, prob)
+        ptr = np.zeros(sz["n"] + 1, np.int64)
+        col = np.zeros(sz["nnz"], np.int32)
+        _check(load_library().fsi_get_pattern(self.ctx, prob, level, _ptr(ptr, C.c_int64), _ptr(col, C.c_int32)))
+        return ptr, col
+
+    def transfer(self, level, which, prob=0):
+        lib = load_library()
+        nrows = self.sizes(level, prob)["n"] if which == 0 else self.sizes(level - 1, prob)["n"]
+        ptr = np.zeros(nrows + 1, np.int64)
+        _check(lib.fsi_get_transfer(self.ctx, prob, level, which, _ptr(ptr, C.c_int64), None, None))
+        col = np.zeros(int(ptr[-1]), np.int32)
+        val = np.zeros(int(ptr[-1]), np.float64)
+        _check(lib.fsi_get_transfer(self.ctx, prob, level, which, _ptr(ptr, C.c_int64), _ptr(col, C.c_int32),
+                                    _ptr(val, C.c_double)))
+        return ptr, col, val
+
+    def blocks(self, level, prob=0):
+        lib = load_library()
+        nb = self.sizes(level, prob)["n_blocks"]
+        ptr = np.zeros(nb + 1, np.int64)
+        _check(lib.fsi_get_blocks(self.ctx, prob, level, _ptr(ptr, C.c_int64), None))
+        idx = np.zeros(int(ptr[-1]), np.int32)
+        _check(lib.fsi_get_blocks(self.ctx, prob, level, _ptr(ptr, C.c_int64), _ptr(idx, C.c_int32)))
+        return ptr, idx
+
+    def apply_operator(self, level, x, prob=0):
+        import torch
+        y = torch.empty_like(x)
+        _check(load_library().fsi_apply_operator(self.ctx, prob, level, _dptr(x), _dptr(y)))
+        return y
+
+    def apply_smoother(self, level, r, transpose=False, prob=0):
+        import torch
+        y = torch.empty_like(r)
+        _check(load_library().fsi_apply_smoother(self.ctx, prob, level, _dptr(r), _dptr(y), int(transpose)))
+        return y
+
+    def apply_vcycle(self, v, transpose=False, prob=0):
+        import torch
+        z = torch.empty_like(v)
+        _check(load_library().fsi_apply_vcycle(self.ctx, prob, _dptr(v), _dptr(z), int(transpose)))
+        return z
+
+
+def _make_autograd():
+    import torch
+
+    class FSISolve(torch.autograd.Function):
+        """x = J2^{-1} b with a hand-written backward: the adjoint solve
+        J2^T lambda = dL/dx (transposed V-cycle preconditioner), giving
+        dL/db = lambda.  The gradients with respect to the operator values
+        and mu_s are available from FSISolver.adjoint."""
+
+        @staticmethod
+        def forward(ctx, b, solver, rtol=1e-8):
+            x, st = solver.solve(b, rtol=rtol)
+            ctx.solver = solver
+            ctx.rtol = rtol
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (x,) = ctx.saved_tensors
+            lam, _, _, _ = ctx.solver.adjoint(gx.contiguous(), x, rtol=ctx.rtol, want_dA=False, want_dmu=False)
+            return lam, None, None
+
+    return FSISolve
+
+
+_FSISOLVE = None
+
+
+def fsi_solve_autograd(b, solver, rtol=1e-8):
+    """Differentiable x = J2^{-1} b (torch.autograd.Function, adjoint backward)."""
+    global _FSISOLVE
+    if _FSISOLVE is None:
+        _FSISOLVE = _make_autograd()
+    return _FSISOLVE.apply(b, solver, rtol)

@@ -1,0 +1,929 @@
+// C ABI of the solver (include/fsi.h): set-up of the hierarchy and the
+// smoothers, the V-cycle (Sec. 3.2-3.3) and restarted flexible GMRES, the
+// adjoint, and accessors.  Host code here only orders kernel launches and
+// moves set-up data; every arithmetic step of a solve runs in the kernels.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <type_traits>
+
+#include "context.h"
+
+namespace fsi {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int NRED = 304;           // CTAs of the Krylov reductions (2 per SM)
+
+// lanes per row of the SpMV kernel from the mean row length
+int pick_group(int64_t rows, int64_t nnz) {
+    const double avg = rows ? (double)nnz / (double)rows : 0.0;
+    if (avg <= 3) return 1;
+    if (avg <= 8) return 2;
+    if (avg <= 20) return 4;
+    if (avg <= 64) return 8;
+    return 16;
+}
+
+fsi_status upload(DevBuf &d, const void *h, size_t bytes, cudaStream_t s) {
+    FSI_TRY(d.alloc(bytes));
+    if (bytes) FSI_CUDA(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
+    return FSI_OK;
+}
+
+// host CSR (int64 ptr) -> device CSR (int32 ptr/col, float64 values)
+fsi_status upload_csr(DevCSR &D, const HostCSR &H, cudaStream_t s) {
+    if (H.nnz() > INT32_MAX) {
+        set_error("operator has more than 2^31 nonzeros");
+        return FSI_ERR_ARG;
+    }
+    D.n_rows = H.n_rows;
+    D.n_cols = H.n_cols;
+    D.nnz = H.nnz();
+    std::vector<int32_t> p32(H.ptr.begin(), H.ptr.end());
+    FSI_TRY(upload(D.ptr, p32.data(), p32.size() * 4, s));
+    FSI_TRY(upload(D.col, H.col.data(), H.col.size() * 4, s));
+    if (!H.val.empty()) FSI_TRY(upload(D.val64, H.val.data(), H.val.size() * 8, s));
+    D.group = pick_group(D.n_rows, D.nnz);
+    FSI_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    return FSI_OK;
+}
+
+fsi_status make_f32(DevCSR &D, cudaStream_t s) {
+    if (D.val32.p || D.nnz == 0) return FSI_OK;
+    FSI_TRY(D.val32.alloc((size_t)D.nnz * 4));
+    return launch_cast_f64_f32(D.val64.as<double>(), D.val32.as<float>(), D.nnz, s);
+}
+
+// device CSR -> host CSR (with values)
+fsi_status download_csr(const DevCSR &D, HostCSR &H, cudaStream_t s) {
+    std::vector<int32_t> p32(D.n_rows + 1);
+    H.n_rows = D.n_rows;
+    H.n_cols = D.n_cols;
+    H.col.resize(D.nnz);
+    H.val.resize(D.nnz);
+    FSI_CUDA(cudaMemcpyAsync(p32.data(), D.ptr.p, p32.size() * 4, cudaMemcpyDeviceToHost, s));
+    if (D.nnz) {
+        FSI_CUDA(cudaMemcpyAsync(H.col.data(), D.col.p, (size_t)D.nnz * 4, cudaMemcpyDeviceToHost, s));
+        FSI_CUDA(cudaMemcpyAsync(H.val.data(), D.val64.p, (size_t)D.nnz * 8, cudaMemcpyDeviceToHost, s));
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    H.ptr.assign(p32.begin(), p32.end());
+    return FSI_OK;
+}
+
+void transpose_csr(const HostCSR &A, HostCSR &T) {
+    T.n_rows = A.n_cols;
+    T.n_cols = A.n_rows;
+    T.ptr.assign(T.n_rows + 1, 0);
+    for (int64_t k = 0; k < A.nnz(); ++k) T.ptr[A.col[k] + 1]++;
+    for (int64_t r = 0; r < T.n_rows; ++r) T.ptr[r + 1] += T.ptr[r];
+    T.col.resize(A.nnz());
+    T.val.resize(A.nnz());
+    std::vector<int64_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+    for (int64_t r = 0; r < A.n_rows; ++r)
+        for (int64_t k = A.ptr[r]; k < A.ptr[r + 1]; ++k) {
+            const int64_t q = pos[A.col[k]]++;
+            T.col[q] = (int32_t)r;
+            T.val[q] = A.val[k];
+        }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+fsi_status read_flag(Context &cx, int *out) {
+    FSI_CUDA(cudaMemcpyAsync(out, cx.flags.p, 4, cudaMemcpyDeviceToHost, cx.stream));
+    FSI_CUDA(cudaStreamSynchronize(cx.stream));
+    return FSI_OK;
+}
+
+// --------------------------------------------------------------- V-cycle
+template <class T> const T *mval(const DevCSR &A);
+template <> const float *mval<float>(const DevCSR &A) { return A.val32.as<float>(); }
+template <> const double *mval<double>(const DevCSR &A) { return A.val64.as<double>(); }
+
+// x += omega P2^{-1} r: Schwarz blocks and the Jacobi rows in one launch
+// CUDA events around fine-level launches while profiling (fsi_profile)
+cudaEvent_t take_event(Context &cx) {
+    if (cx.ev_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = cx.ev_pool.back();
+    cx.ev_pool.pop_back();
+    return e;
+}
+struct ProfMark {
+    Context &cx;
+    int kind;
+    bool on;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfMark(Context &c, int k, bool enable) : cx(c), kind(k), on(enable && c.profile) {
+        if (on) {
+            a = take_event(cx);
+            b = take_event(cx);
+            cudaEventRecord(a, cx.stream);
+        }
+    }
+    ~ProfMark() {
+        if (on) {
+            cudaEventRecord(b, cx.stream);
+            cx.ev_marks.push_back({kind, {a, b}});
+        }
+    }
+};
+// after the stream is idle: add the recorded durations to the totals
+void collect_marks(Context &cx) {
+    for (auto &m : cx.ev_marks) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, m.second.first, m.second.second);
+        cx.prof_ms[m.first] += ms;
+        cx.prof_n[m.first] += 1;
+        cx.ev_pool.push_back(m.second.first);
+        cx.ev_pool.push_back(m.second.second);
+    }
+    cx.ev_marks.clear();
+}
+
+template <class T>
+fsi_status smooth_apply(Context &cx, LevelDev &L, const T *r, T *x, bool tr, bool fine = false) {
+    ProfMark pm(cx, 0, fine);
+    return launch_block_apply<T>(L, r, x, (T)cx.omega, tr ? 1 : 0, cx.stream);
+}
+
+// x_l = M_l^{-1} b_l from a zero guess (transposed cycle if tr)
+template <class T>
+fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
+    cudaStream_t s = cx.stream;
+    if (l == 0) return launch_dense_gemv<T>(pb.coarse_inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
+    LevelDev &L = pb.dev[l];
+    LevelDev &C = pb.dev[l - 1];
+    const DevCSR &A = tr ? L.AT : L.A;
+    const DevCSR &Rm = tr ? L.PT : L.R;     // restriction
+    const DevCSR &Pm = tr ? L.RT : L.P;     // prolongation
+    const int npre = tr ? cx.nu_post : cx.nu_pre, npost = tr ? cx.nu_pre : cx.nu_post;
+    const bool fine = l == (int)pb.dev.size() - 1;
+    T *r = L.r.as<T>();
+    FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), s));
+    for (int k = 0; k < npre; ++k) {
+        if (k == 0) {
+            FSI_TRY(smooth_apply<T>(cx, L, b, x, tr, fine));
+        } else {
+            FSI_TRY(launch_spmv<T, T, T>(A, mval<T>(A), x, b, r, SPMV_RESID, s));
+            FSI_TRY(smooth_apply<T>(cx, L, r, x, tr, fine));
+        }
+    }
+    {
+        ProfMark pm(cx, 1, fine);
+        FSI_TRY(launch_spmv<T, T, T>(A, mval<T>(A), x, b, r, SPMV_RESID, s));
+    }
+    FSI_TRY(launch_spmv<T, T, T>(Rm, mval<T>(Rm), r, (const T *)nullptr, C.b.as<T>(), SPMV_SET, s));
+    FSI_TRY(vcycle<T>(cx, pb, l - 1, C.b.as<T>(), C.x.as<T>(), tr));
+    FSI_TRY(launch_spmv<T, T, T>(Pm, mval<T>(Pm), C.x.as<T>(), (const T *)nullptr, x, SPMV_ADD, s));
+    for (int k = 0; k < npost; ++k) {
+        {
+            ProfMark pm(cx, 1, fine);
+            FSI_TRY(launch_spmv<T, T, T>(A, mval<T>(A), x, b, r, SPMV_RESID, s));
+        }
+        FSI_TRY(smooth_apply<T>(cx, L, r, x, tr, fine));
+    }
+    return FSI_OK;
+}
+
+// ------------------------------------------------------------ workspace
+fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
+    if (pb.m_alloc >= m) return FSI_OK;
+    const int64_t n = pb.dev.back().n;
+    const size_t tsz = cx.precision == FSI_MIXED ? 4 : 8;
+    FSI_TRY(pb.V.alloc((size_t)n * (m + 1) * 8));
+    FSI_TRY(pb.Z.alloc((size_t)n * m * 8));     // float64: the outer SpMV reads it without conversions
+    FSI_TRY(pb.H.alloc((size_t)(m + 1) * m * 8));
+    FSI_TRY(pb.g.alloc((size_t)(m + 2) * 8));
+    FSI_TRY(pb.cs.alloc((size_t)(m + 1) * 8));
+    FSI_TRY(pb.sn.alloc((size_t)(m + 1) * 8));
+    FSI_TRY(pb.y.alloc((size_t)(m + 1) * 8));
+    FSI_TRY(pb.w.alloc((size_t)n * 8));
+    FSI_TRY(pb.rvec.alloc((size_t)n * 8));
+    FSI_TRY(pb.partials.alloc((size_t)NRED * 65 * 8));
+    FSI_TRY(pb.scal.alloc(64 * 8));
+    FSI_TRY(pb.h1.alloc((size_t)(m + 1) * 8));
+    FSI_TRY(pb.h2.alloc((size_t)(m + 1) * 8));
+    pb.m_alloc = m;
+    return FSI_OK;
+}
+
+// ||v||^2 into scal[slot] (device)
+fsi_status norm2(Context &cx, Problem &pb, const double *v, int64_t n, int slot) {
+    FSI_TRY(launch_mdot(v, n, 1, v, n, pb.partials.as<double>(), NRED, cx.stream));
+    return launch_reduce_partials(pb.partials.as<double>(), NRED, 1, pb.scal.as<double>() + slot, 0, cx.stream);
+}
+
+fsi_status read_scal(Context &cx, Problem &pb, int count) {
+    FSI_CUDA(cudaMemcpyAsync(cx.h_pinned, pb.scal.p, (size_t)count * 8, cudaMemcpyDeviceToHost, cx.stream));
+    FSI_CUDA(cudaStreamSynchronize(cx.stream));
+    return FSI_OK;
+}
+
+// --------------------------------------------------------------- FGMRES
+// Right-preconditioned FGMRES(m) with CGS2 Arnoldi and Givens rotations;
+// converged when the float64 true residual ||b - A x|| <= rtol ||b||.
+template <class T>
+fsi_status fgmres(Context &cx, Problem &pb, const double *b, double *x, const fsi_solve_opts &o,
+                  fsi_solve_stats &st, bool tr) {
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    const int m = o.restart;
+    const int L = (int)pb.dev.size();
+    FSI_TRY(ensure_workspace(cx, pb, m));
+    const DevCSR &A = tr ? F.AT : F.A;
+    double *V = pb.V.as<double>(), *H = pb.H.as<double>(), *g = pb.g.as<double>();
+    double *w = pb.w.as<double>(), *r = pb.rvec.as<double>(), *scal = pb.scal.as<double>();
+    double *Z = pb.Z.as<double>();
+    const double *hs = reinterpret_cast<const double *>(cx.h_pinned);
+    DevBuf &h1 = pb.h1, &h2 = pb.h2;
+    st = fsi_solve_stats();
+    st.status = FSI_OK;
+    // ||b||
+    FSI_TRY(norm2(cx, pb, b, n, 5));
+    FSI_TRY(read_scal(cx, pb, 6));
+    const double bnorm = std::sqrt(hs[5]);
+    if (!std::isfinite(bnorm)) {
+        st.status = FSI_ERR_NONFINITE;
+        set_error("right-hand side has a non-finite norm");
+        return FSI_ERR_NONFINITE;
+    }
+    if (bnorm == 0.0) {
+        FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, s));
+        FSI_CUDA(cudaStreamSynchronize(s));
+        st.converged = 1;
+        return FSI_OK;
+    }
+    if (!o.use_x0) FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, s));
+    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s));
+    FSI_TRY(norm2(cx, pb, r, n, 6));
+    FSI_TRY(read_scal(cx, pb, 7));
+    double beta = std::sqrt(hs[6]);
+    st.r0 = beta;
+    int its = 0;
+    fsi_status status = FSI_OK;
+    T *bfine = nullptr;
+    while (beta > o.rtol * bnorm && its < o.max_iters && std::isfinite(beta)) {
+        FSI_TRY(launch_init_basis(r, V, g, m, scal + 6, n, s));
+        int k = 0;
+        bool stop_all = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (size_t)j * n;
+            double *zj = Z + (size_t)j * n;
+            // z_j = M^{-1} v_j (the cycle runs in T; z_j is kept in float64)
+            if (std::is_same<T, double>::value) {
+                FSI_TRY(vcycle<T>(cx, pb, L - 1, reinterpret_cast<const T *>(vj), reinterpret_cast<T *>(zj), tr));
+            } else {
+                bfine = F.b.as<T>();
+                FSI_TRY(launch_cast_f64_f32(vj, reinterpret_cast<float *>(bfine), n, s));
+                FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
+                FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
+            }
+            // w = A z_j (float64 operator and vector)
+            FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w,
+                                                        SPMV_SET, s));
+            // CGS2
+            const int nv = j + 1;
+            FSI_TRY(launch_mdot(V, n, nv, w, n, pb.partials.as<double>(), NRED, s));
+            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h1.as<double>(), 0, s));
+            FSI_TRY(launch_update_dot(w, V, n, nv, h1.as<double>(), n, pb.partials.as<double>(), NRED, 0, s));
+            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h2.as<double>(), 0, s));
+            FSI_TRY(launch_update_dot(w, V, n, nv, h2.as<double>(), n, pb.partials.as<double>(), NRED, 1, s));
+            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, 1, scal + 7, 0, s));
+            FSI_TRY(launch_givens(H, m + 1, j, h1.as<double>(), h2.as<double>(), scal + 7, pb.cs.as<double>(),
+                                  pb.sn.as<double>(), g, scal, s));
+            FSI_TRY(read_scal(cx, pb, 5));
+            ++its;
+            k = j + 1;
+            const double est = hs[0], hn = hs[1], wn = hs[2];
+            if (hs[4] != 0.0) {
+                status = FSI_ERR_NONFINITE;
+                set_error("non-finite value in the Arnoldi process");
+                stop_all = true;
+                break;
+            }
+            if (est <= o.rtol * bnorm || hn <= 1e-14 * wn || its >= o.max_iters) break;
+            FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
+        }
+        if (stop_all) break;
+        FSI_TRY(launch_backsolve(H, m + 1, k, g, pb.y.as<double>(), s));
+        FSI_TRY(launch_combine<double>(x, Z, n, k, pb.y.as<double>(), n, s));
+        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s));
+        FSI_TRY(norm2(cx, pb, r, n, 6));
+        FSI_TRY(read_scal(cx, pb, 7));
+        beta = std::sqrt(hs[6]);
+        st.cycles++;
+    }
+    st.iterations = its;
+    st.rN = beta;
+    st.rel_residual = beta / bnorm;
+    st.converged = beta <= o.rtol * bnorm;
+    st.rho = (its > 0 && st.r0 > 0) ? std::pow(beta / st.r0, 1.0 / its) : 0.0;
+    if (status == FSI_OK && !std::isfinite(beta)) {
+        status = FSI_ERR_NONFINITE;
+        set_error("non-finite residual");
+    }
+    if (status == FSI_OK && !st.converged) {
+        status = FSI_ERR_NOT_CONVERGED;
+        set_error("FGMRES did not reach rtol within max_iters");
+    }
+    st.status = status;
+    return status;
+}
+
+fsi_status check_opts(const fsi_solve_opts *o) {
+    if (!o) { set_error("opts is NULL"); return FSI_ERR_ARG; }
+    if (!(o->rtol > 0.0) || o->restart < 1 || o->restart > 64 || o->max_iters < 1) {
+        set_error("solve options out of range (rtol > 0, 1 <= restart <= 64, max_iters >= 1)");
+        return FSI_ERR_ARG;
+    }
+    return FSI_OK;
+}
+
+fsi_status build_transposes(Context &cx, Problem &pb) {
+    if (pb.transposes_ready) return FSI_OK;
+    cudaStream_t s = cx.stream;
+    for (size_t l = 0; l < pb.dev.size(); ++l) {
+        LevelDev &L = pb.dev[l];
+        HostCSR A, AT;
+        FSI_TRY(download_csr(L.A, A, s));
+        transpose_csr(A, AT);
+        FSI_TRY(upload_csr(L.AT, AT, s));
+        if (l >= 1) {
+            HostCSR PT, RT;
+            transpose_csr(pb.hP[l], PT);
+            transpose_csr(pb.hR[l], RT);
+            FSI_TRY(upload_csr(L.PT, PT, s));
+            FSI_TRY(upload_csr(L.RT, RT, s));
+        }
+        if (cx.precision == FSI_MIXED) {
+            FSI_TRY(make_f32(L.AT, s));
+            if (l >= 1) {
+                FSI_TRY(make_f32(L.PT, s));
+                FSI_TRY(make_f32(L.RT, s));
+            }
+        }
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    pb.transposes_ready = true;
+    return FSI_OK;
+}
+
+fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
+    cudaStream_t s = cx.stream;
+    ProblemDesc &d = pb.desc;
+    d.dim = in.dim;
+    d.n_fine = in.n_fine;
+    d.n_levels = in.n_levels;
+    d.bc_preset = in.bc_preset;
+    d.mu_s = in.mu_s; d.lambda_s = in.lambda_s; d.rho_s = in.rho_s;
+    d.rho_f = in.rho_f; d.mu_f = in.mu_f; d.dt = in.dt;
+    if (!in.material || !in.advection) { set_error("material/advection is NULL"); return FSI_ERR_ARG; }
+    if (in.dim != 2 && in.dim != 3) { set_error("dim must be 2 or 3"); return FSI_ERR_ARG; }
+    if (in.n_fine < 1 || in.n_fine > 4096) { set_error("n_fine out of range"); return FSI_ERR_ARG; }
+    if (!(in.dt > 0) || !(in.lambda_s > 0) || !(in.mu_s > 0) || !(in.mu_f > 0)) {
+        set_error("coefficients must be positive");
+        return FSI_ERR_ARG;
+    }
+    int64_t nel = 1, nq2 = 1;
+    for (int k = 0; k < in.dim; ++k) { nel *= in.n_fine; nq2 *= 2 * (int64_t)in.n_fine + 1; }
+    d.material.assign(in.material, in.material + nel);
+    d.advection.assign(in.advection, in.advection + (size_t)in.dim * nq2);
+    std::string err = build_levels(d, pb.host);
+    if (!err.empty()) { set_error(err); return FSI_ERR_ARG; }
+    const int L = d.n_levels;
+    pb.dev.resize(L);
+    pb.hP.resize(L);
+    pb.hR.resize(L);
+    if (cx.host_only) {
+        for (int l = 1; l < L; ++l) {
+            build_prolongation(pb.host[l], pb.host[l - 1], pb.hP[l]);
+            build_restriction(pb.hP[l], pb.host[l], pb.host[l - 1], cx.restriction == 1, pb.hR[l]);
+        }
+        for (int l = 0; l < L; ++l) {
+            pb.dev[l].n = pb.host[l].n_dofs;
+            pb.dev[l].A.nnz = pb.host[l].pattern.nnz();
+            if (l >= 1 && cx.patch >= 1) {
+                LevelDev &D = pb.dev[l];
+                build_blocks(pb.host[l], cx.patch, D.h_blk_ptr, D.h_blk_idx);
+                D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
+                D.max_block = 0;
+                for (int64_t j = 0; j < D.n_blocks; ++j)
+                    D.max_block = std::max(D.max_block, D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
+            }
+        }
+        return FSI_OK;
+    }
+    RefTables ref = make_ref_tables(d.dim);
+    for (int l = 0; l < L; ++l) {
+        LevelHost &H = pb.host[l];
+        LevelDev &D = pb.dev[l];
+        D.n = H.n_dofs;
+        FSI_TRY(upload_csr(D.A, H.pattern, s));
+        FSI_TRY(D.A.val64.alloc((size_t)D.A.nnz * 8));
+        FSI_TRY(launch_assemble(H, d, ref, D.A, false, D.A.val64.as<double>(), s));
+        FSI_TRY(upload(D.fixed, H.fixed.data(), H.fixed.size(), s));
+        if (l >= 1) {
+            build_prolongation(H, pb.host[l - 1], pb.hP[l]);
+            build_restriction(pb.hP[l], H, pb.host[l - 1], cx.restriction == 1, pb.hR[l]);
+            FSI_TRY(upload_csr(D.P, pb.hP[l], s));
+            FSI_TRY(upload_csr(D.R, pb.hR[l], s));
+        }
+    }
+    // dA/dmu_s on the fine pattern (adjoint gradient)
+    {
+        LevelDev &F = pb.dev.back();
+        FSI_TRY(pb.dA_mu.alloc((size_t)F.A.nnz * 8));
+        FSI_TRY(launch_assemble(pb.host.back(), d, ref, F.A, true, pb.dA_mu.as<double>(), s));
+    }
+    // coarse direct solve: float64 inverse of A_0 (Gauss-Jordan, partial pivoting)
+    pb.n0 = pb.dev[0].n;
+    FSI_TRY(pb.coarse_inv.alloc((size_t)pb.n0 * pb.n0 * 8));
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    FSI_TRY(coarse_invert(pb.dev[0].A, pb.n0, pb.coarse_inv.as<double>(), cx.flags.as<int>(), s));
+    int flag = 0;
+    FSI_TRY(read_flag(cx, &flag));
+    if (flag) {
+        set_error("coarse-level operator is singular");
+        return FSI_ERR_ZERO_PIVOT;
+    }
+    return FSI_OK;
+}
+
+fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
+    cudaStream_t s = cx.stream;
+    const bool mixed = cx.precision == FSI_MIXED;
+    const size_t tsz = mixed ? 4 : 8;
+    const int VW = mixed ? 4 : 2;
+    for (size_t l = 0; l < pb.dev.size(); ++l) {
+        LevelDev &D = pb.dev[l];
+        LevelHost &H = pb.host[l];
+        if (mixed) {
+            FSI_TRY(make_f32(D.A, s));
+            if (l >= 1) {
+                FSI_TRY(make_f32(D.P, s));
+                FSI_TRY(make_f32(D.R, s));
+            }
+        }
+        FSI_TRY(D.b.alloc((size_t)D.n * tsz));
+        FSI_TRY(D.x.alloc((size_t)D.n * tsz));
+        FSI_TRY(D.r.alloc((size_t)D.n * tsz));
+        if (l == 0) continue;
+        build_blocks(H, cx.patch, D.h_blk_ptr, D.h_blk_idx);
+        D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
+        std::vector<int32_t> bp(D.h_blk_ptr.begin(), D.h_blk_ptr.end());
+        std::vector<int64_t> off(D.n_blocks + 1, 0);
+        std::vector<double> mult(D.n, 0.0);
+        D.max_block = 0;
+        for (int64_t j = 0; j < D.n_blocks; ++j) {
+            const int64_t nj = D.h_blk_ptr[j + 1] - D.h_blk_ptr[j];
+            D.max_block = std::max(D.max_block, nj);
+            const int64_t ld = (nj + VW - 1) / VW * VW;
+            off[j + 1] = off[j] + nj * ld;
+            for (int64_t k = D.h_blk_ptr[j]; k < D.h_blk_ptr[j + 1]; ++k) mult[D.h_blk_idx[k]] += 1.0;
+        }
+        D.inv_elems = off[D.n_blocks];
+        // partition-of-unity weights W_j = 1 / multiplicity
+        std::vector<double> w64(D.h_blk_idx.size());
+        std::vector<float> w32(D.h_blk_idx.size());
+        for (size_t k = 0; k < D.h_blk_idx.size(); ++k) {
+            w64[k] = 1.0 / mult[D.h_blk_idx[k]];
+            w32[k] = (float)w64[k];
+        }
+        FSI_TRY(upload(D.blk_ptr, bp.data(), bp.size() * 4, s));
+        FSI_TRY(upload(D.blk_idx, D.h_blk_idx.data(), D.h_blk_idx.size() * 4, s));
+        FSI_TRY(upload(D.blk_off, off.data(), off.size() * 8, s));
+        if (mixed) FSI_TRY(upload(D.blk_w, w32.data(), w32.size() * 4, s));
+        else FSI_TRY(upload(D.blk_w, w64.data(), w64.size() * 8, s));
+        FSI_TRY(D.inv.alloc((size_t)D.inv_elems * tsz));
+        // Jacobi rows: u^s (lumped K_u^s, Sec. 3.2) and fixed dofs
+        std::vector<int32_t> jac;
+        for (int64_t i = 0; i < D.n; ++i)
+            if (H.fixed[i] || (i >= H.off[3] && i < H.off[4])) jac.push_back((int32_t)i);
+        D.n_jac = (int64_t)jac.size();
+        FSI_TRY(upload(D.jac_idx, jac.data(), jac.size() * 4, s));
+        FSI_TRY(D.jac_inv.alloc((size_t)std::max<int64_t>(D.n_jac, 1) * tsz));
+        FSI_TRY(launch_jacobi_setup(D.A, D.jac_idx.as<int32_t>(), D.n_jac,
+                                    mixed ? nullptr : D.jac_inv.as<double>(),
+                                    mixed ? D.jac_inv.as<float>() : nullptr, s));
+        // apply work items: whole blocks when there are enough of them to fill
+        // the GPU, otherwise row chunks (multiples of 16 rows)
+        {
+            const int64_t want = 4 * (int64_t)cx.num_sms;
+            const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
+            std::vector<int32_t> it;
+            for (int64_t j = 0; j < D.n_blocks; ++j) {
+                const int nj = (int)(D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
+                int chunk = (int)((nj + split - 1) / split);
+                chunk = std::max(16, (chunk + 15) / 16 * 16);
+                for (int r0 = 0; r0 < nj; r0 += chunk) {
+                    it.push_back((int32_t)j);
+                    it.push_back(r0);
+                    it.push_back(std::min(nj, r0 + chunk));
+                    it.push_back(0);
+                }
+            }
+            // Jacobi rows ride in the same launch: items (-1, k0, k1) over the jac list
+            for (int64_t k0 = 0; k0 < D.n_jac; k0 += 2048) {
+                it.push_back(-1);
+                it.push_back((int32_t)k0);
+                it.push_back((int32_t)std::min<int64_t>(D.n_jac, k0 + 2048));
+                it.push_back(0);
+            }
+            D.n_items = (int64_t)it.size() / 4;
+            FSI_TRY(upload(D.items, it.data(), it.size() * 4, s));
+        }
+        FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+        FSI_TRY(launch_block_invert(D.A, D, cx.precision, cx.flags.as<int>(), s, cx.num_sms));
+        int flag = 0;
+        FSI_TRY(read_flag(cx, &flag));
+        if (flag) {
+            set_error("a Schwarz block on level " + std::to_string(l) + " is singular");
+            return FSI_ERR_ZERO_PIVOT;
+        }
+    }
+    pb.transposes_ready = false;
+    pb.m_alloc = 0;
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status apply_smoother_t(Context &cx, LevelDev &L, const double *r, double *y, int tr) {
+    cudaStream_t s = cx.stream;
+    DevBuf rt, yt;
+    FSI_TRY(rt.alloc((size_t)L.n * sizeof(T)));
+    FSI_TRY(yt.alloc((size_t)L.n * sizeof(T)));
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f64_f32(r, rt.as<float>(), L.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(rt.p, r, (size_t)L.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaMemsetAsync(yt.p, 0, (size_t)L.n * sizeof(T), s));
+    const double om = cx.omega;
+    cx.omega = 1.0;   // plain P2^{-1} r
+    fsi_status st = smooth_apply<T>(cx, L, rt.as<T>(), yt.as<T>(), tr != 0);
+    cx.omega = om;
+    FSI_TRY(st);
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f32_f64(yt.as<float>(), y, L.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(y, yt.p, (size_t)L.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status apply_vcycle_t(Context &cx, Problem &pb, const double *v, double *z, int tr) {
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    DevBuf bt, xt;
+    FSI_TRY(bt.alloc((size_t)F.n * sizeof(T)));
+    FSI_TRY(xt.alloc((size_t)F.n * sizeof(T)));
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f64_f32(v, bt.as<float>(), F.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(bt.p, v, (size_t)F.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_TRY(vcycle<T>(cx, pb, (int)pb.dev.size() - 1, bt.as<T>(), xt.as<T>(), tr != 0));
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f32_f64(xt.as<float>(), z, F.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(z, xt.p, (size_t)F.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+
+Problem *get_prob(const fsi_ctx *ctx, int prob, int level) {
+    const Context *cx = reinterpret_cast<const Context *>(ctx);
+    if (!cx || prob < 0 || prob >= (int)cx->probs.size()) return nullptr;
+    Problem *pb = const_cast<Problem *>(&cx->probs[prob]);
+    if (level < 0 || level >= (int)pb->dev.size()) return nullptr;
+    return pb;
+}
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+const char *fsi_last_error(void) { return g_last_error.c_str(); }
+
+fsi_status fsi_setup_hierarchy(const fsi_problem *probs, int n_probs, const fsi_hier_opts *opts,
+                               void *cuda_stream, fsi_ctx **out) {
+    g_last_error.clear();
+    if (!probs || n_probs < 1 || !out) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    *out = nullptr;
+    std::unique_ptr<Context> cx(new Context());
+    FSI_CUDA(cudaGetDevice(&cx->device));
+    cx->stream = static_cast<cudaStream_t>(cuda_stream);
+    cx->restriction = opts ? opts->restriction : 0;
+    if (cx->restriction != 0 && cx->restriction != 1) { set_error("restriction must be 0 or 1"); return FSI_ERR_ARG; }
+    FSI_CUDA(cudaDeviceGetAttribute(&cx->num_sms, cudaDevAttrMultiProcessorCount, cx->device));
+    FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&cx->h_pinned), 64 * 8));
+    FSI_TRY(cx->flags.alloc(16));
+    cx->probs.resize(n_probs);
+    for (int i = 0; i < n_probs; ++i) {
+        fsi_status st = setup_problem(*cx, cx->probs[i], probs[i]);
+        if (st != FSI_OK) {
+            cudaFreeHost(cx->h_pinned);
+            cx->h_pinned = nullptr;
+            return st;
+        }
+    }
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    *out = reinterpret_cast<fsi_ctx *>(cx.release());
+    return FSI_OK;
+}
+
+fsi_status fsi_setup_host_only(const fsi_problem *prob, const fsi_hier_opts *opts, int patch, fsi_ctx **out) {
+    g_last_error.clear();
+    if (!prob || !out || patch < 0 || patch > 16) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    *out = nullptr;
+    std::unique_ptr<Context> cx(new Context());
+    cx->host_only = true;
+    cx->patch = patch;
+    cx->restriction = opts ? opts->restriction : 0;
+    if (cx->restriction != 0 && cx->restriction != 1) { set_error("restriction must be 0 or 1"); return FSI_ERR_ARG; }
+    cx->probs.resize(1);
+    FSI_TRY(setup_problem(*cx, cx->probs[0], *prob));
+    *out = reinterpret_cast<fsi_ctx *>(cx.release());
+    return FSI_OK;
+}
+
+fsi_status fsi_get_pattern(const fsi_ctx *ctx, int prob, int level, int64_t *row_ptr, int32_t *col) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || !row_ptr || !col) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const HostCSR &P = pb->host[level].pattern;
+    std::memcpy(row_ptr, P.ptr.data(), P.ptr.size() * 8);
+    std::memcpy(col, P.col.data(), P.col.size() * 4);
+    return FSI_OK;
+}
+
+fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !opts) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if ((opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) || opts->patch < 1 || opts->patch > 16 ||
+        !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8) {
+        set_error("smoother options out of range");
+        return FSI_ERR_ARG;
+    }
+    DeviceGuard guard(cx->device);
+    cx->precision = opts->precision;
+    cx->patch = opts->patch;
+    cx->omega = opts->omega;
+    cx->nu_pre = opts->nu_pre;
+    cx->nu_post = opts->nu_post;
+    cx->smoothers_ready = false;
+    for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    cx->smoothers_ready = true;
+    return FSI_OK;
+}
+
+static fsi_status solve_one(Context &cx, Problem &pb, const double *b, double *x, const fsi_solve_opts *o,
+                            fsi_solve_stats *st, bool tr) {
+    auto t0 = std::chrono::steady_clock::now();
+    fsi_solve_stats local;
+    fsi_status s = (cx.precision == FSI_MIXED) ? fgmres<float>(cx, pb, b, x, *o, local, tr)
+                                               : fgmres<double>(cx, pb, b, x, *o, local, tr);
+    auto t1 = std::chrono::steady_clock::now();
+    local.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (!cx.ev_marks.empty()) {
+        cudaStreamSynchronize(cx.stream);
+        collect_marks(cx);
+    }
+    if (s != FSI_OK) local.status = s;
+    if (st) *st = local;
+    return s;
+}
+
+fsi_status fsi_solve(fsi_ctx *ctx, const double *b, double *x, const fsi_solve_opts *opts, fsi_solve_stats *st) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !b || !x) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    FSI_TRY(check_opts(opts));
+    if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    return solve_one(*cx, cx->probs[0], b, x, opts, st, false);
+}
+
+fsi_status fsi_solve_batched(fsi_ctx *ctx, const double *const *b, double *const *x, const fsi_solve_opts *opts,
+                             fsi_solve_stats *st) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !b || !x) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    FSI_TRY(check_opts(opts));
+    if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    fsi_status worst = FSI_OK;
+    for (size_t i = 0; i < cx->probs.size(); ++i) {
+        if (!b[i] || !x[i]) { set_error("NULL vector in batch"); return FSI_ERR_ARG; }
+        fsi_status s = solve_one(*cx, cx->probs[i], b[i], x[i], opts, st ? &st[i] : nullptr, false);
+        if (s == FSI_ERR_CUDA || s == FSI_ERR_ALLOC || s == FSI_ERR_ARG) return s;
+        if (s != FSI_OK && worst == FSI_OK) worst = s;
+    }
+    return worst;
+}
+
+fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *lambda, double *dA_vals,
+                       double *dmu_s, const fsi_solve_opts *opts, fsi_solve_stats *st) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !w || !x || !lambda) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    FSI_TRY(check_opts(opts));
+    if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    Problem &pb = cx->probs[0];
+    FSI_TRY(build_transposes(*cx, pb));
+    fsi_status s = solve_one(*cx, pb, w, lambda, opts, st, true);
+    if (s != FSI_OK && s != FSI_ERR_NOT_CONVERGED) return s;
+    LevelDev &F = pb.dev.back();
+    if (dA_vals) FSI_TRY(launch_pattern_grad(F.A, lambda, x, dA_vals, cx->stream));
+    if (dmu_s) {
+        // -lambda^T (dA/dmu_s) x
+        FSI_TRY(launch_spmv<double, double, double>(F.A, pb.dA_mu.as<double>(), x, (const double *)nullptr,
+                                                    pb.w.as<double>(), SPMV_SET, cx->stream));
+        FSI_TRY(launch_mdot(lambda, F.n, 1, pb.w.as<double>(), F.n, pb.partials.as<double>(), NRED, cx->stream));
+        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, 1, pb.scal.as<double>() + 8, 0, cx->stream));
+        FSI_CUDA(cudaMemcpyAsync(cx->h_pinned, pb.scal.as<double>() + 8, 8, cudaMemcpyDeviceToHost, cx->stream));
+        FSI_CUDA(cudaStreamSynchronize(cx->stream));
+        *dmu_s = -reinterpret_cast<const double *>(cx->h_pinned)[0];
+    }
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    return s;
+}
+
+fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !out || mode < 0 || mode > 2) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (mode == 1) {
+        cx->prof_ms[0] = cx->prof_ms[1] = 0;
+        cx->prof_n[0] = cx->prof_n[1] = 0;
+        cx->launch_base = launches_so_far();
+        cx->profile = true;
+    } else if (mode == 0) {
+        cx->profile = false;
+    }
+    // algorithmic bytes of one fine-level smoother apply and residual SpMV
+    const Problem &pb = cx->probs[0];
+    const LevelDev &F = pb.dev.back();
+    const double ts = cx->precision == FSI_MIXED ? 4.0 : 8.0;
+    double blk = 0.0;
+    for (int64_t j = 0; j + 1 < (int64_t)F.h_blk_ptr.size(); ++j) {
+        const double nj = (double)(F.h_blk_ptr[j + 1] - F.h_blk_ptr[j]);
+        blk += nj * nj * ts + nj * (4.0 + ts + ts + 2.0 * ts);   // inverse, idx, weight, gather r, x RMW
+    }
+    blk += (double)F.n_jac * (4.0 + ts + ts + 2.0 * ts);
+    const double spmv = (double)F.A.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)F.n * 3.0 * ts;
+    out[0] = (double)cx->prof_n[0];
+    out[1] = cx->prof_ms[0];
+    out[2] = blk;
+    out[3] = (double)cx->prof_n[1];
+    out[4] = cx->prof_ms[1];
+    out[5] = spmv;
+    out[6] = (double)(launches_so_far() - cx->launch_base);
+    out[7] = 0.0;
+    return FSI_OK;
+}
+
+fsi_status fsi_get_sizes(const fsi_ctx *ctx, int prob, int level, int64_t *out) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || !out) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const LevelDev &D = pb->dev[level];
+    const LevelHost &H = pb->host[level];
+    out[0] = H.n_dofs;
+    out[1] = D.A.nnz;
+    out[2] = D.n_blocks;
+    out[3] = D.max_block;
+    for (int g = 0; g < 7; ++g) out[4 + g] = H.off[g];
+    return FSI_OK;
+}
+
+fsi_status fsi_get_dof_map(const fsi_ctx *ctx, int prob, int level, int32_t *field, int32_t *comp, int32_t *node) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || !field || !comp || !node) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const LevelHost &H = pb->host[level];
+    std::memcpy(field, H.dof_field.data(), H.n_dofs * 4);
+    std::memcpy(comp, H.dof_comp.data(), H.n_dofs * 4);
+    std::memcpy(node, H.dof_node.data(), H.n_dofs * 4);
+    return FSI_OK;
+}
+
+fsi_status fsi_get_matrix(const fsi_ctx *ctx, int prob, int level, int64_t *row_ptr, int32_t *col, double *val) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || !row_ptr || !col || !val) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const Context *cx = reinterpret_cast<const Context *>(ctx);
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    HostCSR H;
+    FSI_TRY(download_csr(pb->dev[level].A, H, cx->stream));
+    std::memcpy(row_ptr, H.ptr.data(), H.ptr.size() * 8);
+    std::memcpy(col, H.col.data(), H.col.size() * 4);
+    std::memcpy(val, H.val.data(), H.val.size() * 8);
+    return FSI_OK;
+}
+
+fsi_status fsi_get_transfer(const fsi_ctx *ctx, int prob, int level, int which, int64_t *row_ptr, int32_t *col,
+                            double *val) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || level < 1 || !row_ptr || (which != 0 && which != 1)) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const HostCSR &H = which == 0 ? pb->hP[level] : pb->hR[level];
+    std::memcpy(row_ptr, H.ptr.data(), H.ptr.size() * 8);
+    if (col) std::memcpy(col, H.col.data(), H.col.size() * 4);
+    if (val) std::memcpy(val, H.val.data(), H.val.size() * 8);
+    return FSI_OK;
+}
+
+fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_ptr, int32_t *idx) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || level < 1 || !blk_ptr) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const LevelDev &D = pb->dev[level];
+    if (D.h_blk_ptr.empty()) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    std::memcpy(blk_ptr, D.h_blk_ptr.data(), D.h_blk_ptr.size() * 8);
+    if (idx) std::memcpy(idx, D.h_blk_idx.data(), D.h_blk_idx.size() * 4);
+    return FSI_OK;
+}
+
+fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x, double *y) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || !x || !y) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    const DevCSR &A = pb->dev[level].A;
+    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, (const double *)nullptr, y, SPMV_SET,
+                                                cx->stream));
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    return FSI_OK;
+}
+
+fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y, int transpose) {
+    Problem *pb = get_prob(ctx, prob, level);
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!pb || level < 1 || !r || !y) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    LevelDev &L = pb->dev[level];
+    return cx->precision == FSI_MIXED ? apply_smoother_t<float>(*cx, L, r, y, transpose)
+                                      : apply_smoother_t<double>(*cx, L, r, y, transpose);
+}
+
+fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, int transpose) {
+    Problem *pb = get_prob(ctx, prob, 0);
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!pb || !v || !z) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx->device);
+    if (transpose) FSI_TRY(build_transposes(*cx, *pb));
+    return cx->precision == FSI_MIXED ? apply_vcycle_t<float>(*cx, *pb, v, z, transpose)
+                                      : apply_vcycle_t<double>(*cx, *pb, v, z, transpose);
+}
+
+void fsi_destroy(fsi_ctx *ctx) {
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx) return;
+    if (cx->host_only) {
+        delete cx;
+        return;
+    }
+    {
+        DeviceGuard guard(cx->device);
+        cudaStreamSynchronize(cx->stream);
+        if (cx->h_pinned) cudaFreeHost(cx->h_pinned);
+        cx->h_pinned = nullptr;
+        collect_marks(*cx);
+        for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
+        cx->ev_pool.clear();
+        cx->probs.clear();
+        cx->flags.release();
+    }
+    delete cx;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Device-side data of a solver context and the internal kernel interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fsi.h"
+#include "host_setup.h"
+
+namespace fsi {
+
+// Last-error message (thread local) and CUDA checks that turn into statuses.
+void set_error(const std::string &msg);
+#define FSI_CUDA(...)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (__VA_ARGS__);                                                \
+        if (e_ != cudaSuccess) {                                                       \
+            ::fsi::set_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+            return FSI_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+#define FSI_TRY(...)                       \
+    do {                                   \
+        fsi_status s_ = (__VA_ARGS__);     \
+        if (s_ != FSI_OK) return s_;       \
+    } while (0)
+
+// Owned device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    fsi_status alloc(size_t nbytes) {
+        release();
+        if (nbytes == 0) nbytes = 16;
+        if (cudaMalloc(&p, nbytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of " + std::to_string(nbytes) + " bytes failed");
+            p = nullptr;
+            return FSI_ERR_ALLOC;
+        }
+        bytes = nbytes;
+        return FSI_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// CSR on the device: int32 row pointers and columns, float64 values and
+// (mixed precision) a float32 copy.
+struct DevCSR {
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    DevBuf ptr, col, val64, val32;
+    int group = 8;        // threads per row in the SpMV kernel
+};
+
+struct LevelDev {
+    int64_t n = 0;
+    DevCSR A, AT;         // operator and (adjoint) its transpose
+    DevCSR P, R;          // l >= 1: P_l (n_l x n_{l-1}), R_l (n_{l-1} x n_l)
+    DevCSR PT, RT;        // adjoint: P^T (restriction), R^T (prolongation)
+    DevBuf fixed;         // uint8 per dof
+    // Schwarz blocks (l >= 1)
+    int64_t n_blocks = 0, max_block = 0, inv_elems = 0;
+    std::vector<int64_t> h_blk_ptr;
+    std::vector<int32_t> h_blk_idx;
+    DevBuf blk_ptr, blk_idx, blk_off, blk_w;   // int32, int32, int64, working-precision weights
+    DevBuf inv;                                 // block inverses, row-major, padded rows
+    int64_t n_items = 0;
+    DevBuf items;                               // int4 (block, row begin, row end, 0) apply work items
+    int64_t n_jac = 0;
+    DevBuf jac_idx, jac_inv;                    // int32, working precision 1/diag
+    // V-cycle vectors in working precision
+    DevBuf b, x, r;
+};
+
+struct Problem {
+    ProblemDesc desc;
+    std::vector<LevelHost> host;
+    std::vector<LevelDev> dev;       // index = level
+    std::vector<HostCSR> hP, hR;     // host transfers (for accessors)
+    int64_t n0 = 0;                  // coarse size
+    DevBuf coarse_inv;               // n0 x n0 float64 inverse of A_0 (row-major)
+    DevBuf coarse_b, coarse_x;       // float64 coarse vectors
+    DevBuf dA_mu;                    // float64 values of dA/dmu_s on the fine pattern
+    bool transposes_ready = false;
+    // Krylov workspace (fine level)
+    int m_alloc = 0;
+    DevBuf V, Z, H, g, cs, sn, y, w, rvec, xwork, partials, scal, h1, h2;
+};
+
+// kernels launched by the library (all contexts), for launch accounting
+void count_launch(int n = 1);
+int64_t launches_so_far();
+
+struct Context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int restriction = 0;
+    int precision = FSI_FP64;
+    int patch = 1;
+    double omega = 1.0;
+    int nu_pre = 1, nu_post = 1;
+    bool smoothers_ready = false;
+    bool host_only = false;          // inspection context without device state
+    std::vector<Problem> probs;
+    DevBuf flags;                    // int32[4]: zero pivot, nonfinite, ...
+    int num_sms = 152;
+    int64_t *h_pinned = nullptr;     // pinned host scratch for scalars
+    // profiling of fine-level launches (fsi_profile)
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;   // kind, start/stop
+    double prof_ms[2] = {0, 0};
+    int64_t prof_n[2] = {0, 0};
+    int64_t launch_base = 0;
+};
+
+// ---------------------------------------------------------------- kernels
+// (launch wrappers; all asynchronous on the given stream)
+fsi_status launch_assemble(const LevelHost &L, const ProblemDesc &p, const RefTables &ref,
+                           const DevCSR &A, bool mu_derivative, double *val_out, cudaStream_t s);
+fsi_status launch_cast_f64_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
+fsi_status launch_cast_f32_f64(const float *src, double *dst, int64_t n, cudaStream_t s);
+
+enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
+// y = A x | y = b - A x | y += A x ; matrix precision follows TA, vectors TX/TY
+template <class TA, class TX, class TY>
+fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
+                       cudaStream_t s);
+
+fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int precision, int *flags,
+                               cudaStream_t s, int num_sms);
+template <class T>
+fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, int transpose,
+                              cudaStream_t s);
+template <class T>
+fsi_status launch_jacobi_apply(const LevelDev &lev, const T *r, T *x, T omega, cudaStream_t s);
+
+fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s);
+template <class T>
+fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int transpose,
+                             cudaStream_t s);
+
+// Krylov helpers
+fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
+                       double *partials, int nblocks, cudaStream_t s);
+fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
+                             int64_t n, double *partials, int nblocks, int norm_only,
+                             cudaStream_t s);
+fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out,
+                                  int accumulate, cudaStream_t s);
+fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2,
+                         const double *hn2, double *cs, double *sn, double *g, double *scal,
+                         cudaStream_t s);
+fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
+                             cudaStream_t s);
+fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y,
+                            cudaStream_t s);
+template <class T>
+fsi_status launch_combine(double *x, const T *Z, int64_t ld, int k, const double *y, int64_t n,
+                          cudaStream_t s);
+fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2,
+                             int64_t n, cudaStream_t s);
+fsi_status launch_pattern_grad(const DevCSR &A, const double *lam, const double *x, double *out,
+                               cudaStream_t s);
+fsi_status launch_jacobi_setup(const DevCSR &A, const int32_t *idx, int64_t n, double *d64, float *d32,
+                               cudaStream_t s);
+fsi_status launch_set_fixed_diag(const DevCSR &A, const uint8_t *fixed, double *val, cudaStream_t s);
+
+}  // namespace fsi

@@ -1,0 +1,288 @@
+// Flexible GMRES kernels (outer Krylov solver, Sec. 3.2), all float64.
+//
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2) in three fused
+// streaming passes over the basis V (column-major, one vector per column):
+//   pass 1: partial dots V^T w                       (launch_mdot)
+//   pass 2: w -= V h1 and partial dots V^T w         (launch_update_dot)
+//   pass 3: w -= V h2 and partial ||w||^2            (launch_update_dot, norm_only)
+// Each pass writes one partial sum per CTA and vector; a one-CTA kernel adds
+// them in a fixed order (deterministic).  The Givens update of the Hessenberg
+// column and the residual estimate run in one thread on the device.
+#include "context.h"
+
+namespace fsi {
+
+namespace {
+
+constexpr int KMAX = 65;     // vectors in a pass: restart + 1 <= 65
+constexpr int KT = 256;      // threads per CTA
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double *out) {
+    __shared__ double red[KT / 32][NV];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i >= nv) break;
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < KT / 32; ++w) v += red[w][i];
+        out[i] = v;
+    }
+}
+
+// Rows are split into gridDim.x contiguous chunks; thread t of a CTA visits
+// rows chunk_start + t, + KT, ... so that every vector is read coalesced.
+template <int NV>
+__global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
+                                                  const double *__restrict__ w, int64_t n,
+                                                  double *__restrict__ partials) {
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+        const double wr = w[r];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) acc[i] += V[(size_t)i * ld + r] * wr;
+    }
+    block_reduce_store<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(KT) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                        int64_t ld, int nv, const double *__restrict__ h,
+                                                        int64_t n, double *__restrict__ partials, int norm_only) {
+    __shared__ double hs[KMAX];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    double nrm = 0.0;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+        double v[NV];
+        double wr = w[r];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) {
+                v[i] = V[(size_t)i * ld + r];
+                wr -= v[i] * hs[i];
+            }
+        w[r] = wr;
+        if (norm_only) {
+            nrm += wr * wr;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) acc[i] += v[i] * wr;
+        }
+    }
+    if (norm_only) {
+        acc[0] = nrm;
+        block_reduce_store<NV>(acc, 1, partials + (size_t)blockIdx.x * KMAX);
+    } else {
+        block_reduce_store<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+    }
+}
+
+// one warp per vector: lanes stride over the per-CTA partials in a fixed
+// order, then a fixed shuffle tree (deterministic)
+__global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int nv,
+                                       double *__restrict__ out, int accumulate) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    for (int i = warp; i < nv; i += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * KMAX + i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = accumulate ? out[i] + s : s;
+    }
+}
+
+// Column j of the Hessenberg matrix H (ld = restart + 1): h = h1 + h2 from
+// the two Gram-Schmidt passes, h_{j+1,j} = sqrt(hn2).  Applies the previous
+// rotations, forms rotation j, updates g.  scal[0] = |g_{j+1}| (estimate),
+// scal[1] = h_{j+1,j}, scal[2] = ||A z_j|| (= sqrt(|h|^2 + h_{j+1,j}^2)),
+// scal[3] = 1 on breakdown-free column, 0 if both entries of the rotation
+// vanish; scal[4] non-finite flag.
+__global__ void givens_kernel(double *H, int ld, int j, const double *h1, const double *h2,
+                              const double *hn2, double *cs, double *sn, double *g, double *scal) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double *col = H + (size_t)j * ld;
+    double ss = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        col[i] = h1[i] + h2[i];
+        ss += col[i] * col[i];
+    }
+    const double hn = sqrt(fmax(hn2[0], 0.0));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    double c = 1.0, s = 0.0;
+    if (den > 0.0) {
+        c = col[j] / den;
+        s = col[j + 1] / den;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    scal[0] = fabs(g[j + 1]);
+    scal[1] = hn;
+    scal[2] = sqrt(ss + hn * hn);
+    scal[3] = den > 0.0 ? 1.0 : 0.0;
+    scal[4] = (isfinite(scal[0]) && isfinite(hn) && isfinite(den)) ? 0.0 : 1.0;
+}
+
+__global__ void scale_copy_kernel(const double *__restrict__ w, double *__restrict__ v,
+                                  const double *__restrict__ scal, int idx, int64_t n) {
+    const double inv = 1.0 / scal[idx];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        v[r] = w[r] * inv;
+}
+
+// start of a cycle: beta = sqrt(nrm2), v0 = r / beta, g = (beta, 0, ...)
+__global__ void init_basis_kernel(const double *__restrict__ r, double *__restrict__ v0, double *__restrict__ g,
+                                  int m, const double *__restrict__ nrm2, int64_t n) {
+    const double beta = sqrt(nrm2[0]);
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v0[i] = r[i] * inv;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta : 0.0;
+}
+
+// y = H(1:k,1:k)^{-1} g(1:k), upper triangular
+__global__ void backsolve_kernel(const double *H, int ld, int k, const double *g, double *y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k; ++j) s -= H[(size_t)j * ld + i] * y[j];
+        y[i] = s / H[(size_t)i * ld + i];
+    }
+}
+
+template <class T>
+__global__ void combine_kernel(double *__restrict__ x, const T *__restrict__ Z, int64_t ld, int k,
+                               const double *__restrict__ y, int64_t n) {
+    __shared__ double ys[KMAX];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[r];
+        for (int i = 0; i < k; ++i) s += (double)Z[(size_t)i * ld + r] * ys[i];
+        x[r] = s;
+    }
+}
+
+inline int egrid(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+#define FSI_NV_SWITCH(nv, CALL)                          \
+    do {                                                 \
+        if ((nv) <= 1) { CALL(1); }                      \
+        else if ((nv) <= 2) { CALL(2); }                 \
+        else if ((nv) <= 4) { CALL(4); }                 \
+        else if ((nv) <= 8) { CALL(8); }                 \
+        else if ((nv) <= 16) { CALL(16); }               \
+        else if ((nv) <= 32) { CALL(32); }               \
+        else { CALL(KMAX); }                             \
+    } while (0)
+
+fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
+                       double *partials, int nblocks, cudaStream_t s) {
+    if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
+#define CALL_MDOT(NV) mdot_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials)
+    FSI_NV_SWITCH(nv, CALL_MDOT);
+#undef CALL_MDOT
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
+                             int64_t n, double *partials, int nblocks, int norm_only, cudaStream_t s) {
+    if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
+#define CALL_UPD(NV) update_dot_kernel<NV><<<nblocks, KT, 0, s>>>(w, V, ld, nv, h, n, partials, norm_only)
+    FSI_NV_SWITCH(nv, CALL_UPD);
+#undef CALL_UPD
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out, int accumulate,
+                                  cudaStream_t s) {
+    reduce_partials_kernel<<<1, 1024, 0, s>>>(partials, nblocks, nv, out, accumulate);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2, const double *hn2,
+                         double *cs, double *sn, double *g, double *scal, cudaStream_t s) {
+    givens_kernel<<<1, 32, 0, s>>>(H, ld, j, h1, h2, hn2, cs, sn, g, scal);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
+                             cudaStream_t s) {
+    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, scal, idx, n);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2, int64_t n,
+                             cudaStream_t s) {
+    init_basis_kernel<<<egrid(n), 256, 0, s>>>(r, v0, g, m, nrm2, n);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y, cudaStream_t s) {
+    backsolve_kernel<<<1, 32, 0, s>>>(H, ld, k, g, y);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status launch_combine(double *x, const T *Z, int64_t ld, int k, const double *y, int64_t n,
+                          cudaStream_t s) {
+    combine_kernel<T><<<egrid(n), 256, 0, s>>>(x, Z, ld, k, y, n);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+template fsi_status launch_combine<float>(double *, const float *, int64_t, int, const double *, int64_t,
+                                          cudaStream_t);
+template fsi_status launch_combine<double>(double *, const double *, int64_t, int, const double *, int64_t,
+                                           cudaStream_t);
+
+}  // namespace fsi
