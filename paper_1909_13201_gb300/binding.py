@@ -181,21 +181,26 @@ class FSISolver:
     def _opts(rtol, restart, max_iters, use_x0):
         return SolveOpts_t(rtol, restart, max_iters, 1 if use_x0 else 0)
 
-    def solve(self, b, x=None, rtol=1e-8, restart=30, max_iters=1000, check=True):
-        """Solve J2 x = b on problem 0.  b: CUDA float64 tensor (host tensors
-        are copied in and the result copied back)."""
+    def solve(self, b, x0=None, rtol=1e-8, restart=30, max_iters=1000, check=True, out=None):
+        """Solve J2 x = b on problem 0 and return (x, stats).
+
+        b: float64 tensor (CUDA; a host tensor is copied in and the result
+        copied back).  x0: optional initial guess.  out: optional CUDA tensor
+        that receives the solution (otherwise a new one is allocated)."""
         import torch
         host = not b.is_cuda
         bd = b.to("cuda", non_blocking=True) if host else b
-        use_x0 = x is not None
-        xd = (x.to("cuda") if (x is not None and not x.is_cuda) else x) if use_x0 else torch.empty_like(bd)
+        xd = out if out is not None else torch.empty_like(bd)
+        use_x0 = x0 is not None
+        if use_x0:
+            xd.copy_(x0)
         st = SolveStats_t()
         opts = self._opts(rtol, restart, max_iters, use_x0)
         s = load_library().fsi_solve(self.ctx, _dptr(bd), _dptr(xd), C.byref(opts), C.byref(st))
         if check:
             _check(s)
-        out = xd.to("cpu") if host else xd
-        return out, st.to_dict()
+        res = xd.to("cpu") if host else xd
+        return res, st.to_dict()
 
     def solve_batched(self, bs, xs=None, rtol=1e-8, restart=30, max_iters=1000, check=True):
         import torch
