@@ -8,8 +8,10 @@ x0 = 0 to a float64 true relative residual <= 1e-8 (V-cycle with FS-ASM
 smoothing, Arnoldi, refinement): every step of the solve path.  Set-up
 (hierarchy, assembly, block factorisation) is timed separately.
 
-  value      mixed precision (float32 cycle, float64 Krylov), device-resident
-             right-hand side, CUDA events on the solver's stream;
+  value      mixed precision (float32 cycle with float16 row-scaled block
+             inverses, float64 Krylov), device-resident right-hand side, CUDA
+             events on the solver's stream;
+  mixed_f32_inverses  the same with float32 block inverses;
   fp64       the all-float64 path on the same system (mixed/fp64 speed-up);
   e2e        mixed precision through the public call with host buffers
              (pinned H2D of b, solve, D2H of x inside the timed region);
@@ -43,7 +45,7 @@ RTOL = 1e-8
 # FGMRES iterations the oracle's algorithm needs on each seeded workload to
 # reach RTOL (oracle.fgmres.solve on the same right-hand side); used to
 # project the oracle's per-iteration time to the metric.
-ORACLE_ITERATIONS = {1: 40}
+ORACLE_ITERATIONS = {1: 40, 4: 31}
 
 
 def parse():
@@ -172,7 +174,7 @@ def measured_peaks():
 def ncu_traffic():
     """Per-launch DRAM bytes of the fine smoother apply from the committed ncu
     summary, valid only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "block_apply_c1_mixed.md")
+    path = os.path.join(ROOT, "profiles", "block_apply_h_c1_mixed_half.md")
     src = os.path.join(ROOT, "paper_1909_13201_gb300", "csrc", "kernels_block.cu")
     if not os.path.exists(path):
         return None
@@ -197,7 +199,7 @@ def run_ours(args, rank, world, local):
     import torch.distributed as dist
 
     from paper_1909_13201_gb300 import inputs as I
-    from paper_1909_13201_gb300.binding import FSI_FP64, FSI_MIXED, FSISolver
+    from paper_1909_13201_gb300.binding import FSI_FP64, FSI_MIXED, FSI_MIXED_HALF, FSISolver
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -245,9 +247,9 @@ def run_ours(args, rank, world, local):
         _, st = s.solve(b, rtol=RTOL, out=x)
         stats.update(st)
 
-    # ---- mixed precision (headline)
+    # ---- mixed precision with float16 block-inverse storage (headline)
     t0 = time.time()
-    s.setup_smoothers(precision=FSI_MIXED)
+    s.setup_smoothers(precision=FSI_MIXED_HALF)
     torch.cuda.synchronize()
     setup_mixed_s = time.time() - t0
     for _ in range(args.warmup):
@@ -283,6 +285,14 @@ def run_ours(args, rank, world, local):
 
     solve_e2e()
     ms_e2e = timed(max(2, args.steps // 2), solve_e2e)
+    # ---- mixed precision with float32 block inverses
+    t0 = time.time()
+    s.setup_smoothers(precision=FSI_MIXED)
+    torch.cuda.synchronize()
+    setup_f32_s = time.time() - t0
+    solve_dev()
+    ms32 = timed(max(2, args.steps // 2), solve_dev)
+    st32 = dict(stats)
     # ---- all-float64 path on the same system
     t0 = time.time()
     s.setup_smoothers(precision=FSI_FP64)
@@ -299,7 +309,8 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 cycle / f64 Krylov", "data": "synthetic (seeded, no dataset)",
+        "vs_baseline": None, "dtype": "f32 cycle (f16 row-scaled block inverses) / f64 Krylov",
+        "data": "synthetic (seeded, no dataset)",
         "config": {"workload": p.name, "fine_elements": f"{p.n_fine}x{p.n_fine}", "levels": p.n_levels,
                    "unknowns": n, "vanka_group": p.patch, "restart": 30, "rtol": RTOL,
                    "parallelism": f"replicas x{world}",
@@ -308,10 +319,13 @@ def run_ours(args, rank, world, local):
         "rel_residual": st_mixed.get("rel_residual"),
         "fp64": {"value": world * n / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": st64.get("iterations"),
                  "speedup_mixed_over_fp64": ms64 / ms},
-        "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed": setup_mixed_s, "smoothers_fp64": setup_fp64_s},
+        "mixed_f32_inverses": {"value": world * n / (ms32 * 1e-3), "ms_per_step": ms32,
+                               "iterations": st32.get("iterations")},
+        "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed_half": setup_mixed_s,
+                    "smoothers_mixed_f32": setup_f32_s, "smoothers_fp64": setup_fp64_s},
         "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
-        "roofline": {"bound": "hbm", "kernel": "block_apply_kernel<float> (fine level)",
+        "roofline": {"bound": "hbm", "kernel": "block_apply_h_kernel (fine level, f16 inverses)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
                      "algorithmic_bytes_per_launch": prof["smoother_bytes"], "mean_launch_ms": sm_ms,

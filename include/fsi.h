@@ -49,7 +49,12 @@ typedef enum {
 } fsi_status;
 
 enum { FSI_BC_CHANNEL_2D = 0, FSI_BC_BOX_3D = 1 };
-enum { FSI_FP64 = 0, FSI_MIXED = 1 };
+/* FSI_FP64: everything float64.  FSI_MIXED: float32 V-cycle (level operators,
+ * transfers, block inverses, vectors), float64 FGMRES and outer operator.
+ * FSI_MIXED_HALF: as FSI_MIXED, with the Schwarz block inverses stored in
+ * float16 with one float32 scale per row (max-abs row normalisation) and
+ * applied with float32 accumulation. */
+enum { FSI_FP64 = 0, FSI_MIXED = 1, FSI_MIXED_HALF = 2 };
 
 /* One linearised FSI problem on the unit square/cube (Sec. 2.2 weak form,
  * linearised at d = 0 with a frozen advection field; linear-elastic solid
@@ -69,7 +74,7 @@ typedef struct {
 } fsi_hier_opts;
 
 typedef struct {
-    int precision;              /* FSI_FP64 or FSI_MIXED (float32 cycle, float64 Krylov) */
+    int precision;              /* FSI_FP64, FSI_MIXED or FSI_MIXED_HALF */
     int patch;                  /* Vanka group edge b >= 1: b^dim pressure vertices per block */
     double omega;               /* Richardson damping (Sec. 3.2), > 0 */
     int nu_pre, nu_post;        /* smoothing steps, >= 1 */

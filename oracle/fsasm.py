@@ -31,6 +31,10 @@ partition-of-unity weights W_j = diag(1/multiplicity):
     x <- x + omega P2^{-1} (b - A x)        (damped Richardson, Sec. 3.2).
 
 The oracle factors each block with partial-pivoting LU (scipy/LAPACK getrf).
+Storage emulations of the mixed modes: ``dtype=float32`` factors and solves
+in float32; ``half=True`` forms the float64 inverse from the LU factors,
+normalises each row by its max-abs entry, rounds it to float16 and applies it
+in float32 times the float32 row scale.
 """
 from __future__ import annotations
 
@@ -98,9 +102,10 @@ class FSASM:
     """The smoother's preconditioner P2^{-1} on one level."""
 
     def __init__(self, A: sp.csr_matrix, lev: Level, b: int, *, dtype=np.float64,
-                 weighted: bool = True):
+                 weighted: bool = True, half: bool = False):
         self.n = A.shape[0]
-        self.dtype = dtype
+        self.dtype = np.float32 if half else dtype
+        self.half = half
         self.blocks = block_index_sets(lev, b)
         mult = np.zeros(self.n)
         for idx in self.blocks:
@@ -121,7 +126,14 @@ class FSASM:
             blk = np.zeros((idx.size, idx.size))
             blk[rows[keep], cols[keep]] = sub.data[keep]
             local[idx] = -1
-            self.lu.append(la.lu_factor(blk.astype(dtype), check_finite=True))
+            if half:
+                inv = la.lu_solve(la.lu_factor(blk), np.eye(idx.size))
+                scale = np.abs(inv).max(1)
+                scale[scale == 0] = 1.0
+                m16 = (inv / scale[:, None]).astype(np.float16)
+                self.lu.append((m16, scale.astype(np.float32)))
+            else:
+                self.lu.append(la.lu_factor(blk.astype(dtype), check_finite=True))
         self.jacobi = np.flatnonzero((lev.group == G_US) | lev.fixed)
         self.inv_diag = 1.0 / Ad.diagonal()[self.jacobi]
 
@@ -132,7 +144,11 @@ class FSASM:
         y = np.zeros(self.n, dt)
         w = self.weight.astype(dt)
         for idx, lu in zip(self.blocks, self.lu):
-            y[idx] += w[idx] * la.lu_solve(lu, r[idx])
+            if self.half:
+                m16, scale = lu
+                y[idx] += w[idx] * (scale * (m16.astype(np.float32) @ r[idx]))
+            else:
+                y[idx] += w[idx] * la.lu_solve(lu, r[idx])
         y[self.jacobi] += (r[self.jacobi] * self.inv_diag.astype(dt)).astype(dt)
         return y
 
@@ -143,6 +159,10 @@ class FSASM:
         y = np.zeros(self.n, dt)
         w = self.weight.astype(dt)
         for idx, lu in zip(self.blocks, self.lu):
-            y[idx] += la.lu_solve(lu, w[idx] * r[idx], trans=1)
+            if self.half:
+                m16, scale = lu
+                y[idx] += m16.astype(np.float32).T @ (scale * w[idx] * r[idx])
+            else:
+                y[idx] += la.lu_solve(lu, w[idx] * r[idx], trans=1)
         y[self.jacobi] += (r[self.jacobi] * self.inv_diag.astype(dt)).astype(dt)
         return y

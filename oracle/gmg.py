@@ -8,6 +8,8 @@ are rediscretised on each level; transfers are P2 and R2 of Sec. 3.3.
 Mixed mode (extension, not in the paper): level operators, transfers,
 Schwarz factors and V-cycle vectors are rounded to float32 and the cycle's
 arithmetic runs in float32; the coarse direct solve stays float64.
+mixed="half" additionally stores the Schwarz block inverses in float16 with
+a float32 scale per row (see fsasm.FSASM).
 
 The transposed cycle (adjoint extension) applies the transposed operators in
 reverse order: transposed post-smoothing first, restriction by P^T,
@@ -30,7 +32,8 @@ class Hierarchy:
                  nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
                  weighted: bool = True):
         self.prob = prob
-        self.mixed = mixed
+        self.mixed = bool(mixed)
+        half = mixed == "half"
         self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
         self.wdtype = np.float32 if mixed else np.float64
         self.levels = build_levels(prob)
@@ -42,7 +45,7 @@ class Hierarchy:
                                        classical=classical_restriction) for l in range(1, nl)]
         b = prob.patch if patch is None else patch
         self.smoothers = [None] + [FSASM(self.A[l], self.levels[l], b, dtype=self.wdtype,
-                                         weighted=weighted) for l in range(1, nl)]
+                                         weighted=weighted, half=half) for l in range(1, nl)]
         self.coarse_lu = la.lu_factor(self.A[0].toarray())
         wd = self.wdtype
         self.Aw = [A.astype(wd) for A in self.A]

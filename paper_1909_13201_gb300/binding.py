@@ -16,7 +16,7 @@ from . import build as _build
 
 FSI_OK, FSI_ERR_ARG, FSI_ERR_CUDA, FSI_ERR_ALLOC, FSI_ERR_ZERO_PIVOT, FSI_ERR_NOT_CONVERGED, \
     FSI_ERR_BREAKDOWN, FSI_ERR_NONFINITE, FSI_ERR_STATE = range(9)
-FSI_FP64, FSI_MIXED = 0, 1
+FSI_FP64, FSI_MIXED, FSI_MIXED_HALF = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_ALLOC", 4: "ERR_ZERO_PIVOT",
                 5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_NONFINITE", 8: "ERR_STATE"}
 

@@ -217,7 +217,6 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
 fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
     if (pb.m_alloc >= m) return FSI_OK;
     const int64_t n = pb.dev.back().n;
-    const size_t tsz = cx.precision == FSI_MIXED ? 4 : 8;
     FSI_TRY(pb.V.alloc((size_t)n * (m + 1) * 8));
     FSI_TRY(pb.Z.alloc((size_t)n * m * 8));     // float64: the outer SpMV reads it without conversions
     FSI_TRY(pb.H.alloc((size_t)(m + 1) * m * 8));
@@ -384,7 +383,7 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
             FSI_TRY(upload_csr(L.PT, PT, s));
             FSI_TRY(upload_csr(L.RT, RT, s));
         }
-        if (cx.precision == FSI_MIXED) {
+        if (cx.precision != FSI_FP64) {
             FSI_TRY(make_f32(L.AT, s));
             if (l >= 1) {
                 FSI_TRY(make_f32(L.PT, s));
@@ -480,9 +479,11 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
 
 fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
     cudaStream_t s = cx.stream;
-    const bool mixed = cx.precision == FSI_MIXED;
+    const bool mixed = cx.precision != FSI_FP64;             // float32 cycle
     const size_t tsz = mixed ? 4 : 8;
-    const int VW = mixed ? 4 : 2;
+    const int store = cx.precision == FSI_MIXED_HALF ? 2 : (mixed ? 1 : 0);
+    const int VW = store == 2 ? 8 : (store == 1 ? 4 : 2);   // 16-byte rows
+    const size_t isz = store == 2 ? 2 : (store == 1 ? 4 : 8);
     for (size_t l = 0; l < pb.dev.size(); ++l) {
         LevelDev &D = pb.dev[l];
         LevelHost &H = pb.host[l];
@@ -523,7 +524,10 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_TRY(upload(D.blk_off, off.data(), off.size() * 8, s));
         if (mixed) FSI_TRY(upload(D.blk_w, w32.data(), w32.size() * 4, s));
         else FSI_TRY(upload(D.blk_w, w64.data(), w64.size() * 8, s));
-        FSI_TRY(D.inv.alloc((size_t)D.inv_elems * tsz));
+        FSI_TRY(D.inv.alloc((size_t)D.inv_elems * isz));
+        D.inv_store = store;
+        if (store == 2) FSI_TRY(D.inv_scale.alloc(D.h_blk_idx.size() * 4));
+        else D.inv_scale.release();
         // Jacobi rows: u^s (lumped K_u^s, Sec. 3.2) and fixed dofs
         std::vector<int32_t> jac;
         for (int64_t i = 0; i < D.n; ++i)
@@ -562,7 +566,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             FSI_TRY(upload(D.items, it.data(), it.size() * 4, s));
         }
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
-        FSI_TRY(launch_block_invert(D.A, D, cx.precision, cx.flags.as<int>(), s, cx.num_sms));
+        FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
         int flag = 0;
         FSI_TRY(read_flag(cx, &flag));
         if (flag) {
@@ -684,7 +688,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     Context *cx = reinterpret_cast<Context *>(ctx);
     if (!cx || !opts) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
-    if ((opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) || opts->patch < 1 || opts->patch > 16 ||
+    if (opts->precision < FSI_FP64 || opts->precision > FSI_MIXED_HALF || opts->patch < 1 || opts->patch > 16 ||
         !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8) {
         set_error("smoother options out of range");
         return FSI_ERR_ARG;
@@ -706,7 +710,7 @@ static fsi_status solve_one(Context &cx, Problem &pb, const double *b, double *x
                             fsi_solve_stats *st, bool tr) {
     auto t0 = std::chrono::steady_clock::now();
     fsi_solve_stats local;
-    fsi_status s = (cx.precision == FSI_MIXED) ? fgmres<float>(cx, pb, b, x, *o, local, tr)
+    fsi_status s = (cx.precision != FSI_FP64) ? fgmres<float>(cx, pb, b, x, *o, local, tr)
                                                : fgmres<double>(cx, pb, b, x, *o, local, tr);
     auto t1 = std::chrono::steady_clock::now();
     local.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -793,11 +797,13 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     // algorithmic bytes of one fine-level smoother apply and residual SpMV
     const Problem &pb = cx->probs[0];
     const LevelDev &F = pb.dev.back();
-    const double ts = cx->precision == FSI_MIXED ? 4.0 : 8.0;
+    const double ts = cx->precision != FSI_FP64 ? 4.0 : 8.0;
+    const double is = cx->precision == FSI_MIXED_HALF ? 2.0 : ts;
+    const double rowx = cx->precision == FSI_MIXED_HALF ? 4.0 : 0.0;   // row scale
     double blk = 0.0;
     for (int64_t j = 0; j + 1 < (int64_t)F.h_blk_ptr.size(); ++j) {
         const double nj = (double)(F.h_blk_ptr[j + 1] - F.h_blk_ptr[j]);
-        blk += nj * nj * ts + nj * (4.0 + ts + ts + 2.0 * ts);   // inverse, idx, weight, gather r, x RMW
+        blk += nj * nj * is + nj * (4.0 + ts + ts + 2.0 * ts + rowx);   // inverse, idx, weight, gather r, x RMW
     }
     blk += (double)F.n_jac * (4.0 + ts + ts + 2.0 * ts);
     const double spmv = (double)F.A.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)F.n * 3.0 * ts;
@@ -890,7 +896,7 @@ fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r
     if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
     DeviceGuard guard(cx->device);
     LevelDev &L = pb->dev[level];
-    return cx->precision == FSI_MIXED ? apply_smoother_t<float>(*cx, L, r, y, transpose)
+    return cx->precision != FSI_FP64 ? apply_smoother_t<float>(*cx, L, r, y, transpose)
                                       : apply_smoother_t<double>(*cx, L, r, y, transpose);
 }
 
@@ -901,7 +907,7 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
     if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
     DeviceGuard guard(cx->device);
     if (transpose) FSI_TRY(build_transposes(*cx, *pb));
-    return cx->precision == FSI_MIXED ? apply_vcycle_t<float>(*cx, *pb, v, z, transpose)
+    return cx->precision != FSI_FP64 ? apply_vcycle_t<float>(*cx, *pb, v, z, transpose)
                                       : apply_vcycle_t<double>(*cx, *pb, v, z, transpose);
 }
 

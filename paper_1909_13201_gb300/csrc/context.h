@@ -80,6 +80,8 @@ struct LevelDev {
     std::vector<int32_t> h_blk_idx;
     DevBuf blk_ptr, blk_idx, blk_off, blk_w;   // int32, int32, int64, working-precision weights
     DevBuf inv;                                 // block inverses, row-major, padded rows
+    DevBuf inv_scale;                           // float16 storage: float32 scale per block row
+    int inv_store = 0;                          // 0 float64, 1 float32, 2 float16 + row scale
     int64_t n_items = 0;
     DevBuf items;                               // int4 (block, row begin, row end, 0) apply work items
     int64_t n_jac = 0;
@@ -143,7 +145,8 @@ template <class TA, class TX, class TY>
 fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
                        cudaStream_t s);
 
-fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int precision, int *flags,
+// storage: 0 float64, 1 float32, 2 float16 with a float32 scale per row
+fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int storage, int *flags,
                                cudaStream_t s, int num_sms);
 template <class T>
 fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, int transpose,

@@ -17,6 +17,9 @@
 // weighted result W_j y is scatter-added into x (atomics: blocks overlap).
 // Jacobi rows (u^s and fixed dofs) are a separate elementwise kernel.
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "context.h"
 
@@ -33,8 +36,9 @@ struct GJParams {
     const int64_t *blk_off;
     const int32_t *row_ptr, *col;
     const double *val;
-    void *inv;                 // float or double
-    int out_f32;
+    void *inv;                 // double, float or __half
+    float *scale;              // float16 storage: per block row
+    int storage;               // 0 float64, 1 float32, 2 float16 + row scale
     int rows_per_cta;          // R
     int *flags;
 };
@@ -117,7 +121,22 @@ __global__ void __launch_bounds__(GJ_THREADS) block_gj_kernel(GJParams P) {
     // keep peers' shared memory alive until every CTA stopped reading it
     if (C > 1) cluster.sync();
     const int64_t off = P.blk_off[blk];
-    if (P.out_f32) {
+    if (P.storage == 2) {
+        // row-normalised float16: scale = max |row|, entries in [-1, 1]
+        const int ldo = (n + 7) & ~7;
+        __half *out = static_cast<__half *>(P.inv) + off;
+        const int warp2 = threadIdx.x / 32, lane2 = threadIdx.x % 32;
+        for (int li = warp2; li < nr; li += blockDim.x / 32) {
+            double m = 0.0;
+            for (int j = lane2; j < n; j += 32) m = fmax(m, fabs(A[(size_t)li * ld + j]));
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const double sc = m > 0.0 ? m : 1.0;
+            if (lane2 == 0) P.scale[s0 + r0 + li] = (float)sc;
+            const double isc = 1.0 / sc;
+            for (int j = lane2; j < ldo; j += 32)
+                out[(size_t)(r0 + li) * ldo + j] = __float2half_rn(j < n ? (float)(A[(size_t)li * ld + j] * isc) : 0.0f);
+        }
+    } else if (P.storage == 1) {
         const int ldo = (n + 3) & ~3;
         float *out = static_cast<float *>(P.inv) + off;
         for (int t = threadIdx.x; t < nr * ldo; t += blockDim.x) {
@@ -255,6 +274,109 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_t_kernel(const int4
     }
 }
 
+// float16 storage (row-normalised, float32 scale per row), float32 vectors
+__device__ __forceinline__ float dot8(const uint4 &m, const float4 &a, const float4 &b) {
+    const __half2 *h = reinterpret_cast<const __half2 *>(&m);
+    const float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
+    const float2 f2 = __half22float2(h[2]), f3 = __half22float2(h[3]);
+    return f0.x * a.x + f0.y * a.y + f1.x * a.z + f1.y * a.w + f2.x * b.x + f2.y * b.y + f3.x * b.z + f3.y * b.w;
+}
+
+__global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4 *__restrict__ items,
+                                                                      const int32_t *__restrict__ blk_ptr,
+                                                                      const int32_t *__restrict__ blk_idx,
+                                                                      const int64_t *__restrict__ blk_off,
+                                                                      const float *__restrict__ blk_w,
+                                                                      const __half *__restrict__ inv,
+                                                                      const float *__restrict__ scale,
+                                                                      const int32_t *__restrict__ jac_idx,
+                                                                      const float *__restrict__ jac_inv,
+                                                                      const float *__restrict__ r, float *__restrict__ x,
+                                                                      float omega) {
+    __shared__ __align__(16) float rs[MAX_BLOCK];
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, r0 = it.y, r1 = it.z;
+    if (blk < 0) {
+        for (int k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+            const int i = jac_idx[k];
+            x[i] += omega * r[i] * jac_inv[k];
+        }
+        return;
+    }
+    const int s0 = blk_ptr[blk];
+    const int n = blk_ptr[blk + 1] - s0;
+    const int ld = (n + 7) & ~7;
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) rs[i] = (i < n) ? r[blk_idx[s0 + i]] : 0.0f;
+    __syncthreads();
+    const uint4 *M = reinterpret_cast<const uint4 *>(inv + blk_off[blk]);
+    const float4 *rv = reinterpret_cast<const float4 *>(rs);
+    const int nv = ld / 8;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int NW = APPLY_THREADS / 32;
+    for (int i = r0 + warp * RPW; i < r1; i += NW * RPW) {
+        float a[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) a[q] = 0.0f;
+        for (int c = lane; c < nv; c += 32) {
+            const float4 ra = rv[2 * c], rb = rv[2 * c + 1];
+            uint4 m[RPW];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+                if (i + q < r1) m[q] = __ldcs(M + (size_t)(i + q) * nv + c);
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+                if (i + q < r1) a[q] += dot8(m[q], ra, rb);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+        if (lane < RPW && i + lane < r1) {
+            float v = a[0];
+#pragma unroll
+            for (int q = 1; q < RPW; ++q)
+                if (lane == q) v = a[q];
+            const int g = s0 + i + lane;
+            atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
+        }
+    }
+}
+
+// transposed: A^{-1} = D_s M (D_s row scales), so A^{-T} W r = M^T (D_s W r)
+__global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const int4 *__restrict__ items,
+                                                                        const int32_t *__restrict__ blk_ptr,
+                                                                        const int32_t *__restrict__ blk_idx,
+                                                                        const int64_t *__restrict__ blk_off,
+                                                                        const float *__restrict__ blk_w,
+                                                                        const __half *__restrict__ inv,
+                                                                        const float *__restrict__ scale,
+                                                                        const int32_t *__restrict__ jac_idx,
+                                                                        const float *__restrict__ jac_inv,
+                                                                        const float *__restrict__ r, float *__restrict__ x,
+                                                                        float omega) {
+    __shared__ float rs[MAX_BLOCK];
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, c0 = it.y, c1 = it.z;
+    if (blk < 0) {
+        for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+            const int i = jac_idx[k];
+            x[i] += omega * r[i] * jac_inv[k];
+        }
+        return;
+    }
+    const int s0 = blk_ptr[blk];
+    const int n = blk_ptr[blk + 1] - s0;
+    const int ld = (n + 7) & ~7;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = scale[s0 + i] * blk_w[s0 + i] * r[blk_idx[s0 + i]];
+    __syncthreads();
+    const __half *M = inv + blk_off[blk];
+    for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+        float acc = 0.0f;
+        for (int i = 0; i < n; ++i) acc += __half2float(M[(size_t)i * ld + j]) * rs[i];
+        atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
+    }
+}
+
 template <class T>
 __global__ void jacobi_kernel(const int32_t *__restrict__ idx, const T *__restrict__ dinv, int64_t n,
                               const T *__restrict__ r, T *__restrict__ x, T omega) {
@@ -359,7 +481,7 @@ __global__ void dense_gemv_t_kernel(const double *__restrict__ M, int64_t n, con
 
 }  // namespace
 
-fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int precision, int *flags,
+fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int storage, int *flags,
                                cudaStream_t s, int num_sms) {
     (void)num_sms;
     if (lev.n_blocks == 0) return FSI_OK;
@@ -383,7 +505,8 @@ fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int precisi
     P.col = A.col.as<int32_t>();
     P.val = A.val64.as<double>();
     P.inv = lev.inv.p;
-    P.out_f32 = precision == FSI_MIXED ? 1 : 0;
+    P.scale = lev.inv_scale.as<float>();
+    P.storage = storage;
     P.rows_per_cta = (n + C - 1) / C;
     P.flags = flags;
     const size_t smem = smem_for(C);
@@ -431,6 +554,23 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
     if (lev.max_block > MAX_BLOCK) {
         set_error("Schwarz block larger than the apply kernel's staging buffer");
         return FSI_ERR_ARG;
+    }
+    if (std::is_same<T, float>::value && lev.inv_store == 2) {
+        const float *rf = reinterpret_cast<const float *>(r);
+        float *xf = reinterpret_cast<float *>(x);
+        if (transpose)
+            block_apply_h_t_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+                lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
+                lev.jac_inv.as<float>(), rf, xf, (float)omega);
+        else
+            block_apply_h_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+                lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
+                lev.jac_inv.as<float>(), rf, xf, (float)omega);
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+        return FSI_OK;
     }
     if (transpose)
         block_apply_t_kernel<T><<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
