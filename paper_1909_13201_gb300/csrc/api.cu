@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -214,8 +215,18 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
 }
 
 // ------------------------------------------------------------ workspace
+void drop_graphs(Problem &pb) {
+    for (auto &v : pb.graphs) {
+        for (auto &ge : v)
+            if (ge) cudaGraphExecDestroy(ge);
+        v.clear();
+    }
+    for (auto &v : pb.graph_kernels) v.clear();
+}
+
 fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
     if (pb.m_alloc >= m) return FSI_OK;
+    drop_graphs(pb);
     const int64_t n = pb.dev.back().n;
     FSI_TRY(pb.V.alloc((size_t)n * (m + 1) * 8));
     FSI_TRY(pb.Z.alloc((size_t)n * m * 8));     // float64: the outer SpMV reads it without conversions
@@ -289,37 +300,73 @@ fsi_status fgmres(Context &cx, Problem &pb, const double *b, double *x, const fs
     st.r0 = beta;
     int its = 0;
     fsi_status status = FSI_OK;
-    T *bfine = nullptr;
+    // one Arnoldi step j: z_j = M^{-1} v_j, w = A z_j, CGS2, Givens, the
+    // scalars (estimate, h_{j+1,j}, ||A z_j||, flags) to pinned host memory,
+    // and v_{j+1} = w / h_{j+1,j}.  Fixed buffers only, so the step is
+    // captured once per j as a CUDA graph and replayed in every solve.
+    auto issue = [&](int j) -> fsi_status {
+        double *vj = V + (size_t)j * n;
+        double *zj = Z + (size_t)j * n;
+        if (std::is_same<T, double>::value) {
+            FSI_TRY(vcycle<T>(cx, pb, L - 1, reinterpret_cast<const T *>(vj), reinterpret_cast<T *>(zj), tr));
+        } else {
+            T *bfine = F.b.as<T>();
+            FSI_TRY(launch_cast_f64_f32(vj, reinterpret_cast<float *>(bfine), n, s));
+            FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
+            FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
+        }
+        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w,
+                                                    SPMV_SET, s));
+        const int nv = j + 1;
+        FSI_TRY(launch_mdot(V, n, nv, w, n, pb.partials.as<double>(), NRED, s));
+        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h1.as<double>(), 0, s));
+        FSI_TRY(launch_update_dot(w, V, n, nv, h1.as<double>(), n, pb.partials.as<double>(), NRED, 0, s));
+        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h2.as<double>(), 0, s));
+        FSI_TRY(launch_update_dot(w, V, n, nv, h2.as<double>(), n, pb.partials.as<double>(), NRED, 1, s));
+        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, 1, scal + 7, 0, s));
+        FSI_TRY(launch_givens(H, m + 1, j, h1.as<double>(), h2.as<double>(), scal + 7, pb.cs.as<double>(),
+                              pb.sn.as<double>(), g, scal, s));
+        FSI_CUDA(cudaMemcpyAsync(cx.h_pinned, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
+        FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
+        return FSI_OK;
+    };
+    const bool graphs = cx.use_graphs && !cx.profile && s != nullptr;
+    auto &gexec = pb.graphs[tr ? 1 : 0];
+    auto &gkern = pb.graph_kernels[tr ? 1 : 0];
+    if (graphs && (int)gexec.size() != m) {
+        for (auto &ge : gexec)
+            if (ge) cudaGraphExecDestroy(ge);
+        gexec.assign(m, nullptr);
+        gkern.assign(m, 0);
+    }
     while (beta > o.rtol * bnorm && its < o.max_iters && std::isfinite(beta)) {
         FSI_TRY(launch_init_basis(r, V, g, m, scal + 6, n, s));
         int k = 0;
         bool stop_all = false;
         for (int j = 0; j < m; ++j) {
-            double *vj = V + (size_t)j * n;
-            double *zj = Z + (size_t)j * n;
-            // z_j = M^{-1} v_j (the cycle runs in T; z_j is kept in float64)
-            if (std::is_same<T, double>::value) {
-                FSI_TRY(vcycle<T>(cx, pb, L - 1, reinterpret_cast<const T *>(vj), reinterpret_cast<T *>(zj), tr));
+            if (graphs) {
+                if (!gexec[j]) {
+                    const int64_t before = launches_so_far();
+                    cudaGraph_t gr = nullptr;
+                    FSI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                    fsi_status cs = issue(j);
+                    cudaError_t ce = cudaStreamEndCapture(s, &gr);
+                    if (cs != FSI_OK) {
+                        if (gr) cudaGraphDestroy(gr);
+                        return cs;
+                    }
+                    FSI_CUDA(ce);
+                    FSI_CUDA(cudaGraphInstantiate(&gexec[j], gr, 0));
+                    cudaGraphDestroy(gr);
+                    gkern[j] = launches_so_far() - before;
+                    count_launch(-(int)gkern[j]);   // captured, not run
+                }
+                FSI_CUDA(cudaGraphLaunch(gexec[j], s));
+                count_launch((int)gkern[j]);
             } else {
-                bfine = F.b.as<T>();
-                FSI_TRY(launch_cast_f64_f32(vj, reinterpret_cast<float *>(bfine), n, s));
-                FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
-                FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
+                FSI_TRY(issue(j));
             }
-            // w = A z_j (float64 operator and vector)
-            FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w,
-                                                        SPMV_SET, s));
-            // CGS2
-            const int nv = j + 1;
-            FSI_TRY(launch_mdot(V, n, nv, w, n, pb.partials.as<double>(), NRED, s));
-            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h1.as<double>(), 0, s));
-            FSI_TRY(launch_update_dot(w, V, n, nv, h1.as<double>(), n, pb.partials.as<double>(), NRED, 0, s));
-            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h2.as<double>(), 0, s));
-            FSI_TRY(launch_update_dot(w, V, n, nv, h2.as<double>(), n, pb.partials.as<double>(), NRED, 1, s));
-            FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, 1, scal + 7, 0, s));
-            FSI_TRY(launch_givens(H, m + 1, j, h1.as<double>(), h2.as<double>(), scal + 7, pb.cs.as<double>(),
-                                  pb.sn.as<double>(), g, scal, s));
-            FSI_TRY(read_scal(cx, pb, 5));
+            FSI_CUDA(cudaStreamSynchronize(s));
             ++its;
             k = j + 1;
             const double est = hs[0], hn = hs[1], wn = hs[2];
@@ -330,7 +377,6 @@ fsi_status fgmres(Context &cx, Problem &pb, const double *b, double *x, const fs
                 break;
             }
             if (est <= o.rtol * bnorm || hn <= 1e-14 * wn || its >= o.max_iters) break;
-            FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
         }
         if (stop_all) break;
         FSI_TRY(launch_backsolve(H, m + 1, k, g, pb.y.as<double>(), s));
@@ -576,6 +622,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
     }
     pb.transposes_ready = false;
     pb.m_alloc = 0;
+    drop_graphs(pb);
     return FSI_OK;
 }
 
@@ -644,6 +691,13 @@ fsi_status fsi_setup_hierarchy(const fsi_problem *probs, int n_probs, const fsi_
     if (cx->restriction != 0 && cx->restriction != 1) { set_error("restriction must be 0 or 1"); return FSI_ERR_ARG; }
     FSI_CUDA(cudaDeviceGetAttribute(&cx->num_sms, cudaDevAttrMultiProcessorCount, cx->device));
     FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&cx->h_pinned), 64 * 8));
+    FSI_CUDA(cudaStreamCreateWithFlags(&cx->work, cudaStreamNonBlocking));
+    FSI_CUDA(cudaEventCreateWithFlags(&cx->ev_in, cudaEventDisableTiming));
+    FSI_CUDA(cudaEventCreateWithFlags(&cx->ev_out, cudaEventDisableTiming));
+    {
+        const char *g = getenv("FSI_USE_GRAPHS");
+        cx->use_graphs = !(g && g[0] == '0');
+    }
     FSI_TRY(cx->flags.alloc(16));
     cx->probs.resize(n_probs);
     for (int i = 0; i < n_probs; ++i) {
@@ -710,8 +764,18 @@ static fsi_status solve_one(Context &cx, Problem &pb, const double *b, double *x
                             fsi_solve_stats *st, bool tr) {
     auto t0 = std::chrono::steady_clock::now();
     fsi_solve_stats local;
+    // the solve runs on the context's own non-blocking stream (graph capture
+    // is not possible on a legacy default stream), ordered after the work
+    // already queued on the caller's stream and before anything queued later
+    cudaStream_t user = cx.stream;
+    FSI_CUDA(cudaEventRecord(cx.ev_in, user));
+    FSI_CUDA(cudaStreamWaitEvent(cx.work, cx.ev_in, 0));
+    cx.stream = cx.work;
     fsi_status s = (cx.precision != FSI_FP64) ? fgmres<float>(cx, pb, b, x, *o, local, tr)
                                                : fgmres<double>(cx, pb, b, x, *o, local, tr);
+    cx.stream = user;
+    FSI_CUDA(cudaEventRecord(cx.ev_out, cx.work));
+    FSI_CUDA(cudaStreamWaitEvent(user, cx.ev_out, 0));
     auto t1 = std::chrono::steady_clock::now();
     local.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     if (!cx.ev_marks.empty()) {
@@ -926,8 +990,13 @@ void fsi_destroy(fsi_ctx *ctx) {
         collect_marks(*cx);
         for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
         cx->ev_pool.clear();
+        for (auto &pb : cx->probs) drop_graphs(pb);
+        if (cx->work) cudaStreamSynchronize(cx->work);
         cx->probs.clear();
         cx->flags.release();
+        if (cx->ev_in) cudaEventDestroy(cx->ev_in);
+        if (cx->ev_out) cudaEventDestroy(cx->ev_out);
+        if (cx->work) cudaStreamDestroy(cx->work);
     }
     delete cx;
 }

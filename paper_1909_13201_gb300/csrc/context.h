@@ -103,6 +103,9 @@ struct Problem {
     // Krylov workspace (fine level)
     int m_alloc = 0;
     DevBuf V, Z, H, g, cs, sn, y, w, rvec, xwork, partials, scal, h1, h2;
+    // one CUDA graph per Arnoldi step j (index 0: forward, 1: transposed)
+    std::vector<cudaGraphExec_t> graphs[2];
+    std::vector<int64_t> graph_kernels[2];
 };
 
 // kernels launched by the library (all contexts), for launch accounting
@@ -130,6 +133,10 @@ struct Context {
     double prof_ms[2] = {0, 0};
     int64_t prof_n[2] = {0, 0};
     int64_t launch_base = 0;
+    // solves run on a context-owned non-blocking stream
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    bool use_graphs = true;
 };
 
 // ---------------------------------------------------------------- kernels
