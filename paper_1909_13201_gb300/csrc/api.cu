@@ -251,157 +251,285 @@ fsi_status norm2(Context &cx, Problem &pb, const double *v, int64_t n, int slot)
     return launch_reduce_partials(pb.partials.as<double>(), NRED, 1, pb.scal.as<double>() + slot, 0, cx.stream);
 }
 
-fsi_status read_scal(Context &cx, Problem &pb, int count) {
-    FSI_CUDA(cudaMemcpyAsync(cx.h_pinned, pb.scal.p, (size_t)count * 8, cudaMemcpyDeviceToHost, cx.stream));
-    FSI_CUDA(cudaStreamSynchronize(cx.stream));
-    return FSI_OK;
-}
 
 // --------------------------------------------------------------- FGMRES
 // Right-preconditioned FGMRES(m) with CGS2 Arnoldi and Givens rotations;
 // converged when the float64 true residual ||b - A x|| <= rtol ||b||.
+//
+// The method is written as a resumable state machine so that several
+// independent problems advance together: each round enqueues one step of
+// every active run on the run's own stream (asynchronously, ending with a
+// device-to-host copy of the step's scalars into the run's pinned slot),
+// waits for all streams, and then lets every run read its scalars and pick
+// its next step.  One problem is the plain sequential solve.
+struct Run {
+    Problem *pb = nullptr;
+    const double *b = nullptr;
+    double *x = nullptr;
+    bool tr = false;
+    fsi_solve_opts o{};
+    enum { NORM_B, START, CYCLE, STEP, DONE } phase = NORM_B;
+    int its = 0, j = 0, k = 0;
+    double bnorm = 0, beta = 0;
+    fsi_status status = FSI_OK;
+    fsi_solve_stats st{};
+    std::chrono::steady_clock::time_point t0;
+};
+
+// one Arnoldi step j of problem pb on stream s: z_j = M^{-1} v_j, w = A z_j,
+// CGS2, Givens, the scalars (estimate, h_{j+1,j}, ||A z_j||, flags) to the
+// pinned slot, and v_{j+1} = w / h_{j+1,j}.  Fixed buffers only, so it is
+// captured once per j as a CUDA graph and replayed in later solves.
 template <class T>
-fsi_status fgmres(Context &cx, Problem &pb, const double *b, double *x, const fsi_solve_opts &o,
-                  fsi_solve_stats &st, bool tr) {
+fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
     cudaStream_t s = cx.stream;
     LevelDev &F = pb.dev.back();
     const int64_t n = F.n;
-    const int m = o.restart;
     const int L = (int)pb.dev.size();
-    FSI_TRY(ensure_workspace(cx, pb, m));
     const DevCSR &A = tr ? F.AT : F.A;
     double *V = pb.V.as<double>(), *H = pb.H.as<double>(), *g = pb.g.as<double>();
-    double *w = pb.w.as<double>(), *r = pb.rvec.as<double>(), *scal = pb.scal.as<double>();
-    double *Z = pb.Z.as<double>();
-    const double *hs = reinterpret_cast<const double *>(cx.h_pinned);
-    DevBuf &h1 = pb.h1, &h2 = pb.h2;
-    st = fsi_solve_stats();
-    st.status = FSI_OK;
-    // ||b||
-    FSI_TRY(norm2(cx, pb, b, n, 5));
-    FSI_TRY(read_scal(cx, pb, 6));
-    const double bnorm = std::sqrt(hs[5]);
-    if (!std::isfinite(bnorm)) {
-        st.status = FSI_ERR_NONFINITE;
-        set_error("right-hand side has a non-finite norm");
-        return FSI_ERR_NONFINITE;
+    double *w = pb.w.as<double>(), *scal = pb.scal.as<double>(), *Z = pb.Z.as<double>();
+    double *vj = V + (size_t)j * n;
+    double *zj = Z + (size_t)j * n;
+    if (std::is_same<T, double>::value) {
+        FSI_TRY(vcycle<T>(cx, pb, L - 1, reinterpret_cast<const T *>(vj), reinterpret_cast<T *>(zj), tr));
+    } else {
+        T *bfine = F.b.as<T>();
+        FSI_TRY(launch_cast_f64_f32(vj, reinterpret_cast<float *>(bfine), n, s));
+        FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
+        FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
     }
-    if (bnorm == 0.0) {
-        FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, s));
-        FSI_CUDA(cudaStreamSynchronize(s));
-        st.converged = 1;
-        return FSI_OK;
-    }
-    if (!o.use_x0) FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, s));
-    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s));
-    FSI_TRY(norm2(cx, pb, r, n, 6));
-    FSI_TRY(read_scal(cx, pb, 7));
-    double beta = std::sqrt(hs[6]);
-    st.r0 = beta;
-    int its = 0;
-    fsi_status status = FSI_OK;
-    // one Arnoldi step j: z_j = M^{-1} v_j, w = A z_j, CGS2, Givens, the
-    // scalars (estimate, h_{j+1,j}, ||A z_j||, flags) to pinned host memory,
-    // and v_{j+1} = w / h_{j+1,j}.  Fixed buffers only, so the step is
-    // captured once per j as a CUDA graph and replayed in every solve.
-    auto issue = [&](int j) -> fsi_status {
-        double *vj = V + (size_t)j * n;
-        double *zj = Z + (size_t)j * n;
-        if (std::is_same<T, double>::value) {
-            FSI_TRY(vcycle<T>(cx, pb, L - 1, reinterpret_cast<const T *>(vj), reinterpret_cast<T *>(zj), tr));
-        } else {
-            T *bfine = F.b.as<T>();
-            FSI_TRY(launch_cast_f64_f32(vj, reinterpret_cast<float *>(bfine), n, s));
-            FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
-            FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
-        }
-        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w,
-                                                    SPMV_SET, s));
-        const int nv = j + 1;
-        FSI_TRY(launch_mdot(V, n, nv, w, n, pb.partials.as<double>(), NRED, s));
-        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h1.as<double>(), 0, s));
-        FSI_TRY(launch_update_dot(w, V, n, nv, h1.as<double>(), n, pb.partials.as<double>(), NRED, 0, s));
-        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, nv, h2.as<double>(), 0, s));
-        FSI_TRY(launch_update_dot(w, V, n, nv, h2.as<double>(), n, pb.partials.as<double>(), NRED, 1, s));
-        FSI_TRY(launch_reduce_partials(pb.partials.as<double>(), NRED, 1, scal + 7, 0, s));
-        FSI_TRY(launch_givens(H, m + 1, j, h1.as<double>(), h2.as<double>(), scal + 7, pb.cs.as<double>(),
-                              pb.sn.as<double>(), g, scal, s));
-        FSI_CUDA(cudaMemcpyAsync(cx.h_pinned, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
-        FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
-        return FSI_OK;
-    };
-    const bool graphs = cx.use_graphs && !cx.profile && s != nullptr;
-    auto &gexec = pb.graphs[tr ? 1 : 0];
-    auto &gkern = pb.graph_kernels[tr ? 1 : 0];
-    if (graphs && (int)gexec.size() != m) {
-        for (auto &ge : gexec)
-            if (ge) cudaGraphExecDestroy(ge);
-        gexec.assign(m, nullptr);
-        gkern.assign(m, 0);
-    }
-    while (beta > o.rtol * bnorm && its < o.max_iters && std::isfinite(beta)) {
-        FSI_TRY(launch_init_basis(r, V, g, m, scal + 6, n, s));
-        int k = 0;
-        bool stop_all = false;
-        for (int j = 0; j < m; ++j) {
-            if (graphs) {
-                if (!gexec[j]) {
-                    const int64_t before = launches_so_far();
-                    cudaGraph_t gr = nullptr;
-                    FSI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                    fsi_status cs = issue(j);
-                    cudaError_t ce = cudaStreamEndCapture(s, &gr);
-                    if (cs != FSI_OK) {
-                        if (gr) cudaGraphDestroy(gr);
-                        return cs;
-                    }
-                    FSI_CUDA(ce);
-                    FSI_CUDA(cudaGraphInstantiate(&gexec[j], gr, 0));
-                    cudaGraphDestroy(gr);
-                    gkern[j] = launches_so_far() - before;
-                    count_launch(-(int)gkern[j]);   // captured, not run
+    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w, SPMV_SET, s));
+    const int nv = j + 1;
+    double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
+    FSI_TRY(launch_mdot(V, n, nv, w, n, part, NRED, s));
+    FSI_TRY(launch_reduce_partials(part, NRED, nv, h1, 0, s));
+    FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s));
+    FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
+    FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
+    FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
+    FSI_TRY(launch_givens(H, m + 1, j, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s));
+    FSI_CUDA(cudaMemcpyAsync(pb.h_scal, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
+    FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
+    return FSI_OK;
+}
+
+// enqueue ||v||^2 -> scal[slot] and its copy to the pinned slot
+fsi_status norm2_to_host(Context &cx, Problem &pb, const double *v, int64_t n, int slot) {
+    FSI_TRY(norm2(cx, pb, v, n, slot));
+    FSI_CUDA(cudaMemcpyAsync(pb.h_scal + slot, pb.scal.as<double>() + slot, 8, cudaMemcpyDeviceToHost, cx.stream));
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status enqueue(Context &cx, Run &R) {
+    Problem &pb = *R.pb;
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    const int m = R.o.restart;
+    const DevCSR &A = R.tr ? F.AT : F.A;
+    double *r = pb.rvec.as<double>();
+    switch (R.phase) {
+        case Run::NORM_B:
+            return norm2_to_host(cx, pb, R.b, n, 5);
+        case Run::START:
+            if (!R.o.use_x0) FSI_CUDA(cudaMemsetAsync(R.x, 0, (size_t)n * 8, s));
+            FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), R.x, R.b, r, SPMV_RESID, s));
+            return norm2_to_host(cx, pb, r, n, 6);
+        case Run::CYCLE:
+            FSI_TRY(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, pb.scal.as<double>() + 6, n, s));
+            R.j = 0;
+            // fall through: the first step of the cycle goes in the same round
+        case Run::STEP: {
+            const int j = R.j;
+            const bool graphs = cx.use_graphs && !cx.profile && s != nullptr;
+            auto &gexec = pb.graphs[R.tr ? 1 : 0];
+            auto &gkern = pb.graph_kernels[R.tr ? 1 : 0];
+            if (!graphs) return issue_step<T>(cx, pb, j, m, R.tr);
+            if ((int)gexec.size() != m) {
+                for (auto &ge : gexec)
+                    if (ge) cudaGraphExecDestroy(ge);
+                gexec.assign(m, nullptr);
+                gkern.assign(m, 0);
+            }
+            if (!gexec[j]) {
+                const int64_t before = launches_so_far();
+                cudaGraph_t gr = nullptr;
+                FSI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                fsi_status cs = issue_step<T>(cx, pb, j, m, R.tr);
+                cudaError_t ce = cudaStreamEndCapture(s, &gr);
+                if (cs != FSI_OK) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return cs;
                 }
-                FSI_CUDA(cudaGraphLaunch(gexec[j], s));
-                count_launch((int)gkern[j]);
-            } else {
-                FSI_TRY(issue(j));
+                FSI_CUDA(ce);
+                FSI_CUDA(cudaGraphInstantiate(&gexec[j], gr, 0));
+                cudaGraphDestroy(gr);
+                gkern[j] = launches_so_far() - before;
+                count_launch(-(int)gkern[j]);        // captured, not run
             }
-            FSI_CUDA(cudaStreamSynchronize(s));
-            ++its;
-            k = j + 1;
-            const double est = hs[0], hn = hs[1], wn = hs[2];
-            if (hs[4] != 0.0) {
-                status = FSI_ERR_NONFINITE;
-                set_error("non-finite value in the Arnoldi process");
-                stop_all = true;
-                break;
-            }
-            if (est <= o.rtol * bnorm || hn <= 1e-14 * wn || its >= o.max_iters) break;
+            FSI_CUDA(cudaGraphLaunch(gexec[j], s));
+            count_launch((int)gkern[j]);
+            return FSI_OK;
         }
-        if (stop_all) break;
-        FSI_TRY(launch_backsolve(H, m + 1, k, g, pb.y.as<double>(), s));
-        FSI_TRY(launch_combine<double>(x, Z, n, k, pb.y.as<double>(), n, s));
-        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s));
-        FSI_TRY(norm2(cx, pb, r, n, 6));
-        FSI_TRY(read_scal(cx, pb, 7));
-        beta = std::sqrt(hs[6]);
-        st.cycles++;
+        default:
+            return FSI_OK;
     }
-    st.iterations = its;
-    st.rN = beta;
-    st.rel_residual = beta / bnorm;
-    st.converged = beta <= o.rtol * bnorm;
-    st.rho = (its > 0 && st.r0 > 0) ? std::pow(beta / st.r0, 1.0 / its) : 0.0;
-    if (status == FSI_OK && !std::isfinite(beta)) {
+}
+
+// end of a cycle: x += Z y, true residual
+fsi_status enqueue_end_cycle(Context &cx, Run &R) {
+    Problem &pb = *R.pb;
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    const int m = R.o.restart;
+    const DevCSR &A = R.tr ? F.AT : F.A;
+    FSI_TRY(launch_backsolve(pb.H.as<double>(), m + 1, R.k, pb.g.as<double>(), pb.y.as<double>(), s));
+    FSI_TRY(launch_combine<double>(R.x, pb.Z.as<double>(), n, R.k, pb.y.as<double>(), n, s));
+    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), R.x, R.b, pb.rvec.as<double>(), SPMV_RESID, s));
+    return norm2_to_host(cx, pb, pb.rvec.as<double>(), n, 6);
+}
+
+void finish(Run &R, fsi_status status) {
+    R.phase = Run::DONE;
+    R.st.iterations = R.its;
+    R.st.rN = R.beta;
+    R.st.rel_residual = R.bnorm > 0 ? R.beta / R.bnorm : 0.0;
+    R.st.converged = R.bnorm == 0.0 || R.beta <= R.o.rtol * R.bnorm;
+    R.st.rho = (R.its > 0 && R.st.r0 > 0) ? std::pow(R.beta / R.st.r0, 1.0 / R.its) : 0.0;
+    if (status == FSI_OK && !std::isfinite(R.beta)) {
         status = FSI_ERR_NONFINITE;
         set_error("non-finite residual");
     }
-    if (status == FSI_OK && !st.converged) {
+    if (status == FSI_OK && !R.st.converged) {
         status = FSI_ERR_NOT_CONVERGED;
         set_error("FGMRES did not reach rtol within max_iters");
     }
-    st.status = status;
-    return status;
+    R.status = status;
+    R.st.status = status;
+    R.st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - R.t0).count();
+}
+
+// after the round's streams are idle: read the scalars, choose the next step
+fsi_status advance(Context &cx, Run &R, bool &end_cycle) {
+    const double *hs = R.pb->h_scal;
+    end_cycle = false;
+    switch (R.phase) {
+        case Run::NORM_B:
+            R.bnorm = std::sqrt(hs[5]);
+            if (!std::isfinite(R.bnorm)) {
+                set_error("right-hand side has a non-finite norm");
+                R.beta = NAN;
+                finish(R, FSI_ERR_NONFINITE);
+            } else if (R.bnorm == 0.0) {
+                FSI_CUDA(cudaMemsetAsync(R.x, 0, (size_t)R.pb->dev.back().n * 8, cx.stream));
+                R.beta = 0.0;
+                finish(R, FSI_OK);
+            } else {
+                R.phase = Run::START;
+            }
+            return FSI_OK;
+        case Run::START:
+            R.beta = std::sqrt(hs[6]);
+            R.st.r0 = R.beta;
+            break;
+        case Run::CYCLE:
+        case Run::STEP: {
+            ++R.its;
+            R.k = R.j + 1;
+            const double est = hs[0], hn = hs[1], wn = hs[2];
+            if (hs[4] != 0.0) {
+                set_error("non-finite value in the Arnoldi process");
+                R.beta = NAN;
+                finish(R, FSI_ERR_NONFINITE);
+                return FSI_OK;
+            }
+            if (est <= R.o.rtol * R.bnorm || hn <= 1e-14 * wn || R.its >= R.o.max_iters || R.k == R.o.restart) {
+                end_cycle = true;               // caller enqueues x update + true residual
+            } else {
+                R.j = R.j + 1;
+                R.phase = Run::STEP;
+            }
+            return FSI_OK;
+        }
+        default:
+            return FSI_OK;
+    }
+    // after a true residual (start of solve or end of a cycle)
+    if (R.beta > R.o.rtol * R.bnorm && R.its < R.o.max_iters && std::isfinite(R.beta)) R.phase = Run::CYCLE;
+    else finish(R, FSI_OK);
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status run_batch(Context &cx, std::vector<Run> &runs) {
+    cudaStream_t user = cx.stream;
+    for (auto &R : runs) {
+        FSI_TRY(ensure_workspace(cx, *R.pb, R.o.restart));
+        R.t0 = std::chrono::steady_clock::now();
+        R.st = fsi_solve_stats();
+        // every problem stream starts after the work queued on the caller's stream
+        FSI_CUDA(cudaEventRecord(cx.ev_in, user));
+        FSI_CUDA(cudaStreamWaitEvent(R.pb->stream, cx.ev_in, 0));
+    }
+    fsi_status err = FSI_OK;
+    std::vector<char> residual_next(runs.size(), 0);
+    while (err == FSI_OK) {
+        bool any = false;
+        for (size_t i = 0; i < runs.size(); ++i) {
+            Run &R = runs[i];
+            if (R.phase == Run::DONE) continue;
+            any = true;
+            cx.stream = R.pb->stream;
+            fsi_status e = residual_next[i] ? enqueue_end_cycle(cx, R) : enqueue<T>(cx, R);
+            if (e != FSI_OK) { err = e; break; }
+        }
+        cx.stream = user;
+        if (!any || err != FSI_OK) break;
+        for (auto &R : runs)
+            if (R.phase != Run::DONE) {
+                cudaError_t ce = cudaStreamSynchronize(R.pb->stream);
+                if (ce != cudaSuccess) {
+                    set_error(std::string("solve stream: ") + cudaGetErrorString(ce));
+                    err = FSI_ERR_CUDA;
+                }
+            }
+        if (err != FSI_OK) break;
+        for (size_t i = 0; i < runs.size(); ++i) {
+            Run &R = runs[i];
+            if (R.phase == Run::DONE) continue;
+            cx.stream = R.pb->stream;
+            if (residual_next[i]) {
+                // a cycle ended: hs[6] holds the new true residual
+                residual_next[i] = 0;
+                R.st.cycles++;
+                R.beta = std::sqrt(R.pb->h_scal[6]);
+                if (R.beta > R.o.rtol * R.bnorm && R.its < R.o.max_iters && std::isfinite(R.beta))
+                    R.phase = Run::CYCLE;
+                else
+                    finish(R, FSI_OK);
+                continue;
+            }
+            bool end_cycle = false;
+            fsi_status e = advance(cx, R, end_cycle);
+            if (e != FSI_OK) { err = e; break; }
+            if (end_cycle) residual_next[i] = 1;
+        }
+        cx.stream = user;
+    }
+    cx.stream = user;
+    for (auto &R : runs) {
+        FSI_CUDA(cudaEventRecord(cx.ev_out, R.pb->stream));
+        FSI_CUDA(cudaStreamWaitEvent(user, cx.ev_out, 0));
+        if (R.phase != Run::DONE) finish(R, err == FSI_OK ? FSI_ERR_STATE : err);
+    }
+    if (!cx.ev_marks.empty()) {
+        for (auto &R : runs) cudaStreamSynchronize(R.pb->stream);
+        collect_marks(cx);
+    }
+    return err;
 }
 
 fsi_status check_opts(const fsi_solve_opts *o) {
@@ -488,6 +616,8 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
         return FSI_OK;
     }
     RefTables ref = make_ref_tables(d.dim);
+    FSI_CUDA(cudaStreamCreateWithFlags(&pb.stream, cudaStreamNonBlocking));
+    FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&pb.h_scal), 16 * 8));
     for (int l = 0; l < L; ++l) {
         LevelHost &H = pb.host[l];
         LevelDev &D = pb.dev[l];
@@ -760,30 +890,25 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     return FSI_OK;
 }
 
+static fsi_status solve_runs(Context &cx, std::vector<Run> &runs) {
+    fsi_status s = (cx.precision != FSI_FP64) ? run_batch<float>(cx, runs) : run_batch<double>(cx, runs);
+    if (s != FSI_OK) return s;
+    fsi_status worst = FSI_OK;
+    for (auto &R : runs)
+        if (R.status != FSI_OK && worst == FSI_OK) worst = R.status;
+    return worst;
+}
+
 static fsi_status solve_one(Context &cx, Problem &pb, const double *b, double *x, const fsi_solve_opts *o,
                             fsi_solve_stats *st, bool tr) {
-    auto t0 = std::chrono::steady_clock::now();
-    fsi_solve_stats local;
-    // the solve runs on the context's own non-blocking stream (graph capture
-    // is not possible on a legacy default stream), ordered after the work
-    // already queued on the caller's stream and before anything queued later
-    cudaStream_t user = cx.stream;
-    FSI_CUDA(cudaEventRecord(cx.ev_in, user));
-    FSI_CUDA(cudaStreamWaitEvent(cx.work, cx.ev_in, 0));
-    cx.stream = cx.work;
-    fsi_status s = (cx.precision != FSI_FP64) ? fgmres<float>(cx, pb, b, x, *o, local, tr)
-                                               : fgmres<double>(cx, pb, b, x, *o, local, tr);
-    cx.stream = user;
-    FSI_CUDA(cudaEventRecord(cx.ev_out, cx.work));
-    FSI_CUDA(cudaStreamWaitEvent(user, cx.ev_out, 0));
-    auto t1 = std::chrono::steady_clock::now();
-    local.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    if (!cx.ev_marks.empty()) {
-        cudaStreamSynchronize(cx.stream);
-        collect_marks(cx);
-    }
-    if (s != FSI_OK) local.status = s;
-    if (st) *st = local;
+    std::vector<Run> runs(1);
+    runs[0].pb = &pb;
+    runs[0].b = b;
+    runs[0].x = x;
+    runs[0].tr = tr;
+    runs[0].o = *o;
+    fsi_status s = solve_runs(cx, runs);
+    if (st) *st = runs[0].st;
     return s;
 }
 
@@ -807,14 +932,18 @@ fsi_status fsi_solve_batched(fsi_ctx *ctx, const double *const *b, double *const
     FSI_TRY(check_opts(opts));
     if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
     DeviceGuard guard(cx->device);
-    fsi_status worst = FSI_OK;
+    std::vector<Run> runs(cx->probs.size());
     for (size_t i = 0; i < cx->probs.size(); ++i) {
         if (!b[i] || !x[i]) { set_error("NULL vector in batch"); return FSI_ERR_ARG; }
-        fsi_status s = solve_one(*cx, cx->probs[i], b[i], x[i], opts, st ? &st[i] : nullptr, false);
-        if (s == FSI_ERR_CUDA || s == FSI_ERR_ALLOC || s == FSI_ERR_ARG) return s;
-        if (s != FSI_OK && worst == FSI_OK) worst = s;
+        runs[i].pb = &cx->probs[i];
+        runs[i].b = b[i];
+        runs[i].x = x[i];
+        runs[i].o = *opts;
     }
-    return worst;
+    fsi_status s = solve_runs(*cx, runs);
+    if (st)
+        for (size_t i = 0; i < runs.size(); ++i) st[i] = runs[i].st;
+    return s;
 }
 
 fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *lambda, double *dA_vals,
@@ -990,7 +1119,16 @@ void fsi_destroy(fsi_ctx *ctx) {
         collect_marks(*cx);
         for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
         cx->ev_pool.clear();
-        for (auto &pb : cx->probs) drop_graphs(pb);
+        for (auto &pb : cx->probs) {
+            drop_graphs(pb);
+            if (pb.stream) {
+                cudaStreamSynchronize(pb.stream);
+                cudaStreamDestroy(pb.stream);
+                pb.stream = nullptr;
+            }
+            if (pb.h_scal) cudaFreeHost(pb.h_scal);
+            pb.h_scal = nullptr;
+        }
         if (cx->work) cudaStreamSynchronize(cx->work);
         cx->probs.clear();
         cx->flags.release();

@@ -105,6 +105,8 @@ struct Problem {
     DevBuf V, Z, H, g, cs, sn, y, w, rvec, xwork, partials, scal, h1, h2;
     // one CUDA graph per Arnoldi step j (index 0: forward, 1: transposed)
     std::vector<cudaGraphExec_t> graphs[2];
+    cudaStream_t stream = nullptr;   // the problem's own solve stream
+    double *h_scal = nullptr;        // pinned scalars of the running solve
     std::vector<int64_t> graph_kernels[2];
 };
 
