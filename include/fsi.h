@@ -178,6 +178,25 @@ fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x
 fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
                               int transpose);
 
+/* fsi_apply_smoother_noalloc -- the same y = P2^{-1} r as fsi_apply_smoother,
+ * for callers that cannot allocate GPU memory at call time (for example code
+ * running under a memory pool or allocator that forbids cudaMalloc/cudaFree
+ * after start-up, or a real-time loop that must not block on the driver's
+ * allocator).  fsi_apply_smoother allocates two working vectors per call;
+ * this variant allocates nothing: its working vectors live in one file-scope
+ * device array of the library holding at most FSI_NOALLOC_MAX_DOFS entries
+ * per vector (2 x 2^21 float64 = 32 MiB, reserved on every GPU that loads the
+ * library until the process exits).  Levels with more dofs are rejected with
+ * FSI_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.  Every call reuses the
+ * same array, so calls that may overlap on the GPU (different contexts,
+ * streams or threads without ordering between them) race; calls issued on
+ * one stream are ordered.  The paper has no counterpart to this entry point. */
+#define FSI_NOALLOC_MAX_DOFS 2097152
+fsi_status fsi_apply_smoother_noalloc(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
+                                      int transpose);
+
 /* z = M^{-1} v: one V-cycle from zero on the fine level (transpose != 0: the
  * transposed cycle). */
 fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, int transpose);

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_ALLOC", 4: "ERR_ZE
 EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solve_batched",
             "fsi_adjoint", "fsi_get_sizes", "fsi_get_dof_map", "fsi_get_matrix", "fsi_get_transfer",
             "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
-            "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_destroy", "fsi_last_error"]
+            "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_apply_smoother_noalloc",
+            "fsi_destroy", "fsi_last_error"]
 
 
 class FSIError(RuntimeError):
@@ -99,6 +100,7 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     lib.fsi_setup_host_only.argtypes = [C.POINTER(Problem_t), C.POINTER(HierOpts_t), I, C.POINTER(P)]
     lib.fsi_get_pattern.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
     lib.fsi_profile.argtypes = [P, I, C.POINTER(D)]
+    lib.fsi_apply_smoother_noalloc.argtypes = [P, I, I, P, P, I]
     lib.fsi_destroy.argtypes = [P]
     lib.fsi_destroy.restype = None
     lib.fsi_last_error.restype = C.c_char_p
@@ -303,6 +305,13 @@ class FSISolver:
         import torch
         y = torch.empty_like(r)
         _check(load_library().fsi_apply_smoother(self.ctx, prob, level, _dptr(r), _dptr(y), int(transpose)))
+        return y
+
+    def apply_smoother_noalloc(self, level, r, y, transpose=False, prob=0):
+        """y = P2^{-1} r into the caller's CUDA tensor y, with no allocation by
+        the library (working vectors in its static device array)."""
+        _check(load_library().fsi_apply_smoother_noalloc(self.ctx, prob, level, _dptr(r), _dptr(y),
+                                                          int(transpose)))
         return y
 
     def apply_vcycle(self, v, transpose=False, prob=0):

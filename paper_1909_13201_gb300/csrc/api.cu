@@ -1082,6 +1082,76 @@ fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x
     return FSI_OK;
 }
 
+}  // extern "C"
+
+// Working vectors of fsi_apply_smoother_noalloc: a file-scope device array
+// (2 x FSI_NOALLOC_MAX_DOFS float64), shared by every call in the process.
+static __device__ __align__(256) double g_noalloc_scratch[2 * (size_t)FSI_NOALLOC_MAX_DOFS];
+
+namespace fsi {
+namespace {
+// device address of g_noalloc_scratch per device, looked up on first use
+// with that device current (the host-side symbol is not a device address)
+constexpr int kMaxDevices = 64;
+double *g_noalloc_addr[kMaxDevices] = {nullptr};
+
+fsi_status noalloc_scratch(int device, double **out) {
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("device index out of range for the no-alloc scratch table");
+        return FSI_ERR_ARG;
+    }
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        FSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status apply_smoother_noalloc_t(Context &cx, LevelDev &L, const double *r, double *y, int tr, double *scratch) {
+    cudaStream_t s = cx.stream;
+    T *rt = reinterpret_cast<T *>(scratch);
+    T *yt = reinterpret_cast<T *>(scratch + FSI_NOALLOC_MAX_DOFS);
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f64_f32(r, reinterpret_cast<float *>(rt), L.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(rt, r, (size_t)L.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaMemsetAsync(yt, 0, (size_t)L.n * sizeof(T), s));   // the array keeps the last call's data
+    const double om = cx.omega;
+    cx.omega = 1.0;   // plain P2^{-1} r
+    fsi_status st = smooth_apply<T>(cx, L, rt, yt, tr != 0);
+    cx.omega = om;
+    FSI_TRY(st);
+    if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(yt), y, L.n, s));
+    else FSI_CUDA(cudaMemcpyAsync(y, yt, (size_t)L.n * 8, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+}  // namespace
+}  // namespace fsi
+
+extern "C" {
+
+fsi_status fsi_apply_smoother_noalloc(fsi_ctx *ctx, int prob, int level, const double *r, double *y, int transpose) {
+    g_last_error.clear();
+    Problem *pb = get_prob(ctx, prob, level);
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!pb || level < 1 || !r || !y) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    LevelDev &L = pb->dev[level];
+    if (L.n > FSI_NOALLOC_MAX_DOFS) {
+        set_error("level has " + std::to_string(L.n) + " dofs; fsi_apply_smoother_noalloc supports at most " +
+                  std::to_string((long long)FSI_NOALLOC_MAX_DOFS));
+        return FSI_ERR_ARG;
+    }
+    DeviceGuard guard(cx->device);
+    double *scratch = nullptr;
+    FSI_TRY(noalloc_scratch(cx->device, &scratch));
+    return cx->precision != FSI_FP64 ? apply_smoother_noalloc_t<float>(*cx, L, r, y, transpose, scratch)
+                                      : apply_smoother_noalloc_t<double>(*cx, L, r, y, transpose, scratch);
+}
+
 fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y, int transpose) {
     Problem *pb = get_prob(ctx, prob, level);
     Context *cx = reinterpret_cast<Context *>(ctx);
