@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -466,6 +467,7 @@ fsi_status advance(Context &cx, Run &R, bool &end_cycle) {
 template <class T>
 fsi_status run_batch(Context &cx, std::vector<Run> &runs) {
     cudaStream_t user = cx.stream;
+    FSI_CUDA(cudaMemsetAsync(cx.flags.as<int>() + 2, 0, 4, user));   // kernel error word
     for (auto &R : runs) {
         FSI_TRY(ensure_workspace(cx, *R.pb, R.o.restart));
         R.t0 = std::chrono::steady_clock::now();
@@ -528,6 +530,15 @@ fsi_status run_batch(Context &cx, std::vector<Run> &runs) {
     if (!cx.ev_marks.empty()) {
         for (auto &R : runs) cudaStreamSynchronize(R.pb->stream);
         collect_marks(cx);
+    }
+    if (err == FSI_OK) {
+        int word = 0;
+        FSI_CUDA(cudaMemcpyAsync(&word, cx.flags.as<int>() + 2, 4, cudaMemcpyDeviceToHost, user));
+        FSI_CUDA(cudaStreamSynchronize(user));
+        if (word) {
+            set_error("a staged block copy did not complete in time (kernel error word " + std::to_string(word) + ")");
+            err = FSI_ERR_CUDA;
+        }
     }
     return err;
 }
@@ -741,6 +752,45 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             D.n_items = (int64_t)it.size() / 4;
             FSI_TRY(upload(D.items, it.data(), it.size() * 4, s));
         }
+        // staged-apply items (mixed modes): rows of one block whose stored
+        // inverse fits one 64 KB shared-memory stage; enough items to give
+        // every SM several
+        D.n_titems = 0;
+        // staged apply configuration: FSI_TMA="stages,stage_kb,ctas_per_sm" (0 disables)
+        // (measured slower than the register-streaming apply on GB300: opt-in only)
+        int tma_on = 0, t_st = 3, t_kb = 32, t_cps = 2;
+        if (const char *e = getenv("FSI_TMA")) {
+            if (e[0] != '0') {
+                tma_on = 1;
+                sscanf(e, "%d,%d,%d", &t_st, &t_kb, &t_cps);
+            }
+        }
+        if (store != 0 && tma_on) {
+            D.tma_stages = t_st;
+            D.tma_stage_bytes = t_kb * 1024;
+            const int64_t stage_bytes = D.tma_stage_bytes;
+            const int64_t want = 4 * (int64_t)cx.num_sms;
+            const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
+            std::vector<int32_t> it;
+            for (int64_t j = 0; j < D.n_blocks; ++j) {
+                const int nj = (int)(D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
+                const int64_t row_bytes = (int64_t)((nj + VW - 1) / VW * VW) * (int64_t)isz;
+                int chunk = (int)std::min<int64_t>(nj, stage_bytes / row_bytes);
+                chunk = std::min(chunk, (int)((nj + split - 1) / split));
+                chunk = std::max(4, (chunk + 3) / 4 * 4);
+                chunk = (int)std::min<int64_t>(chunk, stage_bytes / row_bytes);
+                for (int r0 = 0; r0 < nj; r0 += chunk) {
+                    it.push_back((int32_t)j);
+                    it.push_back(r0);
+                    it.push_back(std::min(nj, r0 + chunk));
+                    it.push_back(0);
+                }
+            }
+            D.n_titems = (int64_t)it.size() / 4;
+            FSI_TRY(upload(D.titems, it.data(), it.size() * 4, s));
+            D.tma_grid = (int64_t)cx.num_sms * t_cps;
+        }
+        D.err = cx.flags.as<int>() + 2;
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
         FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
         int flag = 0;

@@ -84,6 +84,11 @@ struct LevelDev {
     int inv_store = 0;                          // 0 float64, 1 float32, 2 float16 + row scale
     int64_t n_items = 0;
     DevBuf items;                               // int4 (block, row begin, row end, 0) apply work items
+    int64_t n_titems = 0;                       // staged (TMA) apply: block items of <= 64 KB each
+    DevBuf titems;
+    int64_t tma_grid = 0;                       // persistent CTAs
+    int tma_stages = 3, tma_stage_bytes = 64 * 1024;
+    int *err = nullptr;                         // context error word (bit 2: staged-copy wait timed out)
     int64_t n_jac = 0;
     DevBuf jac_idx, jac_inv;                    // int32, working precision 1/diag
     // V-cycle vectors in working precision

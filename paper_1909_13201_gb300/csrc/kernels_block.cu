@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "context.h"
@@ -170,6 +171,21 @@ __device__ __forceinline__ typename Vec<T>::type ld_stream(const typename Vec<T>
     return __ldcs(p);   // streaming: read once, evict first
 }
 
+// Sum 4 per-lane row partials over the warp with 6 shuffles (a transposing
+// butterfly): afterwards lane 8 q holds the total of row q (q = 0..3).
+template <class T>
+__device__ __forceinline__ T warp_reduce4(const T (&a)[4], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    const T s0 = b4 ? a[0] : a[2], s1 = b4 ? a[1] : a[3];
+    const T k0 = (b4 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const T k1 = (b4 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+    T v = (b3 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b3 ? k0 : k1, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 constexpr int APPLY_THREADS = 128;
 constexpr int MAX_BLOCK = 1024;
 constexpr int RPW = 4;          // rows per warp iteration (independent 16-byte loads in flight)
@@ -223,17 +239,9 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_kernel(const int4 *
             for (int q = 0; q < RPW; ++q)
                 if (i + q < r1) a[q] += dotv(m[q], rc);
         }
-#pragma unroll
-        for (int q = 0; q < RPW; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
-        if (lane < RPW && i + lane < r1) {
-            T v = a[0];
-#pragma unroll
-            for (int q = 1; q < RPW; ++q)
-                if (lane == q) v = a[q];
-            atomicAdd(&x[blk_idx[s0 + i + lane]], omega * blk_w[s0 + i + lane] * v);
-        }
+        const T v = warp_reduce4<T>(a, lane);
+        const int q = lane >> 3;
+        if ((lane & 7) == 0 && i + q < r1) atomicAdd(&x[blk_idx[s0 + i + q]], omega * blk_w[s0 + i + q] * v);
     }
 }
 
@@ -282,6 +290,7 @@ __device__ __forceinline__ float dot8(const uint4 &m, const float4 &a, const flo
     return f0.x * a.x + f0.y * a.y + f1.x * a.z + f1.y * a.w + f2.x * b.x + f2.y * b.y + f3.x * b.z + f3.y * b.w;
 }
 
+template <int HR>
 __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4 *__restrict__ items,
                                                                       const int32_t *__restrict__ blk_ptr,
                                                                       const int32_t *__restrict__ blk_idx,
@@ -313,32 +322,91 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4
     const int nv = ld / 8;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     constexpr int NW = APPLY_THREADS / 32;
-    for (int i = r0 + warp * RPW; i < r1; i += NW * RPW) {
-        float a[RPW];
+    for (int i = r0 + warp * HR; i < r1; i += NW * HR) {
+        float a[HR];
 #pragma unroll
-        for (int q = 0; q < RPW; ++q) a[q] = 0.0f;
+        for (int q = 0; q < HR; ++q) a[q] = 0.0f;
         for (int c = lane; c < nv; c += 32) {
             const float4 ra = rv[2 * c], rb = rv[2 * c + 1];
-            uint4 m[RPW];
+            uint4 m[HR];
 #pragma unroll
-            for (int q = 0; q < RPW; ++q)
+            for (int q = 0; q < HR; ++q)
                 if (i + q < r1) m[q] = __ldcs(M + (size_t)(i + q) * nv + c);
 #pragma unroll
-            for (int q = 0; q < RPW; ++q)
+            for (int q = 0; q < HR; ++q)
                 if (i + q < r1) a[q] += dot8(m[q], ra, rb);
         }
-#pragma unroll
-        for (int q = 0; q < RPW; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
-        if (lane < RPW && i + lane < r1) {
-            float v = a[0];
-#pragma unroll
-            for (int q = 1; q < RPW; ++q)
-                if (lane == q) v = a[q];
-            const int g = s0 + i + lane;
+        static_assert(HR == 4, "the transposing reduction sums 4 rows");
+        const float v = warp_reduce4<float>(a, lane);
+        const int q = lane >> 3;
+        if ((lane & 7) == 0 && i + q < r1) {
+            const int g = s0 + i + q;
             atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
         }
+    }
+}
+
+// Blocks of at most 256 dofs (every 2D block): each lane owns one 16-byte
+// chunk of a row, so the loads of a 4-row group are one uint4 per lane and
+// row.  The first group's loads are issued before the residual gather (the
+// HBM and L2 latencies overlap) and the next group's loads are in flight
+// while the current group is reduced and scattered.
+__global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_pipe_kernel(const int4 *__restrict__ items,
+                                                                           const int32_t *__restrict__ blk_ptr,
+                                                                           const int32_t *__restrict__ blk_idx,
+                                                                           const int64_t *__restrict__ blk_off,
+                                                                           const float *__restrict__ blk_w,
+                                                                           const __half *__restrict__ inv,
+                                                                           const float *__restrict__ scale,
+                                                                           const int32_t *__restrict__ jac_idx,
+                                                                           const float *__restrict__ jac_inv,
+                                                                           const float *__restrict__ r,
+                                                                           float *__restrict__ x, float omega) {
+    __shared__ __align__(16) float rs[256];
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, r0 = it.y, r1 = it.z;
+    if (blk < 0) {
+        for (int k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+            const int i = jac_idx[k];
+            x[i] += omega * r[i] * jac_inv[k];
+        }
+        return;
+    }
+    const int s0 = blk_ptr[blk];
+    const int n = blk_ptr[blk + 1] - s0;
+    const int ld = (n + 7) & ~7;
+    const int nv = ld / 8;                      // <= 32
+    const uint4 *M = reinterpret_cast<const uint4 *>(inv + blk_off[blk]);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int NW = APPLY_THREADS / 32;
+    const bool col_ok = lane < nv;
+    int i = r0 + warp * 4;
+    uint4 m[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        m[q] = (col_ok && i + q < r1) ? __ldcs(M + (size_t)(i + q) * nv + lane) : make_uint4(0, 0, 0, 0);
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) rs[k] = (k < n) ? r[blk_idx[s0 + k]] : 0.0f;
+    __syncthreads();
+    const float4 *rv = reinterpret_cast<const float4 *>(rs);
+    const float4 ra = col_ok ? rv[2 * lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 rb = col_ok ? rv[2 * lane + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (; i < r1; i += NW * 4) {
+        const int in = i + NW * 4;
+        uint4 mn[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            mn[q] = (col_ok && in + q < r1) ? __ldcs(M + (size_t)(in + q) * nv + lane) : make_uint4(0, 0, 0, 0);
+        float a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = dot8(m[q], ra, rb);
+        const float v = warp_reduce4<float>(a, lane);
+        const int q = lane >> 3;
+        if ((lane & 7) == 0 && i + q < r1) {
+            const int g = s0 + i + q;
+            atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
+        }
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) m[qq] = mn[qq];
     }
 }
 
@@ -374,6 +442,216 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const in
         float acc = 0.0f;
         for (int i = 0; i < n; ++i) acc += __half2float(M[(size_t)i * ld + j]) * rs[i];
         atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent apply with TMA bulk staging (mixed modes, float32 vectors).
+// One CTA per SM walks the work items item = blockIdx.x + k gridDim.x.  The
+// rows of each item's inverse are contiguous in HBM (n_rows x ld entries,
+// rows padded to 16 bytes), so one cp.async.bulk copy moves them into a
+// TMA_STAGES-deep shared-memory ring, completing on an mbarrier; while item k
+// is computed from shared memory the copies of items k+1 .. k+STAGES-1 are in
+// flight, and the residual entries of item k+1 are gathered into registers.
+// Every mbarrier wait is bounded: on time-out the kernel sets bit 2 of *err,
+// waits (bounded) for its own copies still in flight and returns.
+constexpr int TMA_THREADS = 256;
+constexpr uint32_t TMA_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < TMA_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <class S> struct StoreT;
+template <> struct StoreT<__half> { static constexpr int esize = 2, per16 = 8; };
+template <> struct StoreT<float> { static constexpr int esize = 4, per16 = 4; };
+
+// dot of one 16-byte chunk of a stored row with 16 bytes' worth of rs
+__device__ __forceinline__ float chunk_dot(const uint4 &m, const float *rs, const __half *) {
+    const float4 a = reinterpret_cast<const float4 *>(rs)[0], b = reinterpret_cast<const float4 *>(rs)[1];
+    return dot8(m, a, b);
+}
+__device__ __forceinline__ float chunk_dot(const uint4 &m, const float *rs, const float *) {
+    const float4 a = reinterpret_cast<const float4 *>(rs)[0];
+    const float4 mm = *reinterpret_cast<const float4 *>(&m);
+    return mm.x * a.x + mm.y * a.y + mm.z * a.z + mm.w * a.w;
+}
+
+struct TmaItemInfo {
+    int blk, r0, r1, s0, n, ld;
+    const char *src;
+    uint32_t bytes;
+};
+
+template <class S>
+__device__ __forceinline__ TmaItemInfo tma_item(const int4 *items, int it, const int32_t *blk_ptr,
+                                                const int64_t *blk_off, const S *inv) {
+    TmaItemInfo t;
+    const int4 v = items[it];
+    t.blk = v.x;
+    t.r0 = v.y;
+    t.r1 = v.z;
+    t.s0 = blk_ptr[t.blk];
+    t.n = blk_ptr[t.blk + 1] - t.s0;
+    t.ld = (t.n + StoreT<S>::per16 - 1) / StoreT<S>::per16 * StoreT<S>::per16;
+    t.src = reinterpret_cast<const char *>(inv + blk_off[t.blk]) + (size_t)t.r0 * t.ld * StoreT<S>::esize;
+    t.bytes = (uint32_t)((size_t)(t.r1 - t.r0) * t.ld * StoreT<S>::esize);
+    return t;
+}
+
+template <class S, int TMA_STAGES>
+__global__ void __launch_bounds__(TMA_THREADS) block_apply_tma_kernel(
+    int TMA_STAGE_BYTES, const int4 *__restrict__ items, int n_items, const int32_t *__restrict__ blk_ptr,
+    const int32_t *__restrict__ blk_idx, const int64_t *__restrict__ blk_off, const float *__restrict__ blk_w,
+    const S *__restrict__ inv, const float *__restrict__ scale, const int32_t *__restrict__ jac_idx,
+    const float *__restrict__ jac_inv, int n_jac, const float *__restrict__ r, float *__restrict__ x, float omega,
+    int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *stage = smem;                                            // [STAGES][STAGE_BYTES]
+    float *rsbuf = reinterpret_cast<float *>(smem + TMA_STAGES * TMA_STAGE_BYTES);   // [2][MAX_BLOCK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rsbuf + 2 * MAX_BLOCK);    // [STAGES]
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    constexpr int NW = TMA_THREADS / 32;
+    constexpr int PER16 = StoreT<S>::per16;
+    if (tid == 0) {
+        for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: the first STAGES items of this CTA
+    if (tid == 0) {
+        for (int q = 0; q < TMA_STAGES; ++q) {
+            const int it = blockIdx.x + q * gridDim.x;
+            if (it >= n_items) break;
+            const TmaItemInfo t = tma_item<S>(items, it, blk_ptr, blk_off, inv);
+            mbar_expect_tx(&bar[q], t.bytes);
+            tma_load(stage + (size_t)q * TMA_STAGE_BYTES, t.src, t.bytes, &bar[q]);
+        }
+    }
+    // residual entries of the first item into registers
+    constexpr int GATHER = MAX_BLOCK / TMA_THREADS;
+    float gv[GATHER];
+    int cur = blockIdx.x;
+    if (cur < n_items) {
+        const TmaItemInfo t = tma_item<S>(items, cur, blk_ptr, blk_off, inv);
+#pragma unroll
+        for (int q = 0; q < GATHER; ++q) {
+            const int i = tid + q * TMA_THREADS;
+            gv[q] = i < t.n ? r[blk_idx[t.s0 + i]] : 0.0f;
+        }
+    }
+    bool ok = true;
+    int k = 0;
+    for (; cur < n_items; cur += gridDim.x, ++k) {
+        const int sidx = k % TMA_STAGES;
+        const uint32_t parity = (uint32_t)((k / TMA_STAGES) & 1);
+        const TmaItemInfo t = tma_item<S>(items, cur, blk_ptr, blk_off, inv);
+        float *rs = rsbuf + (k & 1) * MAX_BLOCK;
+#pragma unroll
+        for (int q = 0; q < GATHER; ++q) {
+            const int i = tid + q * TMA_THREADS;
+            if (i < t.ld) rs[i] = gv[q];
+        }
+        // prefetch the next item's residual entries while this one is computed
+        const int nxt = cur + gridDim.x;
+        if (nxt < n_items) {
+            const TmaItemInfo tn = tma_item<S>(items, nxt, blk_ptr, blk_off, inv);
+#pragma unroll
+            for (int q = 0; q < GATHER; ++q) {
+                const int i = tid + q * TMA_THREADS;
+                gv[q] = i < tn.n ? r[blk_idx[tn.s0 + i]] : 0.0f;
+            }
+        }
+        // every thread waits (bounded) for stage sidx; the time-out decision is
+        // made CTA-uniform by the barrier reduction, so no thread is left
+        // waiting at a barrier another thread skipped
+        const int landed = mbar_wait(&bar[sidx], parity) ? 1 : 0;
+        if (!__syncthreads_and(landed)) {       // also orders the rs writes
+            ok = false;
+            break;
+        }
+        const uint4 *M = reinterpret_cast<const uint4 *>(stage + (size_t)sidx * TMA_STAGE_BYTES);
+        const int nv = t.ld / PER16;            // 16-byte chunks per row
+        const int rows = t.r1 - t.r0;
+        for (int i = warp * RPW; i < rows; i += NW * RPW) {
+            float a[RPW];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) a[q] = 0.0f;
+            for (int c = lane; c < nv; c += 32) {
+                const float *rc = rs + c * PER16;
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (i + q < rows) a[q] += chunk_dot(M[(size_t)(i + q) * nv + c], rc, (const S *)nullptr);
+            }
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+            if (lane < RPW && i + lane < rows) {
+                float v = a[0];
+#pragma unroll
+                for (int q = 1; q < RPW; ++q)
+                    if (lane == q) v = a[q];
+                const int g = t.s0 + t.r0 + i + lane;
+                const float sc = scale ? scale[g] : 1.0f;
+                atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * sc * v);
+            }
+        }
+        __syncthreads();                        // every warp is done with stage sidx
+        if (tid == 0) {
+            const int refill = cur + TMA_STAGES * gridDim.x;
+            if (refill < n_items) {
+                const TmaItemInfo tr = tma_item<S>(items, refill, blk_ptr, blk_off, inv);
+                mbar_expect_tx(&bar[sidx], tr.bytes);
+                tma_load(stage + (size_t)sidx * TMA_STAGE_BYTES, tr.src, tr.bytes, &bar[sidx]);
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(err, 2);
+        // drain: wait (bounded) for the copies this CTA issued and has not consumed
+        for (int q = 0; q < TMA_STAGES; ++q) {
+            const int kk = k + q;
+            const int it = blockIdx.x + kk * gridDim.x;
+            if (it >= n_items) break;
+            mbar_wait(&bar[kk % TMA_STAGES], (uint32_t)((kk / TMA_STAGES) & 1));
+        }
+        return;
+    }
+    // Jacobi rows (u^s and fixed dofs): grid-stride over the list
+    for (int q = blockIdx.x * TMA_THREADS + tid; q < n_jac; q += gridDim.x * TMA_THREADS) {
+        const int i = jac_idx[q];
+        x[i] += omega * r[i] * jac_inv[q];
     }
 }
 
@@ -555,6 +833,40 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
         set_error("Schwarz block larger than the apply kernel's staging buffer");
         return FSI_ERR_ARG;
     }
+    if (std::is_same<T, float>::value && !transpose && lev.n_titems > 0 && (lev.inv_store == 1 || lev.inv_store == 2)) {
+        const float *rf = reinterpret_cast<const float *>(r);
+        float *xf = reinterpret_cast<float *>(x);
+        const int stages = lev.tma_stages, sbytes = lev.tma_stage_bytes;
+        const size_t smem = (size_t)stages * sbytes + 2 * MAX_BLOCK * sizeof(float) + stages * sizeof(uint64_t);
+        const unsigned grid = (unsigned)std::min<int64_t>(lev.n_titems, lev.tma_grid);
+#define FSI_TMA_LAUNCH(ST, NS, INVP, SCALE)                                                                     \
+    do {                                                                                                        \
+        FSI_CUDA(cudaFuncSetAttribute(block_apply_tma_kernel<ST, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem));                                                              \
+        block_apply_tma_kernel<ST, NS><<<grid, TMA_THREADS, smem, s>>>(                                         \
+            sbytes, lev.titems.as<int4>(), (int)lev.n_titems, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), \
+            lev.blk_off.as<int64_t>(), lev.blk_w.as<float>(), INVP, SCALE, lev.jac_idx.as<int32_t>(),           \
+            lev.jac_inv.as<float>(), (int)lev.n_jac, rf, xf, (float)omega, lev.err);                            \
+    } while (0)
+#define FSI_TMA_STAGES_SWITCH(ST, INVP, SCALE)        \
+    switch (stages) {                                 \
+        case 2: FSI_TMA_LAUNCH(ST, 2, INVP, SCALE); break; \
+        case 3: FSI_TMA_LAUNCH(ST, 3, INVP, SCALE); break; \
+        case 4: FSI_TMA_LAUNCH(ST, 4, INVP, SCALE); break; \
+        case 6: FSI_TMA_LAUNCH(ST, 6, INVP, SCALE); break; \
+        default: FSI_TMA_LAUNCH(ST, 8, INVP, SCALE); break; \
+    }
+        if (lev.inv_store == 2) {
+            FSI_TMA_STAGES_SWITCH(__half, lev.inv.as<__half>(), lev.inv_scale.as<float>());
+        } else {
+            FSI_TMA_STAGES_SWITCH(float, lev.inv.as<float>(), (const float *)nullptr);
+        }
+#undef FSI_TMA_STAGES_SWITCH
+#undef FSI_TMA_LAUNCH
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+        return FSI_OK;
+    }
     if (std::is_same<T, float>::value && lev.inv_store == 2) {
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
@@ -563,8 +875,13 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega);
+        else if (lev.max_block <= 256)
+            block_apply_h_pipe_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+                lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
+                lev.jac_inv.as<float>(), rf, xf, (float)omega);
         else
-            block_apply_h_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+            block_apply_h_kernel<4><<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega);
