@@ -28,12 +28,13 @@ from .transfer import prolongation, restriction
 
 
 class Hierarchy:
-    def __init__(self, prob, *, mixed: bool = False, omega: float = 1.0, nu_pre: int = 1,
+    def __init__(self, prob, *, mixed: bool = False, omega: float | None = None, nu_pre: int = 1,
                  nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
                  weighted: bool = True):
         self.prob = prob
         self.mixed = bool(mixed)
         half = mixed == "half"
+        omega = getattr(prob, "omega", 1.0) if omega is None else omega
         self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
         self.wdtype = np.float32 if mixed else np.float64
         self.levels = build_levels(prob)

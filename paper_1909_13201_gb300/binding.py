@@ -172,9 +172,11 @@ class FSISolver:
         except Exception:
             pass
 
-    def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=1.0, nu_pre=1, nu_post=1):
+    def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=None, nu_pre=1, nu_post=1):
         if patch is None:
             patch = self.problems[0].patch
+        if omega is None:
+            omega = getattr(self.problems[0], "omega", 1.0)
         so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post)
         _check(load_library().fsi_setup_smoothers(self.ctx, C.byref(so)))
         self.precision = precision
