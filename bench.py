@@ -163,6 +163,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# GB300 float64 rate (nominal, no measured figure exists on this machine): the
+# outer product and the Gram-Schmidt passes are bound by it, not by HBM
+FP64_NOMINAL_GFLOPS = 1250.0
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -273,6 +278,9 @@ def run_ours(args, rank, world, local):
     achieved = prof["smoother_bytes"] / (sm_ms * 1e-3) / 1e9
     spmv_ms = prof["spmv_ms"] / max(prof["spmv_launches"], 1)
     spmv_gbs = prof["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
+    outer_ms = prof["outer_ms"] / max(prof["outer_launches"], 1)
+    outer_gbs = prof["outer_bytes"] / (outer_ms * 1e-3) / 1e9
+    outer_gflops = 2.0 * prof["outer_fma"] / (outer_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     # ---- end to end through the public call with host buffers (mixed)
     b_pin = torch.from_numpy(b_host).pin_memory()
@@ -323,7 +331,16 @@ def run_ours(args, rank, world, local):
         bstats[:] = sts
 
     solve_batch()
+    ms_batch_fixed = timed(max(2, args.steps // 4), solve_batch)
+    # per size class, keep the fastest Vanka group size (native autotuner)
+    t0 = time.time()
+    tune_cand = (2, 3, 4)
+    chosen, _ = sb.autotune(tune_cand, rtol=RTOL)
+    torch.cuda.synchronize()
+    tune_s = time.time() - t0
+    solve_batch()
     ms_batch = timed(max(2, args.steps // 4), solve_batch)
+    chosen_by_size = {str(q.n_fine): c for q, c in zip(batch, chosen)}
     batch_dofs = sum(int(v.numel()) for v in bb)
     # ---- adjoint: forward solve plus the transposed solve with gradients (128^2)
     pa = I.make_config(4)
@@ -393,6 +410,9 @@ def run_ours(args, rank, world, local):
         "mixed_f32_inverses": {"value": world * n / (ms32 * 1e-3), "ms_per_step": ms32,
                                "iterations": st32.get("iterations")},
         "batched": {"systems": len(batch), "unknowns_total": batch_dofs, "ms_per_batch": ms_batch,
+                    "ms_per_batch_patch3": ms_batch_fixed,
+                    "autotune": {"candidates": list(tune_cand), "chosen_by_n_fine": chosen_by_size,
+                                 "tune_s": tune_s},
                     "solves_per_s": world * len(batch) / (ms_batch * 1e-3),
                     "dof_per_s": world * batch_dofs / (ms_batch * 1e-3),
                     "iterations_min_max": [min(t["iterations"] for t in bstats),
@@ -414,7 +434,11 @@ def run_ours(args, rank, world, local):
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
                      "algorithmic_bytes_per_launch": prof["smoother_bytes"], "mean_launch_ms": sm_ms,
-                     "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms}},
+                     "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms},
+                     "outer_spmv_f64": {"achieved_gbs": outer_gbs, "frac_hbm": outer_gbs / peak,
+                                        "achieved_fp64_gflops": outer_gflops,
+                                        "frac_fp64_nominal": outer_gflops / FP64_NOMINAL_GFLOPS,
+                                        "mean_launch_ms": outer_ms}},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,

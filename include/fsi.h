@@ -140,6 +140,20 @@ fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *l
                        double *dA_vals, double *dmu_s, const fsi_solve_opts *opts,
                        fsi_solve_stats *st);
 
+/* fsi_autotune -- picks the Vanka group size (fsi_smoother_opts.patch) of
+ * every problem (an extension; the paper fixes its blocks by hand).  Problems
+ * of the same size class (dimension, fine size, level count) share one
+ * choice: for the class's first problem and each of the n_cand candidate
+ * sizes (1..16, n_cand <= 8) the smoothers are rebuilt and a solve of
+ * A x = A 1 with opts is timed on the device (the faster of two runs; a
+ * candidate that does not converge counts as infinitely slow).  Afterwards
+ * every problem's smoothers use its class's fastest candidate.  chosen: host
+ * int[n_probs] receives the choice; times_ms (nullable): host
+ * double[n_probs * n_cand], solve time per problem and candidate.  Requires
+ * fsi_setup_smoothers first (precision, omega and smoothing steps are kept). */
+fsi_status fsi_autotune(fsi_ctx *ctx, const int *candidates, int n_cand, const fsi_solve_opts *opts,
+                        int *chosen, double *times_ms);
+
 /* ----------------------------- accessors --------------------------------- */
 
 /* Sizes of level `level` (0 = coarse .. L-1 = fine) of problem `prob`:
@@ -174,6 +188,7 @@ fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_
 /* y = A_l x (float64 operator). */
 fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x, double *y);
 
+
 /* y = P2^{-1} r on level l >= 1 (transpose != 0: P2^{-T} r), Sec. 3.2. */
 fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
                               int transpose);
@@ -205,11 +220,13 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * mode 1: reset the counters and start recording CUDA events around the
  * fine-level smoother apply and fine-level residual SpMV launches of the
  * following solves; mode 0: stop recording; mode 2: read only.
- * out (host, 8 doubles): [0] smoother launches timed, [1] their total ms,
+ * out (host, 12 doubles): [0] smoother launches timed, [1] their total ms,
  * [2] algorithmic bytes per smoother launch (block inverses, index, weight,
  * gather and scatter traffic), [3] SpMV launches timed, [4] their total ms,
  * [5] algorithmic bytes per SpMV launch, [6] kernels launched by the library
- * since the last reset, [7] reserved.  Problem 0. */
+ * since the last reset, [7] outer float64 products w = A z_j timed, [8] their
+ * total ms, [9] algorithmic bytes per product, [10] nonzeros of the fine
+ * operator (one float64 FMA each), [11] reserved.  Problem 0. */
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
 
 /* Host-only inspection context: builds the levels, numbering, operator

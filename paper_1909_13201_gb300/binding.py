@@ -24,7 +24,7 @@ EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solv
             "fsi_adjoint", "fsi_get_sizes", "fsi_get_dof_map", "fsi_get_matrix", "fsi_get_transfer",
             "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
             "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_apply_smoother_noalloc",
-            "fsi_destroy", "fsi_last_error"]
+            "fsi_autotune", "fsi_destroy", "fsi_last_error"]
 
 
 class FSIError(RuntimeError):
@@ -101,6 +101,7 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     lib.fsi_get_pattern.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
     lib.fsi_profile.argtypes = [P, I, C.POINTER(D)]
     lib.fsi_apply_smoother_noalloc.argtypes = [P, I, I, P, P, I]
+    lib.fsi_autotune.argtypes = [P, C.POINTER(I), I, C.POINTER(SolveOpts_t), C.POINTER(I), C.POINTER(D)]
     lib.fsi_destroy.argtypes = [P]
     lib.fsi_destroy.restype = None
     lib.fsi_last_error.restype = C.c_char_p
@@ -234,14 +235,28 @@ class FSISolver:
             _check(s)
         return lam, dA, (dmu.value if want_dmu else None), st.to_dict()
 
+    def autotune(self, candidates=(1, 2, 3), rtol=1e-8, restart=30, max_iters=300):
+        """Per size class, time one solve per candidate Vanka group size and
+        keep the fastest (fsi_autotune).  Returns (chosen[n_probs],
+        times_ms[n_probs][n_cand])."""
+        cand = (C.c_int * len(candidates))(*candidates)
+        n = len(self.problems)
+        chosen = (C.c_int * n)()
+        times = np.zeros(n * len(candidates), np.float64)
+        opts = self._opts(rtol, restart, max_iters, False)
+        _check(load_library().fsi_autotune(self.ctx, cand, len(candidates), C.byref(opts), chosen,
+                                           _ptr(times, C.c_double)))
+        return list(chosen), times.reshape(n, len(candidates))
+
     def profile(self, mode):
         """mode 1 start (reset), 0 stop, 2 read.  Returns the counters of
         fsi_profile as a dict."""
-        out = np.zeros(8, np.float64)
+        out = np.zeros(12, np.float64)
         _check(load_library().fsi_profile(self.ctx, mode, _ptr(out, C.c_double)))
         return {"smoother_launches": int(out[0]), "smoother_ms": out[1], "smoother_bytes": out[2],
                 "spmv_launches": int(out[3]), "spmv_ms": out[4], "spmv_bytes": out[5],
-                "kernel_launches": int(out[6])}
+                "kernel_launches": int(out[6]), "outer_launches": int(out[7]), "outer_ms": out[8],
+                "outer_bytes": out[9], "outer_fma": out[10]}
 
     # ------------------------------------------------------------ accessors
     @property

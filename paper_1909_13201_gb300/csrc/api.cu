@@ -223,6 +223,11 @@ void drop_graphs(Problem &pb) {
         v.clear();
     }
     for (auto &v : pb.graph_kernels) v.clear();
+    for (int d = 0; d < 2; ++d) {
+        if (pb.solve_graph[d]) cudaGraphExecDestroy(pb.solve_graph[d]);
+        pb.solve_graph[d] = nullptr;
+        pb.solve_graph_m[d] = 0;
+    }
 }
 
 fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
@@ -300,7 +305,13 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
         FSI_TRY(vcycle<T>(cx, pb, L - 1, bfine, F.x.as<T>(), tr));
         FSI_TRY(launch_cast_f32_f64(reinterpret_cast<const float *>(F.x.as<T>()), zj, n, s));
     }
-    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w, SPMV_SET, s));
+    // float64 A z_j: the row-scaled systems reach 1e-8 only a little above
+    // their attainable accuracy, so this product keeps full float64 rounding
+    {
+        ProfMark pm(cx, 2, true);
+        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zj, (const double *)nullptr, w,
+                                                    SPMV_SET, s));
+    }
     const int nv = j + 1;
     double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
     FSI_TRY(launch_mdot(V, n, nv, w, n, part, NRED, s));
@@ -629,6 +640,12 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
     RefTables ref = make_ref_tables(d.dim);
     FSI_CUDA(cudaStreamCreateWithFlags(&pb.stream, cudaStreamNonBlocking));
     FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&pb.h_scal), 16 * 8));
+    FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&pb.h_fg), 2 * sizeof(FgState)));
+    pb.h_fg[0] = FgState();
+    pb.h_fg[1] = FgState();
+    FSI_TRY(pb.fg.alloc(sizeof(FgState)));
+    FSI_CUDA(cudaEventCreate(&pb.ev_a));
+    FSI_CUDA(cudaEventCreate(&pb.ev_b));
     for (int l = 0; l < L; ++l) {
         LevelHost &H = pb.host[l];
         LevelDev &D = pb.dev[l];
@@ -685,7 +702,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_TRY(D.x.alloc((size_t)D.n * tsz));
         FSI_TRY(D.r.alloc((size_t)D.n * tsz));
         if (l == 0) continue;
-        build_blocks(H, cx.patch, D.h_blk_ptr, D.h_blk_idx);
+        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx);
         D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
         std::vector<int32_t> bp(D.h_blk_ptr.begin(), D.h_blk_ptr.end());
         std::vector<int64_t> off(D.n_blocks + 1, 0);
@@ -877,7 +894,10 @@ fsi_status fsi_setup_hierarchy(const fsi_problem *probs, int n_probs, const fsi_
     {
         const char *g = getenv("FSI_USE_GRAPHS");
         cx->use_graphs = !(g && g[0] == '0');
+        const char *dl = getenv("FSI_DEVICE_LOOP");
+        cx->device_loop = !(dl && dl[0] == '0');
     }
+    for (auto &c : cx->cap) FSI_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     FSI_TRY(cx->flags.alloc(16));
     cx->probs.resize(n_probs);
     for (int i = 0; i < n_probs; ++i) {
@@ -930,6 +950,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     DeviceGuard guard(cx->device);
     cx->precision = opts->precision;
     cx->patch = opts->patch;
+    for (auto &pb : cx->probs) pb.patch = opts->patch;
     cx->omega = opts->omega;
     cx->nu_pre = opts->nu_pre;
     cx->nu_post = opts->nu_post;
@@ -940,8 +961,309 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     return FSI_OK;
 }
 
+}  // extern "C"
+
+namespace fsi {
+namespace {
+
+// ------------------------------------------------- device-driven FGMRES
+// The whole solve as one CUDA graph: the prologue (||b||, r0 = b - A x0,
+// ||r0||) is followed by a WHILE node over restart cycles whose body starts
+// the basis, runs a nested WHILE node over Arnoldi steps, and ends with
+// x += Z y and the float64 true residual.  The loop conditions are set on
+// the device (fg_start / givens / fg_cycle kernels), so a solve needs no
+// host round trip; the host reads the control block once at the end.  b and
+// x live in fixed per-problem buffers so the graph is captured once per
+// direction and restart length and replayed for any caller pointers.
+
+// one Arnoldi step with the column index on the device (loop body):
+// z_j = M^{-1} v_j and w = A z_j, then a SWITCH node whose case c holds the
+// Gram-Schmidt/Givens kernels instantiated for nv <= nv_class_bound(c)
+// (the case is chosen on the device from fg->k by take_column), so early
+// steps keep the small-register variants instead of the widest one.
+template <class T>
+fsi_status issue_step_dev_head(Context &cx, Problem &pb, bool tr, cudaGraphConditionalHandle sel) {
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    const int L = (int)pb.dev.size();
+    const DevCSR &A = tr ? F.AT : F.A;
+    FgState *fg = pb.fg.as<FgState>();
+    double *V = pb.V.as<double>(), *w = pb.w.as<double>(), *Z = pb.Z.as<double>();
+    double *zf = pb.zbuf.as<double>();
+    FSI_TRY(launch_take_column<double, T>(V, n, fg, F.b.as<T>(), n, s, sel));
+    FSI_TRY(vcycle<T>(cx, pb, L - 1, F.b.as<T>(), F.x.as<T>(), tr));
+    FSI_TRY(launch_store_column<T>(F.x.as<T>(), zf, Z, n, fg, n, s));
+    FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zf, (const double *)nullptr, w, SPMV_SET, s));
+    return FSI_OK;
+}
+
+fsi_status issue_step_dev_tail(Context &cx, Problem &pb, int m, int nv_bound, cudaGraphConditionalHandle loop) {
+    cudaStream_t s = cx.stream;
+    const int64_t n = pb.dev.back().n;
+    FgState *fg = pb.fg.as<FgState>();
+    double *V = pb.V.as<double>(), *H = pb.H.as<double>(), *g = pb.g.as<double>();
+    double *w = pb.w.as<double>(), *scal = pb.scal.as<double>();
+    double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
+    FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NRED, s, fg));
+    FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h1, 0, s, fg));
+    FSI_TRY(launch_update_dot(w, V, n, nv_bound, h1, n, part, NRED, 0, s, fg));
+    FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h2, 0, s, fg));
+    FSI_TRY(launch_update_dot(w, V, n, nv_bound, h2, n, part, NRED, 1, s, fg));
+    FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
+    FSI_TRY(launch_givens(H, m + 1, 0, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s, fg,
+                          loop));
+    FSI_TRY(launch_scale_copy(w, V, scal, 1, n, s, fg, n));
+    return FSI_OK;
+}
+
+// append a conditional node (WHILE or SWITCH with `size` cases) at the
+// capture position of stream s; returns its body graphs
+fsi_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                           unsigned size, cudaGraphNode_t *node, cudaGraph_t *bodies) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    FSI_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) { set_error("stream is not capturing"); return FSI_ERR_STATE; }
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    FSI_CUDA(cudaGraphAddNode(node, g, deps, nullptr, nd, &p));
+    for (unsigned i = 0; i < size; ++i) bodies[i] = p.conditional.phGraph_out[i];
+    FSI_CUDA(cudaStreamUpdateCaptureDependencies(s, node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    const DevCSR &A = tr ? F.AT : F.A;
+    FgState *fg = pb.fg.as<FgState>();
+    double *scal = pb.scal.as<double>(), *r = pb.rvec.as<double>();
+    double *b = pb.bbuf.as<double>(), *x = pb.xbuf.as<double>();
+    cudaStream_t s0 = pb.stream, s1 = cx.cap[0], s2 = cx.cap[1], s3 = cx.cap[2];
+    cudaStream_t saved = cx.stream;
+    cudaGraph_t top = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t cnt[3] = {0, 0, 0};
+    fsi_status st = FSI_OK;
+    int capturing = 0;        // streams in capture, innermost last
+    cudaStream_t active[4] = {s0, s1, s2, s3};
+    auto fail = [&](fsi_status e) {
+        // captures into existing graphs: the bodies belong to their nodes
+        for (int i = capturing - 1; i >= 0; --i) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(active[i], &junk);
+        }
+        cudaGetLastError();
+        if (top) cudaGraphDestroy(top);
+        cx.stream = saved;
+        return e;
+    };
+#define FSI_CAP(...)                                   \
+    do {                                               \
+        st = (__VA_ARGS__);                            \
+        if (st != FSI_OK) return fail(st);             \
+    } while (0)
+#define FSI_CAPCUDA(...)                               \
+    do {                                               \
+        cudaError_t e_ = (__VA_ARGS__);                \
+        if (e_ != cudaSuccess) {                       \
+            set_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+            return fail(FSI_ERR_CUDA);                 \
+        }                                              \
+    } while (0)
+    const int64_t c0 = launches_so_far();
+    FSI_CAPCUDA(cudaGraphCreate(&top, 0));
+    cudaGraphConditionalHandle h_out = 0, h_in = 0;
+    FSI_CAPCUDA(cudaGraphConditionalHandleCreate(&h_out, top, 0, cudaGraphCondAssignDefault));
+    // prologue
+    FSI_CAPCUDA(cudaStreamBeginCaptureToGraph(s0, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = 1;
+    cx.stream = s0;
+    FSI_CAP(norm2(cx, pb, b, n, 5));
+    FSI_CAP(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s0));
+    FSI_CAP(norm2(cx, pb, r, n, 6));
+    FSI_CAP(launch_fg_start(scal, fg, h_out, s0));
+    const int64_t c1 = launches_so_far();
+    // outer loop over restart cycles
+    cudaGraphNode_t w_out = nullptr, w_in = nullptr;
+    cudaGraph_t body_out = nullptr, body_in = nullptr;
+    FSI_CAP(add_conditional(s0, h_out, cudaGraphCondTypeWhile, 1, &w_out, &body_out));
+    FSI_CAPCUDA(cudaGraphConditionalHandleCreate(&h_in, body_out, 0, 0));
+    FSI_CAPCUDA(cudaStreamBeginCaptureToGraph(s1, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = 2;
+    cx.stream = s1;
+    FSI_CAP(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, scal + 6, n, s1, fg, h_in));
+    FSI_CAP(add_conditional(s1, h_in, cudaGraphCondTypeWhile, 1, &w_in, &body_in));
+    // inner loop: Arnoldi steps
+    const int64_t c2 = launches_so_far();
+    FSI_CAPCUDA(cudaStreamBeginCaptureToGraph(s2, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = 3;
+    cx.stream = s2;
+    cudaGraphConditionalHandle h_sel = 0;
+    FSI_CAPCUDA(cudaGraphConditionalHandleCreate(&h_sel, body_in, 0, 0));
+    FSI_CAP(issue_step_dev_head<T>(cx, pb, tr, h_sel));
+    int ncls = 1;
+    while (ncls < NV_CLASSES && nv_class_bound(ncls - 1) < m) ++ncls;    // cases covering nv <= m
+    cudaGraphNode_t w_sel = nullptr;
+    cudaGraph_t cases[NV_CLASSES] = {};
+    FSI_CAP(add_conditional(s2, h_sel, cudaGraphCondTypeSwitch, (unsigned)ncls, &w_sel, cases));
+    int64_t tail_kernels = 0;
+    for (int c = 0; c < ncls; ++c) {
+        const int64_t t0 = launches_so_far();
+        FSI_CAPCUDA(cudaStreamBeginCaptureToGraph(s3, cases[c], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capturing = 4;
+        cx.stream = s3;
+        FSI_CAP(issue_step_dev_tail(cx, pb, m, std::min(nv_class_bound(c), m), h_in));
+        cudaGraph_t g3 = nullptr;
+        FSI_CAPCUDA(cudaStreamEndCapture(s3, &g3));
+        capturing = 3;
+        tail_kernels = launches_so_far() - t0;     // the same count in every case
+    }
+    cx.stream = s2;
+    {
+        cudaGraph_t g2 = nullptr;
+        FSI_CAPCUDA(cudaStreamEndCapture(s2, &g2));
+        capturing = 2;
+    }
+    const int64_t c3 = launches_so_far();
+    // end of a cycle: x += Z y, true residual, restart test
+    cx.stream = s1;
+    FSI_CAP(launch_backsolve(pb.H.as<double>(), m + 1, 0, pb.g.as<double>(), pb.y.as<double>(), s1, fg));
+    FSI_CAP(launch_combine<double>(x, pb.Z.as<double>(), n, 0, pb.y.as<double>(), n, s1, fg));
+    FSI_CAP(launch_spmv<double, double, double>(A, A.val64.as<double>(), x, b, r, SPMV_RESID, s1));
+    FSI_CAP(norm2(cx, pb, r, n, 6));
+    FSI_CAP(launch_fg_cycle(scal, fg, h_out, s1));
+    {
+        cudaGraph_t g1 = nullptr;
+        FSI_CAPCUDA(cudaStreamEndCapture(s1, &g1));
+        capturing = 1;
+    }
+    const int64_t c4 = launches_so_far();
+    {
+        cudaGraph_t g0 = nullptr;
+        FSI_CAPCUDA(cudaStreamEndCapture(s0, &g0));
+        capturing = 0;
+    }
+    cx.stream = saved;
+    FSI_CAPCUDA(cudaGraphInstantiate(&exec, top, 0));
+    cudaGraphDestroy(top);
+#undef FSI_CAP
+#undef FSI_CAPCUDA
+    cnt[0] = c1 - c0;                       // prologue
+    cnt[1] = (c2 - c1) + (c4 - c3);         // per cycle, outside the steps
+    cnt[2] = (c3 - c2) - (int64_t)(ncls - 1) * tail_kernels;   // per Arnoldi step (one case runs)
+    count_launch(-(int)(c4 - c0));          // captured, not run
+    const int d = tr ? 1 : 0;
+    if (pb.solve_graph[d]) cudaGraphExecDestroy(pb.solve_graph[d]);
+    pb.solve_graph[d] = exec;
+    pb.solve_graph_m[d] = m;
+    for (int i = 0; i < 3; ++i) pb.graph_counts[d][i] = cnt[i];
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
+    cudaStream_t user = cx.stream;
+    FSI_CUDA(cudaMemsetAsync(cx.flags.as<int>() + 2, 0, 4, user));   // kernel error word
+    FSI_CUDA(cudaEventRecord(cx.ev_in, user));
+    for (auto &R : runs) {
+        Problem &pb = *R.pb;
+        const int m = R.o.restart;
+        const int d = R.tr ? 1 : 0;
+        const int64_t n = pb.dev.back().n;
+        FSI_TRY(ensure_workspace(cx, pb, m));
+        if (!pb.bbuf.p) {
+            FSI_TRY(pb.bbuf.alloc((size_t)n * 8));
+            FSI_TRY(pb.xbuf.alloc((size_t)n * 8));
+            FSI_TRY(pb.zbuf.alloc((size_t)n * 8));
+        }
+        FSI_CUDA(cudaStreamWaitEvent(pb.stream, cx.ev_in, 0));
+        if (!pb.solve_graph[d] || pb.solve_graph_m[d] != m) FSI_TRY(capture_solve<T>(cx, pb, R.tr, m));
+        R.st = fsi_solve_stats();
+        FgState &in = pb.h_fg[0];
+        in = FgState();
+        in.rtol = R.o.rtol;
+        in.max_iters = R.o.max_iters;
+        in.m = m;
+        cudaStream_t s = pb.stream;
+        FSI_CUDA(cudaEventRecord(pb.ev_a, s));
+        FSI_CUDA(cudaMemcpyAsync(pb.fg.p, &in, sizeof(FgState), cudaMemcpyHostToDevice, s));
+        FSI_CUDA(cudaMemcpyAsync(pb.bbuf.p, R.b, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        if (R.o.use_x0) FSI_CUDA(cudaMemcpyAsync(pb.xbuf.p, R.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        else FSI_CUDA(cudaMemsetAsync(pb.xbuf.p, 0, (size_t)n * 8, s));
+        FSI_CUDA(cudaGraphLaunch(pb.solve_graph[d], s));
+        FSI_CUDA(cudaMemcpyAsync(R.x, pb.xbuf.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        FSI_CUDA(cudaMemcpyAsync(&pb.h_fg[1], pb.fg.p, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+        FSI_CUDA(cudaEventRecord(pb.ev_b, s));
+    }
+    fsi_status err = FSI_OK;
+    for (auto &R : runs) {
+        Problem &pb = *R.pb;
+        cudaError_t ce = cudaStreamSynchronize(pb.stream);
+        if (ce != cudaSuccess) {
+            set_error(std::string("solve stream: ") + cudaGetErrorString(ce));
+            err = FSI_ERR_CUDA;
+            continue;
+        }
+        const FgState &o = pb.h_fg[1];
+        const int d = R.tr ? 1 : 0;
+        count_launch((int)(pb.graph_counts[d][0] + o.cycles * pb.graph_counts[d][1] +
+                           o.its * pb.graph_counts[d][2]));
+        R.its = o.its;
+        R.bnorm = o.bnorm;
+        R.beta = o.beta;
+        R.st.r0 = o.r0;
+        R.st.cycles = o.cycles;
+        fsi_status status = FSI_OK;
+        if (!std::isfinite(o.bnorm)) {
+            set_error("right-hand side has a non-finite norm");
+            R.beta = NAN;
+            status = FSI_ERR_NONFINITE;
+        } else if (o.bnorm == 0.0) {
+            FSI_CUDA(cudaMemsetAsync(R.x, 0, (size_t)pb.dev.back().n * 8, pb.stream));
+            R.beta = 0.0;
+        } else if (o.flags & 1) {
+            set_error("non-finite value in the Arnoldi process");
+            R.beta = NAN;
+            status = FSI_ERR_NONFINITE;
+        }
+        finish(R, status);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pb.ev_a, pb.ev_b) == cudaSuccess) R.st.solve_ms = ms;
+    }
+    for (auto &R : runs) {
+        FSI_CUDA(cudaEventRecord(cx.ev_out, R.pb->stream));
+        FSI_CUDA(cudaStreamWaitEvent(user, cx.ev_out, 0));
+    }
+    if (err == FSI_OK) {
+        int word = 0;
+        FSI_CUDA(cudaMemcpyAsync(&word, cx.flags.as<int>() + 2, 4, cudaMemcpyDeviceToHost, user));
+        FSI_CUDA(cudaStreamSynchronize(user));
+        if (word) {
+            set_error("a staged block copy did not complete in time (kernel error word " + std::to_string(word) + ")");
+            err = FSI_ERR_CUDA;
+        }
+    }
+    return err;
+}
+
+}  // namespace
+}  // namespace fsi
+
+extern "C" {
+
 static fsi_status solve_runs(Context &cx, std::vector<Run> &runs) {
-    fsi_status s = (cx.precision != FSI_FP64) ? run_batch<float>(cx, runs) : run_batch<double>(cx, runs);
+    const bool dev_loop = cx.use_graphs && cx.device_loop && !cx.profile;
+    fsi_status s = dev_loop ? ((cx.precision != FSI_FP64) ? run_device_loop<float>(cx, runs)
+                                                          : run_device_loop<double>(cx, runs))
+                            : ((cx.precision != FSI_FP64) ? run_batch<float>(cx, runs) : run_batch<double>(cx, runs));
     if (s != FSI_OK) return s;
     fsi_status worst = FSI_OK;
     for (auto &R : runs)
@@ -1030,8 +1352,10 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     if (!cx || !out || mode < 0 || mode > 2) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
     if (mode == 1) {
-        cx->prof_ms[0] = cx->prof_ms[1] = 0;
-        cx->prof_n[0] = cx->prof_n[1] = 0;
+        for (int k = 0; k < 3; ++k) {
+            cx->prof_ms[k] = 0;
+            cx->prof_n[k] = 0;
+        }
         cx->launch_base = launches_so_far();
         cx->profile = true;
     } else if (mode == 0) {
@@ -1057,7 +1381,79 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     out[4] = cx->prof_ms[1];
     out[5] = spmv;
     out[6] = (double)(launches_so_far() - cx->launch_base);
-    out[7] = 0.0;
+    out[7] = (double)cx->prof_n[2];
+    out[8] = cx->prof_ms[2];
+    out[9] = (double)F.A.nnz * 12.0 + (double)(F.n + 1) * 4.0 + (double)F.n * 2.0 * 8.0;   // float64 A z
+    out[10] = (double)F.A.nnz;
+    out[11] = 0.0;
+    return FSI_OK;
+}
+
+fsi_status fsi_autotune(fsi_ctx *ctx, const int *candidates, int n_cand, const fsi_solve_opts *opts,
+                        int *chosen, double *times_ms) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !candidates || n_cand < 1 || n_cand > 8 || !chosen) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
+    FSI_TRY(check_opts(opts));
+    for (int c = 0; c < n_cand; ++c)
+        if (candidates[c] < 1 || candidates[c] > 16) { set_error("candidate patch out of range"); return FSI_ERR_ARG; }
+    DeviceGuard guard(cx->device);
+    cudaStream_t s = cx->stream;
+    const int np = (int)cx->probs.size();
+    std::vector<int> done(np, 0);
+    for (int i = 0; i < np; ++i) {
+        if (done[i]) continue;
+        // size class: same dimension, fine size and level count
+        std::vector<int> cls;
+        for (int k = i; k < np; ++k) {
+            const ProblemDesc &a = cx->probs[i].desc, &b = cx->probs[k].desc;
+            if (!done[k] && a.dim == b.dim && a.n_fine == b.n_fine && a.n_levels == b.n_levels) cls.push_back(k);
+        }
+        Problem &rep = cx->probs[i];
+        const int64_t n = rep.dev.back().n;
+        // right-hand side b = A * 1 and solution buffer (set-up time memory)
+        DevBuf ones, bvec, xvec;
+        FSI_TRY(ones.alloc((size_t)n * 8));
+        FSI_TRY(bvec.alloc((size_t)n * 8));
+        FSI_TRY(xvec.alloc((size_t)n * 8));
+        std::vector<double> h1(n, 1.0);
+        FSI_CUDA(cudaMemcpyAsync(ones.p, h1.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        const DevCSR &A = rep.dev.back().A;
+        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), ones.as<double>(), (const double *)nullptr,
+                                                    bvec.as<double>(), SPMV_SET, s));
+        FSI_CUDA(cudaStreamSynchronize(s));
+        double best_t = 1e300;
+        int best = candidates[0];
+        for (int c = 0; c < n_cand; ++c) {
+            rep.patch = candidates[c];
+            FSI_TRY(setup_smoothers_problem(*cx, rep));
+            double t_ms = 1e300;
+            for (int rep_i = 0; rep_i < 2; ++rep_i) {     // first run captures the step graphs
+                fsi_solve_stats st;
+                fsi_status e = solve_one(*cx, rep, bvec.as<double>(), xvec.as<double>(), opts, &st, false);
+                if (e == FSI_ERR_CUDA || e == FSI_ERR_ALLOC) return e;
+                t_ms = (e == FSI_OK && st.converged) ? st.solve_ms : 1e300;
+            }
+            if (times_ms) times_ms[(size_t)i * n_cand + c] = t_ms;
+            if (t_ms < best_t) {
+                best_t = t_ms;
+                best = candidates[c];
+            }
+        }
+        for (int k : cls) {
+            Problem &pb = cx->probs[k];
+            pb.patch = best;
+            FSI_TRY(setup_smoothers_problem(*cx, pb));
+            chosen[k] = best;
+            done[k] = 1;
+            if (times_ms && k != i)
+                for (int c = 0; c < n_cand; ++c) times_ms[(size_t)k * n_cand + c] = times_ms[(size_t)i * n_cand + c];
+        }
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    g_last_error.clear();      // candidates that did not converge are not an error of the call
     return FSI_OK;
 }
 
@@ -1248,6 +1644,11 @@ void fsi_destroy(fsi_ctx *ctx) {
             }
             if (pb.h_scal) cudaFreeHost(pb.h_scal);
             pb.h_scal = nullptr;
+            if (pb.h_fg) cudaFreeHost(pb.h_fg);
+            pb.h_fg = nullptr;
+            if (pb.ev_a) cudaEventDestroy(pb.ev_a);
+            if (pb.ev_b) cudaEventDestroy(pb.ev_b);
+            pb.ev_a = pb.ev_b = nullptr;
         }
         if (cx->work) cudaStreamSynchronize(cx->work);
         cx->probs.clear();
@@ -1255,6 +1656,8 @@ void fsi_destroy(fsi_ctx *ctx) {
         if (cx->ev_in) cudaEventDestroy(cx->ev_in);
         if (cx->ev_out) cudaEventDestroy(cx->ev_out);
         if (cx->work) cudaStreamDestroy(cx->work);
+        for (auto &c : cx->cap)
+            if (c) cudaStreamDestroy(c);
     }
     delete cx;
 }

@@ -95,8 +95,23 @@ struct LevelDev {
     DevBuf b, x, r;
 };
 
+// Control block of a device-driven FGMRES solve (one per problem, device
+// memory).  The host writes rtol/max_iters/m before a launch and reads the
+// rest afterwards; the kernels of the solve graph update it in between.
+struct FgState {
+    int k = 0;              // Arnoldi columns completed in the current cycle
+    int its = 0;            // total Arnoldi steps
+    int cycles = 0;         // completed restart cycles
+    int flags = 0;          // bit 0: non-finite value met
+    int max_iters = 0, m = 0;
+    int pad0 = 0, pad1 = 0;
+    double rtol = 0.0;
+    double bnorm = 0.0, beta = 0.0, r0 = 0.0;
+};
+
 struct Problem {
     ProblemDesc desc;
+    int patch = 1;                   // Vanka group edge of this problem's smoothers
     std::vector<LevelHost> host;
     std::vector<LevelDev> dev;       // index = level
     std::vector<HostCSR> hP, hR;     // host transfers (for accessors)
@@ -113,6 +128,14 @@ struct Problem {
     cudaStream_t stream = nullptr;   // the problem's own solve stream
     double *h_scal = nullptr;        // pinned scalars of the running solve
     std::vector<int64_t> graph_kernels[2];
+    // device-driven solve: one graph per direction (nested WHILE nodes),
+    // control block, fixed copies of b, x and z_j, per-solve timing events
+    cudaGraphExec_t solve_graph[2] = {nullptr, nullptr};
+    int solve_graph_m[2] = {0, 0};
+    int64_t graph_counts[2][3] = {{0, 0, 0}, {0, 0, 0}};   // kernels: prologue, per cycle, per step
+    DevBuf fg, bbuf, xbuf, zbuf;
+    FgState *h_fg = nullptr;         // pinned: [0] parameters in, [1] state out
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 };
 
 // kernels launched by the library (all contexts), for launch accounting
@@ -137,13 +160,15 @@ struct Context {
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;   // kind, start/stop
-    double prof_ms[2] = {0, 0};
-    int64_t prof_n[2] = {0, 0};
+    double prof_ms[3] = {0, 0, 0};     // fine smoother, fine residual SpMV, outer float64 A z
+    int64_t prof_n[3] = {0, 0, 0};
     int64_t launch_base = 0;
     // solves run on a context-owned non-blocking stream
     cudaStream_t work = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     bool use_graphs = true;
+    bool device_loop = true;         // whole solve as one graph with WHILE nodes
+    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};   // streams for capturing loop bodies
 };
 
 // ---------------------------------------------------------------- kernels
@@ -173,26 +198,46 @@ template <class T>
 fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int transpose,
                              cudaStream_t s);
 
-// Krylov helpers
+// Krylov helpers.  Where a control block `fg` is passed, the column index
+// j (number of vectors nv = j + 1, count k) is read from fg->k on the device
+// instead of the host argument, so one captured launch serves every step of
+// a device-side loop; the host argument then only bounds the template size.
 fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
-                       double *partials, int nblocks, cudaStream_t s);
+                       double *partials, int nblocks, cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
                              int64_t n, double *partials, int nblocks, int norm_only,
-                             cudaStream_t s);
+                             cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out,
-                                  int accumulate, cudaStream_t s);
+                                  int accumulate, cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2,
                          const double *hn2, double *cs, double *sn, double *g, double *scal,
-                         cudaStream_t s);
+                         cudaStream_t s, FgState *fg = nullptr, cudaGraphConditionalHandle loop = 0);
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
-                             cudaStream_t s);
+                             cudaStream_t s, const FgState *fg = nullptr, int64_t ld = 0);
 fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y,
-                            cudaStream_t s);
+                            cudaStream_t s, const FgState *fg = nullptr);
 template <class T>
 fsi_status launch_combine(double *x, const T *Z, int64_t ld, int k, const double *y, int64_t n,
-                          cudaStream_t s);
+                          cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2,
-                             int64_t n, cudaStream_t s);
+                             int64_t n, cudaStream_t s, FgState *fg = nullptr,
+                             cudaGraphConditionalHandle loop = 0);
+// device-loop helpers: dst = (TO) V[:, fg->k]; zfix = Z[:, fg->k] = (double) z
+// take_column also selects the Gram-Schmidt variant of the step (SWITCH
+// node `sel`, value nv_class(fg->k + 1)) when sel is nonzero
+template <class TI, class TO>
+fsi_status launch_take_column(const TI *V, int64_t ld, const FgState *fg, TO *dst, int64_t n, cudaStream_t s,
+                              cudaGraphConditionalHandle sel = 0);
+// Gram-Schmidt kernels are instantiated for nv <= 1, 2, 4, 8, 16, 32, 65
+constexpr int NV_CLASSES = 7;
+__host__ __device__ inline int nv_class_bound(int c) { return c < 6 ? (1 << c) : 65; }
+template <class T>
+fsi_status launch_store_column(const T *z, double *zfix, double *Z, int64_t ld, const FgState *fg, int64_t n,
+                               cudaStream_t s);
+// loop control (one thread): after ||b||^2 (scal[5]) and ||r0||^2 (scal[6]);
+// after the true residual of a cycle (scal[6])
+fsi_status launch_fg_start(const double *scal, FgState *fg, cudaGraphConditionalHandle outer, cudaStream_t s);
+fsi_status launch_fg_cycle(const double *scal, FgState *fg, cudaGraphConditionalHandle outer, cudaStream_t s);
 fsi_status launch_pattern_grad(const DevCSR &A, const double *lam, const double *x, double *out,
                                cudaStream_t s);
 fsi_status launch_jacobi_setup(const DevCSR &A, const int32_t *idx, int64_t n, double *d64, float *d32,

@@ -1,4 +1,7 @@
 // Flexible GMRES kernels (outer Krylov solver, Sec. 3.2), all float64.
+// They serve both the host-driven loop (column index passed by value) and
+// the device-driven loop (column index read from the control block, loop
+// conditions set with cudaGraphSetConditional inside the solve graph).
 //
 // Arnoldi uses classical Gram-Schmidt applied twice (CGS2) in three fused
 // streaming passes over the basis V (column-major, one vector per column):
@@ -41,7 +44,8 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, do
 template <int NV>
 __global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                   const double *__restrict__ w, int64_t n,
-                                                  double *__restrict__ partials) {
+                                                  double *__restrict__ partials, const FgState *fg) {
+    if (fg) nv = min(fg->k + 1, NV);
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
@@ -59,7 +63,9 @@ __global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, 
 template <int NV>
 __global__ void __launch_bounds__(KT) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
                                                         int64_t ld, int nv, const double *__restrict__ h,
-                                                        int64_t n, double *__restrict__ partials, int norm_only) {
+                                                        int64_t n, double *__restrict__ partials, int norm_only,
+                                                        const FgState *fg) {
+    if (fg) nv = min(fg->k + 1, NV);
     __shared__ double hs[KMAX];
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
@@ -98,7 +104,8 @@ __global__ void __launch_bounds__(KT) update_dot_kernel(double *__restrict__ w, 
 // one warp per vector: lanes stride over the per-CTA partials in a fixed
 // order, then a fixed shuffle tree (deterministic)
 __global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int nv,
-                                       double *__restrict__ out, int accumulate) {
+                                       double *__restrict__ out, int accumulate, const FgState *fg) {
+    if (fg) nv = min(fg->k + 1, KMAX);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     for (int i = warp; i < nv; i += nw) {
         double s = 0.0;
@@ -114,9 +121,17 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, int 
 // scal[1] = h_{j+1,j}, scal[2] = ||A z_j|| (= sqrt(|h|^2 + h_{j+1,j}^2)),
 // scal[3] = 1 on breakdown-free column, 0 if both entries of the rotation
 // vanish; scal[4] non-finite flag.
+//
+// With a control block (device-side loop) j = fg->k, and the step's end
+// test runs here: fg->its and fg->k advance, and the loop's condition is
+// cleared when the estimate reaches rtol ||b||, on a (lucky) breakdown
+// h_{j+1,j} <= 1e-14 ||A z_j||, at max_iters, at the restart length, or on
+// a non-finite value (fg->flags bit 0).
 __global__ void givens_kernel(double *H, int ld, int j, const double *h1, const double *h2,
-                              const double *hn2, double *cs, double *sn, double *g, double *scal) {
+                              const double *hn2, double *cs, double *sn, double *g, double *scal,
+                              FgState *fg, cudaGraphConditionalHandle loop) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (fg) j = fg->k;
     double *col = H + (size_t)j * ld;
     double ss = 0.0;
     for (int i = 0; i <= j; ++i) {
@@ -147,18 +162,38 @@ __global__ void givens_kernel(double *H, int ld, int j, const double *h1, const 
     scal[2] = sqrt(ss + hn * hn);
     scal[3] = den > 0.0 ? 1.0 : 0.0;
     scal[4] = (isfinite(scal[0]) && isfinite(hn) && isfinite(den)) ? 0.0 : 1.0;
+    if (fg) {
+        const int its = fg->its + 1, k = j + 1;
+        fg->its = its;
+        fg->k = k;
+        const bool bad = scal[4] != 0.0;
+        if (bad) fg->flags |= 1;
+        const bool stop = bad || scal[0] <= fg->rtol * fg->bnorm || hn <= 1e-14 * scal[2] ||
+                          its >= fg->max_iters || k >= fg->m;
+        cudaGraphSetConditional(loop, stop ? 0u : 1u);
+    }
 }
 
+// v = w / scal[idx]; with a control block v is column fg->k of the basis
+// whose first column is v (leading dimension ld)
 __global__ void scale_copy_kernel(const double *__restrict__ w, double *__restrict__ v,
-                                  const double *__restrict__ scal, int idx, int64_t n) {
+                                  const double *__restrict__ scal, int idx, int64_t n, const FgState *fg,
+                                  int64_t ld) {
+    if (fg) v += (size_t)fg->k * ld;
     const double inv = 1.0 / scal[idx];
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
         v[r] = w[r] * inv;
 }
 
 // start of a cycle: beta = sqrt(nrm2), v0 = r / beta, g = (beta, 0, ...)
+// (device-side loop: also k = 0 and the inner loop's condition set)
 __global__ void init_basis_kernel(const double *__restrict__ r, double *__restrict__ v0, double *__restrict__ g,
-                                  int m, const double *__restrict__ nrm2, int64_t n) {
+                                  int m, const double *__restrict__ nrm2, int64_t n, FgState *fg,
+                                  cudaGraphConditionalHandle loop) {
+    if (fg && blockIdx.x == 0 && threadIdx.x == 0) {
+        fg->k = 0;
+        cudaGraphSetConditional(loop, 1u);
+    }
     const double beta = sqrt(nrm2[0]);
     const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -168,8 +203,9 @@ __global__ void init_basis_kernel(const double *__restrict__ r, double *__restri
 }
 
 // y = H(1:k,1:k)^{-1} g(1:k), upper triangular
-__global__ void backsolve_kernel(const double *H, int ld, int k, const double *g, double *y) {
+__global__ void backsolve_kernel(const double *H, int ld, int k, const double *g, double *y, const FgState *fg) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (fg) k = fg->k;
     for (int i = k - 1; i >= 0; --i) {
         double s = g[i];
         for (int j = i + 1; j < k; ++j) s -= H[(size_t)j * ld + i] * y[j];
@@ -179,7 +215,8 @@ __global__ void backsolve_kernel(const double *H, int ld, int k, const double *g
 
 template <class T>
 __global__ void combine_kernel(double *__restrict__ x, const T *__restrict__ Z, int64_t ld, int k,
-                               const double *__restrict__ y, int64_t n) {
+                               const double *__restrict__ y, int64_t n, const FgState *fg) {
+    if (fg) k = min(fg->k, KMAX);
     __shared__ double ys[KMAX];
     for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
     __syncthreads();
@@ -188,6 +225,58 @@ __global__ void combine_kernel(double *__restrict__ x, const T *__restrict__ Z, 
         for (int i = 0; i < k; ++i) s += (double)Z[(size_t)i * ld + r] * ys[i];
         x[r] = s;
     }
+}
+
+template <class TI, class TO>
+__global__ void take_column_kernel(const TI *__restrict__ V, int64_t ld, const FgState *fg, TO *__restrict__ dst,
+                                   int64_t n, cudaGraphConditionalHandle sel) {
+    if (sel && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int nv = fg->k + 1;
+        int c = 0;
+        while (c < NV_CLASSES - 1 && nv > nv_class_bound(c)) ++c;
+        cudaGraphSetConditional(sel, (unsigned)c);
+    }
+    const TI *v = V + (size_t)fg->k * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (TO)v[i];
+}
+
+template <class T>
+__global__ void store_column_kernel(const T *__restrict__ z, double *__restrict__ zfix, double *__restrict__ Z,
+                                    int64_t ld, const FgState *fg, int64_t n) {
+    double *zc = Z + (size_t)fg->k * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)z[i];
+        zfix[i] = v;
+        zc[i] = v;
+    }
+}
+
+// start of a device-driven solve: ||b|| and ||r0|| from the squared norms,
+// run the outer loop while the residual is above rtol ||b||
+__global__ void fg_start_kernel(const double *scal, FgState *fg, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double bn = sqrt(scal[5]), beta = sqrt(scal[6]);
+    fg->bnorm = bn;
+    fg->beta = beta;
+    fg->r0 = beta;
+    fg->its = 0;
+    fg->cycles = 0;
+    fg->k = 0;
+    fg->flags = (isfinite(bn) && isfinite(beta)) ? 0 : 1;
+    const bool go = fg->flags == 0 && bn > 0.0 && beta > fg->rtol * bn && fg->max_iters > 0;
+    cudaGraphSetConditional(outer, go ? 1u : 0u);
+}
+
+// end of a cycle: the new true residual decides whether to restart
+__global__ void fg_cycle_kernel(const double *scal, FgState *fg, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double beta = sqrt(scal[6]);
+    fg->beta = beta;
+    fg->cycles += 1;
+    if (!isfinite(beta)) fg->flags |= 1;
+    const bool go = fg->flags == 0 && beta > fg->rtol * fg->bnorm && fg->its < fg->max_iters;
+    cudaGraphSetConditional(outer, go ? 1u : 0u);
 }
 
 inline int egrid(int64_t n) {
@@ -211,9 +300,9 @@ inline int egrid(int64_t n) {
     } while (0)
 
 fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
-                       double *partials, int nblocks, cudaStream_t s) {
+                       double *partials, int nblocks, cudaStream_t s, const FgState *fg) {
     if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
-#define CALL_MDOT(NV) mdot_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials)
+#define CALL_MDOT(NV) mdot_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials, fg)
     FSI_NV_SWITCH(nv, CALL_MDOT);
 #undef CALL_MDOT
     count_launch();
@@ -222,9 +311,10 @@ fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int
 }
 
 fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
-                             int64_t n, double *partials, int nblocks, int norm_only, cudaStream_t s) {
+                             int64_t n, double *partials, int nblocks, int norm_only, cudaStream_t s,
+                             const FgState *fg) {
     if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
-#define CALL_UPD(NV) update_dot_kernel<NV><<<nblocks, KT, 0, s>>>(w, V, ld, nv, h, n, partials, norm_only)
+#define CALL_UPD(NV) update_dot_kernel<NV><<<nblocks, KT, 0, s>>>(w, V, ld, nv, h, n, partials, norm_only, fg)
     FSI_NV_SWITCH(nv, CALL_UPD);
 #undef CALL_UPD
     count_launch();
@@ -233,39 +323,41 @@ fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, con
 }
 
 fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out, int accumulate,
-                                  cudaStream_t s) {
-    reduce_partials_kernel<<<1, 1024, 0, s>>>(partials, nblocks, nv, out, accumulate);
+                                  cudaStream_t s, const FgState *fg) {
+    reduce_partials_kernel<<<1, 1024, 0, s>>>(partials, nblocks, nv, out, accumulate, fg);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2, const double *hn2,
-                         double *cs, double *sn, double *g, double *scal, cudaStream_t s) {
-    givens_kernel<<<1, 32, 0, s>>>(H, ld, j, h1, h2, hn2, cs, sn, g, scal);
+                         double *cs, double *sn, double *g, double *scal, cudaStream_t s, FgState *fg,
+                         cudaGraphConditionalHandle loop) {
+    givens_kernel<<<1, 32, 0, s>>>(H, ld, j, h1, h2, hn2, cs, sn, g, scal, fg, loop);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
-                             cudaStream_t s) {
-    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, scal, idx, n);
+                             cudaStream_t s, const FgState *fg, int64_t ld) {
+    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, scal, idx, n, fg, ld);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2, int64_t n,
-                             cudaStream_t s) {
-    init_basis_kernel<<<egrid(n), 256, 0, s>>>(r, v0, g, m, nrm2, n);
+                             cudaStream_t s, FgState *fg, cudaGraphConditionalHandle loop) {
+    init_basis_kernel<<<egrid(n), 256, 0, s>>>(r, v0, g, m, nrm2, n, fg, loop);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
-fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y, cudaStream_t s) {
-    backsolve_kernel<<<1, 32, 0, s>>>(H, ld, k, g, y);
+fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y, cudaStream_t s,
+                            const FgState *fg) {
+    backsolve_kernel<<<1, 32, 0, s>>>(H, ld, k, g, y, fg);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -273,16 +365,56 @@ fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, dou
 
 template <class T>
 fsi_status launch_combine(double *x, const T *Z, int64_t ld, int k, const double *y, int64_t n,
-                          cudaStream_t s) {
-    combine_kernel<T><<<egrid(n), 256, 0, s>>>(x, Z, ld, k, y, n);
+                          cudaStream_t s, const FgState *fg) {
+    combine_kernel<T><<<egrid(n), 256, 0, s>>>(x, Z, ld, k, y, n, fg);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 template fsi_status launch_combine<float>(double *, const float *, int64_t, int, const double *, int64_t,
-                                          cudaStream_t);
+                                          cudaStream_t, const FgState *);
 template fsi_status launch_combine<double>(double *, const double *, int64_t, int, const double *, int64_t,
-                                           cudaStream_t);
+                                           cudaStream_t, const FgState *);
+
+template <class TI, class TO>
+fsi_status launch_take_column(const TI *V, int64_t ld, const FgState *fg, TO *dst, int64_t n, cudaStream_t s,
+                              cudaGraphConditionalHandle sel) {
+    take_column_kernel<TI, TO><<<egrid(n), 256, 0, s>>>(V, ld, fg, dst, n, sel);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+template fsi_status launch_take_column<double, float>(const double *, int64_t, const FgState *, float *, int64_t,
+                                                      cudaStream_t, cudaGraphConditionalHandle);
+template fsi_status launch_take_column<double, double>(const double *, int64_t, const FgState *, double *, int64_t,
+                                                       cudaStream_t, cudaGraphConditionalHandle);
+
+template <class T>
+fsi_status launch_store_column(const T *z, double *zfix, double *Z, int64_t ld, const FgState *fg, int64_t n,
+                               cudaStream_t s) {
+    store_column_kernel<T><<<egrid(n), 256, 0, s>>>(z, zfix, Z, ld, fg, n);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+template fsi_status launch_store_column<float>(const float *, double *, double *, int64_t, const FgState *, int64_t,
+                                               cudaStream_t);
+template fsi_status launch_store_column<double>(const double *, double *, double *, int64_t, const FgState *,
+                                                int64_t, cudaStream_t);
+
+fsi_status launch_fg_start(const double *scal, FgState *fg, cudaGraphConditionalHandle outer, cudaStream_t s) {
+    fg_start_kernel<<<1, 32, 0, s>>>(scal, fg, outer);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status launch_fg_cycle(const double *scal, FgState *fg, cudaGraphConditionalHandle outer, cudaStream_t s) {
+    fg_cycle_kernel<<<1, 32, 0, s>>>(scal, fg, outer);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
 
 }  // namespace fsi

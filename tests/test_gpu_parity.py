@@ -278,3 +278,79 @@ def test_3d_valve_box_parity():
     sh.setup_smoothers(precision=binding.FSI_MIXED_HALF)
     x, st = sh.solve(_cuda(b), rtol=1e-10)
     assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_autotune_per_size_class_patch():
+    """fsi_autotune times each candidate Vanka group size once per size class
+    and rebuilds every problem's smoothers with its class's fastest choice;
+    afterwards each smoother equals the oracle's FS-ASM with that group size
+    and the batched solve still reaches the direct solution."""
+    probs = [I.make_channel_2d(32, 4, 3, 301, band_width=0.3, mu_s=200.0),
+             I.make_channel_2d(24, 3, 3, 302, band_width=0.2, mu_s=300.0),
+             I.make_channel_2d(32, 4, 3, 303, band_width=0.25, mu_s=500.0)]
+    s = binding.FSISolver(probs)
+    s.setup_smoothers(precision=binding.FSI_FP64, patch=1)
+    cand = (1, 2, 3)
+    chosen, times = s.autotune(cand, rtol=1e-8)
+    assert chosen[0] == chosen[2] and all(c in cand for c in chosen)
+    for k, c in enumerate(chosen):
+        assert np.isfinite(times[k][cand.index(c)])
+        assert times[k][cand.index(c)] == min(times[k])
+    np.testing.assert_array_equal(times[0], times[2])
+    rng = np.random.default_rng(5)
+    bs, refs = [], []
+    for k, p in enumerate(probs):
+        H = gmg.Hierarchy(p, patch=chosen[k])
+        lf = len(H.A) - 1
+        r = rng.standard_normal(H.A[lf].shape[0])
+        y = s.apply_smoother(lf, _cuda(r), prob=k).cpu().numpy()
+        ref = H.smoothers[lf].apply(r)
+        assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(ref)
+        b = _rhs(p, H, 40 + k)
+        bs.append(_cuda(b))
+        refs.append(_direct(H.fine, b))
+    xs, sts = s.solve_batched(bs, rtol=1e-10)
+    for x, ref, st in zip(xs, refs, sts):
+        assert st["converged"]
+        assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_device_loop_matches_host_loop(monkeypatch):
+    """The solve runs as one CUDA graph whose restart and Arnoldi loops are
+    WHILE nodes driven from the device; it must reproduce the host-driven
+    loop (same kernels, same order): equal iteration and cycle counts and
+    the same iterate, for a fresh solve, a replay, a warm start and the
+    transposed (adjoint) solve."""
+    p = PROBLEMS["bulge48"]()
+    H = gmg.Hierarchy(p)
+    b = _rhs(p, H, 77)
+    sd = binding.FSISolver(p)
+    sd.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    monkeypatch.setenv("FSI_DEVICE_LOOP", "0")
+    sh = binding.FSISolver(p)
+    monkeypatch.delenv("FSI_DEVICE_LOOP")
+    sh.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    for rtol in (1e-10, 1e-6):
+        for rep in range(2):
+            xd, std = sd.solve(_cuda(b), rtol=rtol, restart=12)
+            xh, sth = sh.solve(_cuda(b), rtol=rtol, restart=12)
+            assert std["iterations"] == sth["iterations"] and std["cycles"] == sth["cycles"]
+            assert std["cycles"] >= 1
+            # the smoother's overlapping scatter-add uses atomics, so two runs
+            # of either loop differ by rounding; the iterates agree to far
+            # below the requested residual
+            xd, xh = xd.cpu().numpy(), xh.cpu().numpy()
+            assert np.linalg.norm(xd - xh) <= 1e-2 * rtol * np.linalg.norm(xh)
+            assert std["converged"] and sth["converged"]
+            assert std["rel_residual"] <= rtol and sth["rel_residual"] <= rtol
+    x0 = _cuda(0.5 * _direct(H.fine, b))
+    xd, std = sd.solve(_cuda(b), x0=x0.clone(), rtol=1e-10)
+    xh, sth = sh.solve(_cuda(b), x0=x0.clone(), rtol=1e-10)
+    assert std["iterations"] == sth["iterations"]
+    assert np.linalg.norm(xd.cpu().numpy() - xh.cpu().numpy()) <= 1e-12 * np.linalg.norm(xh.cpu().numpy())
+    w = _rhs(p, H, 78)
+    x, _ = sd.solve(_cuda(b), rtol=1e-10)
+    ad = sd.adjoint(_cuda(w), x, rtol=1e-10)
+    ah = sh.adjoint(_cuda(w), x, rtol=1e-10)
+    assert ad[3]["iterations"] == ah[3]["iterations"]
+    assert np.linalg.norm(ad[0].cpu().numpy() - ah[0].cpu().numpy()) <= 1e-12 * np.linalg.norm(ah[0].cpu().numpy())
