@@ -78,7 +78,19 @@ typedef struct {
     int patch;                  /* Vanka group edge b >= 1: b^dim pressure vertices per block */
     double omega;               /* Richardson damping (Sec. 3.2), > 0 */
     int nu_pre, nu_post;        /* smoothing steps, >= 1 */
+    int factor;                 /* block inversion ("solved by LU", Sec. 3.2):
+                                 *   FSI_FACTOR_AUTO (0): float64 Gauss-Jordan for FSI_FP64,
+                                 *     FSI_FACTOR_TF32 otherwise;
+                                 *   FSI_FACTOR_FP64 (1): unblocked float64 Gauss-Jordan;
+                                 *   FSI_FACTOR_FP32 (2): blocked float32 Gauss-Jordan, rank-32
+                                 *     updates on the CUDA cores;
+                                 *   FSI_FACTOR_TF32 (3): blocked float32 Gauss-Jordan, rank-32
+                                 *     trailing updates on the tensor cores (tcgen05, TF32
+                                 *     operands, float32 accumulation).
+                                 * 2 and 3 need a mixed precision (FSI_ERR_ARG otherwise). */
 } fsi_smoother_opts;
+
+enum { FSI_FACTOR_AUTO = 0, FSI_FACTOR_FP64 = 1, FSI_FACTOR_FP32 = 2, FSI_FACTOR_TF32 = 3 };
 
 typedef struct {
     double rtol;                /* stop when ||f - J2 x||_2 <= rtol ||f||_2 (float64 true residual) */

@@ -809,7 +809,12 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         }
         D.err = cx.flags.as<int>() + 2;
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
-        FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
+        int method = cx.factor;
+        if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
+        if (method == FSI_FACTOR_FP64)
+            FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
+        else
+            FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
         int flag = 0;
         FSI_TRY(read_flag(cx, &flag));
         if (flag) {
@@ -943,8 +948,13 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     if (!cx || !opts) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
     if (opts->precision < FSI_FP64 || opts->precision > FSI_MIXED_HALF || opts->patch < 1 || opts->patch > 16 ||
-        !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8) {
+        !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8 ||
+        opts->factor < FSI_FACTOR_AUTO || opts->factor > FSI_FACTOR_TF32) {
         set_error("smoother options out of range");
+        return FSI_ERR_ARG;
+    }
+    if (opts->precision == FSI_FP64 && opts->factor >= FSI_FACTOR_FP32) {
+        set_error("float32 block inversion needs a mixed precision");
         return FSI_ERR_ARG;
     }
     DeviceGuard guard(cx->device);
@@ -954,6 +964,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     cx->omega = opts->omega;
     cx->nu_pre = opts->nu_pre;
     cx->nu_post = opts->nu_post;
+    cx->factor = opts->factor;
     cx->smoothers_ready = false;
     for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
     FSI_CUDA(cudaStreamSynchronize(cx->stream));

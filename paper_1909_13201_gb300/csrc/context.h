@@ -150,6 +150,7 @@ struct Context {
     int patch = 1;
     double omega = 1.0;
     int nu_pre = 1, nu_post = 1;
+    int factor = FSI_FACTOR_AUTO;    // block inversion method (resolved per precision)
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;
@@ -192,6 +193,11 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
                               cudaStream_t s);
 template <class T>
 fsi_status launch_jacobi_apply(const LevelDev &lev, const T *r, T *x, T omega, cudaStream_t s);
+
+// blocked float32 Gauss-Jordan (tensor: tcgen05 TF32 rank-32 updates;
+// otherwise float32 FMAs); storage 1 float32, 2 float16 + row scale
+fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int storage, bool tensor, int *flags,
+                                  cudaStream_t s);
 
 fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s);
 template <class T>

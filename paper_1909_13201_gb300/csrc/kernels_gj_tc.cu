@@ -1,0 +1,417 @@
+// Batched block inversion for the mixed-precision smoothers (Sec. 3.2, "each
+// block solved by LU"): blocked Gauss-Jordan in float32 whose rank-32
+// trailing updates run on the 5th-generation tensor cores (tcgen05.mma,
+// kind::tf32, accumulator in tensor memory).
+//
+// The block's rows live in shared memory (float32, row-major), split over a
+// thread-block cluster of C CTAs when they do not fit one CTA.  Columns are
+// eliminated in panels of 32:
+//   1. the CTA owning the panel's 32 rows runs unblocked Gauss-Jordan on
+//      those rows only: afterwards they hold Rp = D^{-1} M[K, :] with the
+//      panel columns replaced by D^{-1} (D = M[K, K]);
+//   2. Rp is written, transposed and rounded to TF32, into every CTA's
+//      operand buffer (distributed shared memory), then a cluster barrier;
+//   3. every CTA builds F = -M[rows, K] (zero on the panel rows), zeroes
+//      M[rows, K], and one thread issues D_tmem = F x Rp (M = 128 rows per
+//      MMA, N <= 256 columns, K = 8 per instruction, 4 instructions);
+//   4. the accumulator is read back with tcgen05.ld and added to M.
+// After the last panel M holds A^{-1} (unpivoted, as the float64 kernel:
+// the J2 order inside a block puts the positive-definite momentum/ALE
+// unknowns before the pressures).  The same kernel with TC = false does the
+// rank-32 update with float32 FMAs on the CUDA cores (reference variant).
+//
+// Operand layout (no swizzle): 8-row x 16-byte core matrices; element (r, k)
+// of a 32-wide K panel sits at (r/8)*1024 + (k/4)*128 + (r%8)*16 + (k%4)*4
+// bytes, so the leading (K) byte offset is 128 and the stride (M/N) byte
+// offset 1024; K step s starts 256 s bytes in.  Every wait is bounded.
+#include <cooperative_groups.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "context.h"
+
+namespace cg = cooperative_groups;
+
+namespace fsi {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int PANEL = 32;
+constexpr int CM_SBO = 1024, CM_LBO = 128;
+
+struct GJTCParams {
+    const int32_t *blk_ptr, *blk_idx;
+    const int64_t *blk_off;
+    const int32_t *row_ptr, *col;
+    const double *val;
+    void *inv;                 // float or __half
+    float *scale;              // float16 storage: per block row
+    int storage;               // 1 float32, 2 float16 + row scale
+    int n_max;                 // largest block
+    int rows_per_cta;          // R (multiple of 32)
+    int ldm;                   // row stride of M in shared memory (floats)
+    int npad;                  // columns rounded up to 16
+    int tiles;                 // 128-row MMA tiles per CTA
+    int tmem_cols;             // allocated tensor-memory columns
+    size_t off_f, off_b, off_misc;   // shared-memory offsets (bytes)
+    int *flags;                // [0] zero pivot, [2] |= 4: MMA wait timed out
+};
+
+__host__ __device__ inline int cm_off(int r, int k) {
+    return (r >> 3) * CM_SBO + (k >> 2) * CM_LBO + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((CM_LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((CM_SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                        // descriptor version of this architecture family
+    return d;                                      // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int C, bool TC>
+__global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (C > 1) ? (int)cluster.block_rank() : 0;
+    const int blk = blockIdx.x / C;
+    const int s0 = P.blk_ptr[blk];
+    const int n = P.blk_ptr[blk + 1] - s0;
+    const int32_t *idx = P.blk_idx + s0;
+    const int R = P.rows_per_cta, ldm = P.ldm;
+    const int r0 = rank * R;
+    const int nr = max(0, min(R, n - r0));             // rows held by this CTA
+    const int npad = (n + 15) & ~15;
+    float *Ms = reinterpret_cast<float *>(smraw);       // [R][ldm]
+    unsigned char *Fs = smraw + P.off_f;                // tiles x 16 KB (A operand)
+    unsigned char *Bs = smraw + P.off_b;                // npad x 128 B (B operand, Rp^T)
+    unsigned char *misc = smraw + P.off_misc;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 8);
+    int *sflag = reinterpret_cast<int *>(misc + 12);    // [0] bad pivot, [1] wait timeout
+    float *fcol = reinterpret_cast<float *>(misc + 64); // [PANEL] panel column of the panel rows
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+
+    if (TC && warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(P.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        sflag[0] = 0;
+        sflag[1] = 0;
+        if (TC) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    }
+    // gather the local rows (float64 CSR -> float32)
+    for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
+    __syncthreads();
+    for (int li = warp; li < nr; li += TC_THREADS / 32) {
+        const int g = idx[r0 + li];
+        for (int k = P.row_ptr[g] + lane; k < P.row_ptr[g + 1]; k += 32) {
+            const int c = P.col[k];
+            int lo = 0, hi = n, pos = -1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1, v = idx[mid];
+                if (v == c) { pos = mid; break; }
+                if (v < c) lo = mid + 1; else hi = mid;
+            }
+            if (pos >= 0) Ms[(size_t)li * ldm + pos] = (float)P.val[k];
+        }
+    }
+    if (TC) asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (TC) asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = TC ? *tslot : 0u;
+    if (C > 1) cluster.sync();
+
+    const int npanels = (n + PANEL - 1) / PANEL;
+    for (int p = 0; p < npanels; ++p) {
+        const int k0 = p * PANEL, kw = min(PANEL, n - k0);
+        const int owner = k0 / R;
+        // ---- 1. panel Gauss-Jordan on the owner's 32 rows
+        if (rank == owner) {
+            const int lb = k0 - r0;                     // first panel row (local)
+            for (int t = 0; t < kw; ++t) {
+                const int c = k0 + t;
+                float *prow = Ms + (size_t)(lb + t) * ldm;
+                float piv = prow[c];
+                if (tid < kw) fcol[tid] = Ms[(size_t)(lb + tid) * ldm + c];
+                __syncthreads();
+                if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
+                    if (tid == 0) sflag[0] = 1;
+                    piv = 1.f;
+                }
+                const float ip = 1.f / piv;
+                for (int j = tid; j < n; j += blockDim.x) prow[j] = (j == c) ? ip : prow[j] * ip;
+                __syncthreads();
+                for (int e = tid; e < kw * n; e += blockDim.x) {
+                    const int u = e / n, j = e - u * n;
+                    if (u == t) continue;
+                    const float f = fcol[u];
+                    float *urow = Ms + (size_t)(lb + u) * ldm;
+                    urow[j] = (j == c) ? -f * ip : fmaf(-f, prow[j], urow[j]);
+                }
+                __syncthreads();
+            }
+            // ---- 2. Rp^T (TF32) into every CTA's B buffer, zero-padded
+            for (int dst = 0; dst < C; ++dst) {
+                unsigned char *bd = Bs;
+                if (C > 1) bd = reinterpret_cast<unsigned char *>(cluster.map_shared_rank(Bs, dst));
+                for (int e = tid; e < npad * PANEL; e += blockDim.x) {
+                    const int j = e / PANEL, t = e - j * PANEL;
+                    const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
+                    *reinterpret_cast<float *>(bd + cm_off(j, t)) = TC ? to_tf32(v) : v;
+                }
+            }
+        }
+        if (C > 1) cluster.sync(); else __syncthreads();
+        // ---- 3. F = -M[rows, K] (0 on the panel rows), zero M[rows, K]
+        const bool own = rank == owner;
+        const int lb = k0 - r0;
+        for (int e = tid; e < P.tiles * 128 * PANEL; e += blockDim.x) {
+            const int li = e / PANEL, t = e - li * PANEL;
+            float v = 0.f;
+            if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) {
+                v = -Ms[(size_t)li * ldm + k0 + t];
+            }
+            *reinterpret_cast<float *>(Fs + (size_t)(li >> 7) * 16384 + cm_off(li & 127, t)) = TC ? to_tf32(v) : v;
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * kw; e += blockDim.x) {
+            const int li = e / kw, t = e - li * kw;
+            if (!(own && li >= lb && li < lb + kw)) Ms[(size_t)li * ldm + k0 + t] = 0.f;
+        }
+        if (TC) {
+            // ---- 4a. tensor cores: D = F x Rp, then M += D
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                const int nchunks = (npad + 255) / 256;
+                const int nc = ((npad / nchunks) + 15) & ~15;
+                for (int tile = 0; tile < P.tiles; ++tile) {
+                    for (int ch = 0; ch < nchunks; ++ch) {
+                        const int c0 = ch * nc, cw = min(nc, npad - c0);
+                        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(cw >> 3) << 17) |
+                                               ((uint32_t)(128 >> 4) << 24);
+                        const uint32_t dt = tmem + (uint32_t)(tile * npad + c0);
+                        const uint32_t a0 = smem_u32(Fs + (size_t)tile * 16384);
+                        const uint32_t b0 = smem_u32(Bs + (size_t)(c0 >> 3) * CM_SBO);
+                        for (int s = 0; s < PANEL / 8; ++s) {
+                            const uint64_t ad = smem_desc(a0 + s * 2 * CM_LBO);
+                            const uint64_t bd = smem_desc(b0 + s * 2 * CM_LBO);
+                            const uint32_t acc = s > 0 ? 1u : 0u;
+                            asm volatile("{\n.reg .pred q;\nsetp.ne.u32 q, %4, 0;\n"
+                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}" ::"r"(dt),
+                                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(mbar)));
+            }
+            {
+                uint32_t done = 0;
+                for (int it = 0; it < (1 << 20) && !done; ++it) {
+                    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                                 "selp.u32 %0, 1, 0, q;\n}"
+                                 : "=r"(done)
+                                 : "r"(smem_u32(mbar)), "r"((uint32_t)(p & 1)));
+                }
+                if (!done) sflag[1] = 1;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // each warp reads its 32-lane quarter; the two warps of a quarter split the columns
+            const int q = warp & 3, half = warp >> 2;
+            for (int tile = 0; tile < P.tiles; ++tile) {
+                const int li = tile * 128 + q * 32 + lane;
+                for (int c0 = half * 16; c0 < npad; c0 += 32) {
+                    uint32_t v[16];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tile * npad + c0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (li < nr) {
+                        float *mrow = Ms + (size_t)li * ldm;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < n) mrow[c0 + j] += __uint_as_float(v[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        } else {
+            // ---- 4b. CUDA cores: M[i, :] += F[i, :] x Rp (float32 FMAs)
+            __syncthreads();
+            for (int e = tid; e < nr * n; e += blockDim.x) {
+                const int li = e / n, j = e - li * n;
+                const unsigned char *frow = Fs + (size_t)(li >> 7) * 16384;
+                float acc = 0.f;
+#pragma unroll 8
+                for (int t = 0; t < PANEL; ++t)
+                    acc = fmaf(*reinterpret_cast<const float *>(frow + cm_off(li & 127, t)),
+                               *reinterpret_cast<const float *>(Bs + cm_off(j, t)), acc);
+                Ms[(size_t)li * ldm + j] += acc;
+            }
+            __syncthreads();
+        }
+        // peers finished reading their B buffers before the next owner writes them
+        if (C > 1) cluster.sync();
+    }
+    if (tid == 0) {
+        if (sflag[0]) atomicExch(P.flags, 1);
+        if (sflag[1]) atomicOr(P.flags + 2, 4);
+    }
+    // ---- output
+    const int64_t off = P.blk_off[blk];
+    if (P.storage == 2) {
+        const int ldo = (n + 7) & ~7;
+        __half *out = static_cast<__half *>(P.inv) + off;
+        for (int li = warp; li < nr; li += TC_THREADS / 32) {
+            float m = 0.f;
+            for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(Ms[(size_t)li * ldm + j]));
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const float sc = m > 0.f ? m : 1.f;
+            if (lane == 0) P.scale[s0 + r0 + li] = sc;
+            const float isc = 1.f / sc;
+            for (int j = lane; j < ldo; j += 32)
+                out[(size_t)(r0 + li) * ldo + j] = __float2half_rn(j < n ? Ms[(size_t)li * ldm + j] * isc : 0.f);
+        }
+    } else {
+        const int ldo = (n + 3) & ~3;
+        float *out = static_cast<float *>(P.inv) + off;
+        for (int t = tid; t < nr * ldo; t += blockDim.x) {
+            const int li = t / ldo, j = t - li * ldo;
+            out[(size_t)(r0 + li) * ldo + j] = (j < n) ? Ms[(size_t)li * ldm + j] : 0.f;
+        }
+    }
+    if (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
+    }
+    if (C > 1) cluster.sync();
+}
+
+template <int C, bool TC>
+fsi_status launch_tc(const GJTCParams &P, int64_t n_blocks, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_blocks * C));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FSI_CUDA(cudaFuncSetAttribute(block_gj_tc_kernel<C, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FSI_CUDA(cudaLaunchKernelEx(&cfg, block_gj_tc_kernel<C, TC>, P));
+    count_launch();
+    return FSI_OK;
+}
+
+}  // namespace
+
+// Shared-memory and tensor-memory plan for blocks of up to n dofs: the
+// smallest cluster whose CTAs hold R = 32-aligned rows within the budgets.
+bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out) {
+    const size_t budget = 225 * 1024;
+    const int npad = (n + 15) & ~15;
+    for (int C = 1; C <= 8; C *= 2) {
+        int R = (n + C - 1) / C;
+        if (C > 1) R = (R + PANEL - 1) / PANEL * PANEL;
+        const int tiles = (R + 127) / 128;
+        if (tiles * npad > 512) continue;
+        int ldm = n;
+        ldm += (33 - (ldm % 32)) % 32;                  // row stride = 1 (mod 32): conflict-free column reads
+        const size_t m_bytes = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
+        const size_t f_bytes = (size_t)tiles * 16384;
+        const size_t b_bytes = ((size_t)npad * 128 + 1023) & ~(size_t)1023;
+        size_t total = m_bytes + f_bytes + b_bytes + 256;
+        // a cluster's CTAs must not share an SM: each holds its tensor-memory
+        // columns until the last cluster barrier, so a second CTA of the same
+        // cluster waiting in tcgen05.alloc on that SM would never proceed
+        if (C > 1) total = std::max(total, (size_t)120 * 1024);
+        if (total <= budget) {
+            *C_out = C;
+            *R_out = R;
+            *smem_out = total;
+            return true;
+        }
+    }
+    return false;
+}
+
+fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int storage, bool tensor, int *flags,
+                                  cudaStream_t s) {
+    if (lev.n_blocks == 0) return FSI_OK;
+    if (storage != 1 && storage != 2) { set_error("float32 block inversion stores float32 or float16"); return FSI_ERR_ARG; }
+    const int n = (int)lev.max_block;
+    int C = 1, R = 0;
+    size_t smem = 0;
+    if (!gj_tc_plan(n, &C, &R, &smem)) {
+        set_error("Schwarz block too large for the float32 cluster inversion (" + std::to_string(n) + " dofs)");
+        return FSI_ERR_ARG;
+    }
+    GJTCParams P;
+    P.blk_ptr = lev.blk_ptr.as<int32_t>();
+    P.blk_idx = lev.blk_idx.as<int32_t>();
+    P.blk_off = lev.blk_off.as<int64_t>();
+    P.row_ptr = A.ptr.as<int32_t>();
+    P.col = A.col.as<int32_t>();
+    P.val = A.val64.as<double>();
+    P.inv = lev.inv.p;
+    P.scale = lev.inv_scale.as<float>();
+    P.storage = storage;
+    P.n_max = n;
+    P.rows_per_cta = R;
+    int ldm = n;
+    ldm += (33 - (ldm % 32)) % 32;
+    P.ldm = ldm;
+    P.npad = (n + 15) & ~15;
+    P.tiles = (R + 127) / 128;
+    int cols = 32;
+    while (cols < P.tiles * P.npad) cols *= 2;
+    P.tmem_cols = cols;
+    P.off_f = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
+    P.off_b = P.off_f + (size_t)P.tiles * 16384;
+    P.off_misc = P.off_b + (((size_t)P.npad * 128 + 1023) & ~(size_t)1023);
+    P.flags = flags;
+#define FSI_TC_CASE(CC)                                                                       \
+    case CC:                                                                                  \
+        return tensor ? launch_tc<CC, true>(P, lev.n_blocks, smem, s)                         \
+                      : launch_tc<CC, false>(P, lev.n_blocks, smem, s);
+    switch (C) {
+        FSI_TC_CASE(1)
+        FSI_TC_CASE(2)
+        FSI_TC_CASE(4)
+        FSI_TC_CASE(8)
+        default:
+            set_error("bad cluster size");
+            return FSI_ERR_ARG;
+    }
+#undef FSI_TC_CASE
+}
+
+}  // namespace fsi

@@ -123,7 +123,8 @@ def test_fgmres_fp64_solution_and_iterations(case):
 def test_mixed_precision_solve(case, prec):
     name, p, H, s = case
     sm = binding.FSISolver(p)
-    sm.setup_smoothers(precision=prec)
+    # float64 block inverses, as in the oracle's storage emulation
+    sm.setup_smoothers(precision=prec, factor=binding.FSI_FACTOR_FP64)
     b = _rhs(p, H, 12)
     xd = _direct(H.fine, b)
     x, st = sm.solve(_cuda(b), rtol=1e-10)
@@ -169,7 +170,7 @@ def test_half_storage_smoother_matches_emulation(case):
     float32 apply) to float32 accumulation error."""
     name, p, H, s = case
     sh = binding.FSISolver(p)
-    sh.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    sh.setup_smoothers(precision=binding.FSI_MIXED_HALF, factor=binding.FSI_FACTOR_FP64)
     Hh = gmg.Hierarchy(p, mixed="half")
     rng = np.random.default_rng(8)
     for l in range(1, len(H.A)):
@@ -356,3 +357,49 @@ def test_device_loop_matches_host_loop(monkeypatch):
     ah = sh.adjoint(_cuda(w), x, rtol=1e-10)
     assert abs(ad[3]["iterations"] - ah[3]["iterations"]) <= 1
     assert np.linalg.norm(ad[0].cpu().numpy() - ah[0].cpu().numpy()) <= 1e-12 * np.linalg.norm(ah[0].cpu().numpy())
+
+
+FACTOR_CASES = {
+    "bulge48": lambda: I.make_channel_2d(48, 4, 3, 4242, bulge=True),     # 171-dof blocks, one CTA
+    "valve8": lambda: I.make_valve_3d(8, 3, 1, 777),                      # 376-dof blocks, 4-CTA cluster
+}
+
+
+@pytest.mark.parametrize("name", list(FACTOR_CASES))
+def test_float32_blocked_inversion(name):
+    """Blocked float32 Gauss-Jordan (32-column panels) with the rank-32
+    updates on the CUDA cores (FP32) or on the tensor cores (tcgen05, TF32
+    operands): the smoother output against the same smoother with float64
+    inverses, on every level, in float32 storage; then full solves with the
+    tensor-core factors in both mixed modes.  Expected errors (the oracle's
+    emulation of the blocked elimination): ~8e-8 (FP32) and ~1.3e-4 (TF32)."""
+    p = FACTOR_CASES[name]()
+    H = gmg.Hierarchy(p)
+    ref = binding.FSISolver(p)
+    ref.setup_smoothers(precision=binding.FSI_MIXED, factor=binding.FSI_FACTOR_FP64)
+    rng = np.random.default_rng(12)
+    for factor, tol in ((binding.FSI_FACTOR_FP32, 2e-6), (binding.FSI_FACTOR_TF32, 2e-3)):
+        sv = binding.FSISolver(p)
+        sv.setup_smoothers(precision=binding.FSI_MIXED, factor=factor)
+        for l in range(1, len(H.A)):
+            r = rng.standard_normal(H.A[l].shape[0]).astype(np.float32).astype(np.float64)
+            y0 = ref.apply_smoother(l, _cuda(r)).cpu().numpy()
+            y = sv.apply_smoother(l, _cuda(r)).cpu().numpy()
+            assert np.linalg.norm(y - y0) <= tol * np.linalg.norm(y0), (factor, l)
+            yt0 = ref.apply_smoother(l, _cuda(r), transpose=True).cpu().numpy()
+            yt = sv.apply_smoother(l, _cuda(r), transpose=True).cpu().numpy()
+            assert np.linalg.norm(yt - yt0) <= tol * np.linalg.norm(yt0), (factor, l)
+    b = _rhs(p, H, 50)
+    xd = _direct(H.fine, b)
+    for prec in (binding.FSI_MIXED, binding.FSI_MIXED_HALF):
+        s64 = binding.FSISolver(p)
+        s64.setup_smoothers(precision=prec, factor=binding.FSI_FACTOR_FP64)
+        stc = binding.FSISolver(p)
+        stc.setup_smoothers(precision=prec)                 # default: tensor-core factors
+        x, st = stc.solve(_cuda(b), rtol=1e-10)
+        assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+        _, st8 = stc.solve(_cuda(b), rtol=1e-8)
+        _, st64 = s64.solve(_cuda(b), rtol=1e-8)
+        assert abs(st8["iterations"] - st64["iterations"]) <= 2, (st8["iterations"], st64["iterations"])
+    with pytest.raises(binding.FSIError):
+        binding.FSISolver(p).setup_smoothers(precision=binding.FSI_FP64, factor=binding.FSI_FACTOR_TF32)
