@@ -174,6 +174,14 @@ class Clocks:
 FP64_NOMINAL_GFLOPS = 1250.0
 
 
+def measured_tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 burst figure times the
+    nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = json.load(open(path)).get("bf16_tflops", 1900.0) if os.path.exists(path) else 1900.0
+    return bf16 * 1.1 / 2.25
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -210,7 +218,8 @@ def run_ours(args, rank, world, local):
     import torch.distributed as dist
 
     from paper_1909_13201_gb300 import inputs as I
-    from paper_1909_13201_gb300.binding import FSI_FP64, FSI_MIXED, FSI_MIXED_HALF, FSISolver
+    from paper_1909_13201_gb300.binding import (FSI_FACTOR_FP32, FSI_FACTOR_FP64, FSI_FACTOR_TF32, FSI_FP64,
+                                                FSI_MIXED, FSI_MIXED_HALF, FSISolver)
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -284,6 +293,10 @@ def run_ours(args, rank, world, local):
     achieved = prof["smoother_bytes"] / (sm_ms * 1e-3) / 1e9
     spmv_ms = prof["spmv_ms"] / max(prof["spmv_launches"], 1)
     spmv_gbs = prof["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
+    rst_ms = prof["restrict_ms"] / max(prof["restrict_launches"], 1)
+    rst_gbs = prof["restrict_bytes"] / (rst_ms * 1e-3) / 1e9
+    pro_ms = prof["prolong_ms"] / max(prof["prolong_launches"], 1)
+    pro_gbs = prof["prolong_bytes"] / (pro_ms * 1e-3) / 1e9
     outer_ms = prof["outer_ms"] / max(prof["outer_launches"], 1)
     outer_gbs = prof["outer_bytes"] / (outer_ms * 1e-3) / 1e9
     outer_gflops = 2.0 * prof["outer_fma"] / (outer_ms * 1e-3) / 1e9
@@ -299,6 +312,23 @@ def run_ours(args, rank, world, local):
 
     solve_e2e()
     ms_e2e = timed(max(2, args.steps // 2), solve_e2e)
+    # ---- set-up: fine-level batched block inversion by each factorisation
+    fact = {}
+    for fname, fcode in (("tf32_tensor_cores", FSI_FACTOR_TF32), ("fp32_cuda_cores", FSI_FACTOR_FP32),
+                         ("fp64_cuda_cores", FSI_FACTOR_FP64)):
+        t0 = time.time()
+        s.profile(1)
+        s.setup_smoothers(precision=FSI_MIXED_HALF, factor=fcode)
+        torch.cuda.synchronize()
+        pf = s.profile(0)
+        inv_ms = pf["invert_ms"] / max(pf["invert_launches"], 1)
+        fact[fname] = {"fine_inversion_ms": inv_ms, "fine_blocks": pf["fine_blocks"],
+                       "gflop": pf["invert_flops"] / 1e9,
+                       "achieved_tflops": pf["invert_flops"] / (inv_ms * 1e-3) / 1e12,
+                       "smoothers_setup_s": time.time() - t0}
+    tf32_peak = measured_tf32_peak()
+    fact["tf32_tensor_cores"]["frac_of_tf32_peak"] = fact["tf32_tensor_cores"]["achieved_tflops"] / tf32_peak
+    fact["tf32_peak_tflops"] = tf32_peak
     # ---- mixed precision with float32 block inverses
     t0 = time.time()
     s.setup_smoothers(precision=FSI_MIXED)
@@ -373,9 +403,15 @@ def run_ours(args, rank, world, local):
     p3 = I.make_config(2)
     t0 = time.time()
     s3 = FSISolver(p3, stream=stream)
+    torch.cuda.synchronize()
+    setup_3d_hier_s = time.time() - t0
+    t0 = time.time()
+    s3.profile(1)
     s3.setup_smoothers(precision=FSI_MIXED_HALF)
     torch.cuda.synchronize()
-    setup_3d_s = time.time() - t0
+    pf3 = s3.profile(0)
+    setup_3d_smooth_s = time.time() - t0
+    inv3_ms = pf3["invert_ms"] / max(pf3["invert_launches"], 1)
     n3 = s3.sizes(p3.n_levels - 1)["n"]
     f3, c3_, nd3 = s3.dof_map(p3.n_levels - 1)
     b3 = torch.from_numpy(I.gather_natural(I.natural_vector(p3, 1), f3.astype(np.int64), c3_.astype(np.int64),
@@ -427,11 +463,16 @@ def run_ours(args, rank, world, local):
                     "workload": "64 seeded 2D channels, fine grids {32,48,64,96,128}^2, band width U[0.1,0.4]"},
         "valve3d": {"workload": p3.name, "unknowns": n3, "ms_per_solve": ms_3d,
                     "dof_per_s": world * n3 / (ms_3d * 1e-3), "iterations": st3.get("iterations"),
-                    "setup_s": setup_3d_s, "omega": p3.omega,
+                    "setup_s": {"hierarchy": setup_3d_hier_s, "smoothers": setup_3d_smooth_s,
+                                "fine_inversion_ms": inv3_ms,
+                                "fine_inversion_tflops": pf3["invert_flops"] / (inv3_ms * 1e-3) / 1e12,
+                                "factor": "tf32_tensor_cores"},
+                    "omega": p3.omega,
                     "smoother_fine": {"mean_launch_ms": sm3, "achieved_gbs": pr3["smoother_bytes"] / sm3 / 1e6,
                                       "frac": pr3["smoother_bytes"] / sm3 / 1e6 / peak}},
         "adjoint": {"workload": pa.name, "unknowns": na, "ms_forward_plus_adjoint": ms_adj,
                     "iterations": astats, "dof_per_s": world * na / (ms_adj * 1e-3)},
+        "factorization": fact,
         "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed_half": setup_mixed_s,
                     "smoothers_mixed_f32": setup_f32_s, "smoothers_fp64": setup_fp64_s},
         "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
@@ -441,6 +482,8 @@ def run_ours(args, rank, world, local):
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
                      "algorithmic_bytes_per_launch": prof["smoother_bytes"], "mean_launch_ms": sm_ms,
                      "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms},
+                     "restriction_fine": {"achieved": rst_gbs, "frac": rst_gbs / peak, "mean_launch_ms": rst_ms},
+                     "prolongation_fine": {"achieved": pro_gbs, "frac": pro_gbs / peak, "mean_launch_ms": pro_ms},
                      "outer_spmv_f64": {"achieved_gbs": outer_gbs, "frac_hbm": outer_gbs / peak,
                                         "achieved_fp64_gflops": outer_gflops,
                                         "frac_fp64_nominal": outer_gflops / FP64_NOMINAL_GFLOPS,

@@ -232,13 +232,18 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * mode 1: reset the counters and start recording CUDA events around the
  * fine-level smoother apply and fine-level residual SpMV launches of the
  * following solves; mode 0: stop recording; mode 2: read only.
- * out (host, 12 doubles): [0] smoother launches timed, [1] their total ms,
+ * out (host, 24 doubles): [0] smoother launches timed, [1] their total ms,
  * [2] algorithmic bytes per smoother launch (block inverses, index, weight,
  * gather and scatter traffic), [3] SpMV launches timed, [4] their total ms,
  * [5] algorithmic bytes per SpMV launch, [6] kernels launched by the library
  * since the last reset, [7] outer float64 products w = A z_j timed, [8] their
  * total ms, [9] algorithmic bytes per product, [10] nonzeros of the fine
- * operator (one float64 FMA each), [11] reserved.  Problem 0. */
+ * operator (one float64 FMA each), [11] fine-level block inversions timed
+ * (fsi_setup_smoothers while recording), [12] their total ms, [13] flops of
+ * one fine-level inversion (2 n_j^3 summed over blocks), [14] fine blocks,
+ * [15] fine-level restrictions timed, [16] their ms, [17] algorithmic bytes
+ * per restriction, [18] fine-level prolongations timed, [19] their ms,
+ * [20] algorithmic bytes per prolongation, [21..23] reserved.  Problem 0. */
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
 
 /* Host-only inspection context: builds the levels, numbering, operator

@@ -253,12 +253,15 @@ class FSISolver:
     def profile(self, mode):
         """mode 1 start (reset), 0 stop, 2 read.  Returns the counters of
         fsi_profile as a dict."""
-        out = np.zeros(12, np.float64)
+        out = np.zeros(24, np.float64)
         _check(load_library().fsi_profile(self.ctx, mode, _ptr(out, C.c_double)))
         return {"smoother_launches": int(out[0]), "smoother_ms": out[1], "smoother_bytes": out[2],
                 "spmv_launches": int(out[3]), "spmv_ms": out[4], "spmv_bytes": out[5],
                 "kernel_launches": int(out[6]), "outer_launches": int(out[7]), "outer_ms": out[8],
-                "outer_bytes": out[9], "outer_fma": out[10]}
+                "outer_bytes": out[9], "outer_fma": out[10], "invert_launches": int(out[11]),
+                "invert_ms": out[12], "invert_flops": out[13], "fine_blocks": int(out[14]),
+                "restrict_launches": int(out[15]), "restrict_ms": out[16], "restrict_bytes": out[17],
+                "prolong_launches": int(out[18]), "prolong_ms": out[19], "prolong_bytes": out[20]}
 
     # ------------------------------------------------------------ accessors
     @property

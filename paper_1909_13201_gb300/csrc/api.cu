@@ -202,9 +202,15 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
         ProfMark pm(cx, 1, fine);
         FSI_TRY(launch_spmv<T, T, T>(A, mval<T>(A), x, b, r, SPMV_RESID, s));
     }
-    FSI_TRY(launch_spmv<T, T, T>(Rm, mval<T>(Rm), r, (const T *)nullptr, C.b.as<T>(), SPMV_SET, s));
+    {
+        ProfMark pm(cx, 4, fine);
+        FSI_TRY(launch_spmv<T, T, T>(Rm, mval<T>(Rm), r, (const T *)nullptr, C.b.as<T>(), SPMV_SET, s));
+    }
     FSI_TRY(vcycle<T>(cx, pb, l - 1, C.b.as<T>(), C.x.as<T>(), tr));
-    FSI_TRY(launch_spmv<T, T, T>(Pm, mval<T>(Pm), C.x.as<T>(), (const T *)nullptr, x, SPMV_ADD, s));
+    {
+        ProfMark pm(cx, 5, fine);
+        FSI_TRY(launch_spmv<T, T, T>(Pm, mval<T>(Pm), C.x.as<T>(), (const T *)nullptr, x, SPMV_ADD, s));
+    }
     for (int k = 0; k < npost; ++k) {
         {
             ProfMark pm(cx, 1, fine);
@@ -811,10 +817,13 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
         int method = cx.factor;
         if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
-        if (method == FSI_FACTOR_FP64)
-            FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
-        else
-            FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
+        {
+            ProfMark pm(cx, 3, l + 1 == pb.dev.size());
+            if (method == FSI_FACTOR_FP64)
+                FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
+            else
+                FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
+        }
         int flag = 0;
         FSI_TRY(read_flag(cx, &flag));
         if (flag) {
@@ -968,6 +977,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     cx->smoothers_ready = false;
     for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
     FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    if (!cx->ev_marks.empty()) collect_marks(*cx);
     cx->smoothers_ready = true;
     return FSI_OK;
 }
@@ -1373,7 +1383,7 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     if (!cx || !out || mode < 0 || mode > 2) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
     if (mode == 1) {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 6; ++k) {
             cx->prof_ms[k] = 0;
             cx->prof_n[k] = 0;
         }
@@ -1406,7 +1416,24 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     out[8] = cx->prof_ms[2];
     out[9] = (double)F.A.nnz * 12.0 + (double)(F.n + 1) * 4.0 + (double)F.n * 2.0 * 8.0;   // float64 A z
     out[10] = (double)F.A.nnz;
-    out[11] = 0.0;
+    out[11] = (double)cx->prof_n[3];
+    out[12] = cx->prof_ms[3];
+    double gj = 0.0;                                   // Gauss-Jordan inversion: 2 n^3 flops per block
+    for (int64_t j = 0; j + 1 < (int64_t)F.h_blk_ptr.size(); ++j) {
+        const double nj = (double)(F.h_blk_ptr[j + 1] - F.h_blk_ptr[j]);
+        gj += 2.0 * nj * nj * nj;
+    }
+    out[13] = gj;
+    out[14] = (double)F.n_blocks;
+    // fine-level transfers (float32 cycle: 4-byte values and vectors)
+    const LevelDev &Cl = pb.dev[pb.dev.size() >= 2 ? pb.dev.size() - 2 : 0];
+    out[15] = (double)cx->prof_n[4];
+    out[16] = cx->prof_ms[4];
+    out[17] = (double)F.R.nnz * (ts + 4.0) + (double)(Cl.n + 1) * 4.0 + (double)F.n * ts + (double)Cl.n * ts;
+    out[18] = (double)cx->prof_n[5];
+    out[19] = cx->prof_ms[5];
+    out[20] = (double)F.P.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)Cl.n * ts + 2.0 * (double)F.n * ts;
+    out[21] = out[22] = out[23] = 0.0;
     return FSI_OK;
 }
 

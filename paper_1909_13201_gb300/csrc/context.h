@@ -161,8 +161,10 @@ struct Context {
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;   // kind, start/stop
-    double prof_ms[3] = {0, 0, 0};     // fine smoother, fine residual SpMV, outer float64 A z
-    int64_t prof_n[3] = {0, 0, 0};
+    // fine smoother, fine residual SpMV, outer float64 A z, fine block
+    // inversion (set-up), fine restriction, fine prolongation
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
     int64_t launch_base = 0;
     // solves run on a context-owned non-blocking stream
     cudaStream_t work = nullptr;

@@ -6,9 +6,9 @@
 // The block's rows live in shared memory (float32, row-major), split over a
 // thread-block cluster of C CTAs when they do not fit one CTA.  Columns are
 // eliminated in panels of 32:
-//   1. the CTA owning the panel's 32 rows runs unblocked Gauss-Jordan on
-//      those rows only: afterwards they hold Rp = D^{-1} M[K, :] with the
-//      panel columns replaced by D^{-1} (D = M[K, K]);
+//   1. the CTA owning the panel's 32 rows inverts D = M[K, K] (one warp,
+//      Gauss-Jordan on 32 x 32 in shared memory) and forms
+//      Rp = D^{-1} M[K, :] with the panel columns replaced by D^{-1};
 //   2. Rp is written, transposed and rounded to TF32, into every CTA's
 //      operand buffer (distributed shared memory), then a cluster barrier;
 //   3. every CTA builds F = -M[rows, K] (zero on the panel rows), zeroes
@@ -40,6 +40,7 @@ namespace {
 constexpr int TC_THREADS = 256;
 constexpr int PANEL = 32;
 constexpr int CM_SBO = 1024, CM_LBO = 128;
+constexpr size_t MISC_BYTES = 64 + PANEL * 33 * 4 + 64;   // mbarrier, TMEM slot, flags, Dm
 
 struct GJTCParams {
     const int32_t *blk_ptr, *blk_idx;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
     uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 8);
     int *sflag = reinterpret_cast<int *>(misc + 12);    // [0] bad pivot, [1] wait timeout
-    float *fcol = reinterpret_cast<float *>(misc + 64); // [PANEL] panel column of the panel rows
+    float *Dm = reinterpret_cast<float *>(misc + 64);   // [PANEL][33] panel diagonal block / its inverse
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
     if (TC && warp == 0) {
@@ -138,37 +139,62 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
     for (int p = 0; p < npanels; ++p) {
         const int k0 = p * PANEL, kw = min(PANEL, n - k0);
         const int owner = k0 / R;
-        // ---- 1. panel Gauss-Jordan on the owner's 32 rows
+        // ---- 1. owner: Dinv = D^{-1} (D = M[K, K], one warp, padded with the
+        //         identity to 32 x 32), then Rp = Dinv M[K, :] in place, with
+        //         the panel columns of Rp equal to Dinv
         if (rank == owner) {
             const int lb = k0 - r0;                     // first panel row (local)
-            for (int t = 0; t < kw; ++t) {
-                const int c = k0 + t;
-                float *prow = Ms + (size_t)(lb + t) * ldm;
-                float piv = prow[c];
-                if (tid < kw) fcol[tid] = Ms[(size_t)(lb + tid) * ldm + c];
-                __syncthreads();
-                if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
-                    if (tid == 0) sflag[0] = 1;
-                    piv = 1.f;
+            for (int e = tid; e < PANEL * PANEL; e += blockDim.x) {
+                const int t = e / PANEL, u = e - t * PANEL;
+                Dm[t * 33 + u] = (t < kw && u < kw) ? Ms[(size_t)(lb + t) * ldm + k0 + u] : (t == u ? 1.f : 0.f);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                for (int t = 0; t < PANEL; ++t) {
+                    float piv = Dm[t * 33 + t];
+                    if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
+                        if (lane == 0) sflag[0] = 1;
+                        piv = 1.f;
+                    }
+                    const float ip = 1.f / piv;
+                    const float f = Dm[lane * 33 + t];
+                    __syncwarp();
+                    Dm[t * 33 + lane] = (lane == t) ? ip : Dm[t * 33 + lane] * ip;     // lane = column
+                    __syncwarp();
+                    if (lane != t) {
+                        for (int u = 0; u < PANEL; ++u)
+                            Dm[lane * 33 + u] = (u == t) ? -f * ip : fmaf(-f, Dm[t * 33 + u], Dm[lane * 33 + u]);
+                    }
+                    __syncwarp();
                 }
-                const float ip = 1.f / piv;
-                for (int j = tid; j < n; j += blockDim.x) prow[j] = (j == c) ? ip : prow[j] * ip;
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < n; j0 += PANEL) {
+                float acc[PANEL * PANEL / TC_THREADS];
+#pragma unroll
+                for (int q = 0; q < PANEL * PANEL / TC_THREADS; ++q) {
+                    const int e = tid + q * TC_THREADS, t = e / PANEL, j = j0 + (e & (PANEL - 1));
+                    float a = 0.f;
+                    if (t < kw && j < n)
+                        for (int u = 0; u < kw; ++u) a = fmaf(Dm[t * 33 + u], Ms[(size_t)(lb + u) * ldm + j], a);
+                    acc[q] = a;
+                }
                 __syncthreads();
-                for (int e = tid; e < kw * n; e += blockDim.x) {
-                    const int u = e / n, j = e - u * n;
-                    if (u == t) continue;
-                    const float f = fcol[u];
-                    float *urow = Ms + (size_t)(lb + u) * ldm;
-                    urow[j] = (j == c) ? -f * ip : fmaf(-f, prow[j], urow[j]);
+#pragma unroll
+                for (int q = 0; q < PANEL * PANEL / TC_THREADS; ++q) {
+                    const int e = tid + q * TC_THREADS, t = e / PANEL, j = j0 + (e & (PANEL - 1));
+                    if (t < kw && j < n)
+                        Ms[(size_t)(lb + t) * ldm + j] = (j >= k0 && j < k0 + kw) ? Dm[t * 33 + (j - k0)] : acc[q];
                 }
                 __syncthreads();
             }
-            // ---- 2. Rp^T (TF32) into every CTA's B buffer, zero-padded
+            // ---- 2. Rp^T (TF32) into every CTA's B buffer, zero-padded; the
+            //         thread order walks each 8 x 16-byte core matrix contiguously
             for (int dst = 0; dst < C; ++dst) {
                 unsigned char *bd = Bs;
                 if (C > 1) bd = reinterpret_cast<unsigned char *>(cluster.map_shared_rank(Bs, dst));
                 for (int e = tid; e < npad * PANEL; e += blockDim.x) {
-                    const int j = e / PANEL, t = e - j * PANEL;
+                    const int t = (e & 3) | (((e >> 5) & 7) << 2), j = ((e >> 2) & 7) | ((e >> 8) << 3);
                     const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
                     *reinterpret_cast<float *>(bd + cm_off(j, t)) = TC ? to_tf32(v) : v;
                 }
@@ -179,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
         const bool own = rank == owner;
         const int lb = k0 - r0;
         for (int e = tid; e < P.tiles * 128 * PANEL; e += blockDim.x) {
-            const int li = e / PANEL, t = e - li * PANEL;
+            const int t = (e & 3) | (((e >> 5) & 7) << 2), li = ((e >> 2) & 7) | ((e >> 8) << 3);
             float v = 0.f;
             if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) {
                 v = -Ms[(size_t)li * ldm + k0 + t];
@@ -348,7 +374,7 @@ bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out) {
         const size_t m_bytes = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
         const size_t f_bytes = (size_t)tiles * 16384;
         const size_t b_bytes = ((size_t)npad * 128 + 1023) & ~(size_t)1023;
-        size_t total = m_bytes + f_bytes + b_bytes + 256;
+        size_t total = m_bytes + f_bytes + b_bytes + MISC_BYTES;
         // a cluster's CTAs must not share an SM: each holds its tensor-memory
         // columns until the last cluster barrier, so a second CTA of the same
         // cluster waiting in tcgen05.alloc on that SM would never proceed
