@@ -7,10 +7,11 @@
 // thread-block cluster of C CTAs when they do not fit one CTA.  Columns are
 // eliminated in panels of 32:
 //   1. the CTA owning the panel's 32 rows inverts D = M[K, K] (one warp,
-//      Gauss-Jordan on 32 x 32 in shared memory) and forms
+//      Gauss-Jordan on 32 x 32 in registers, lane j holding column j) and forms
 //      Rp = D^{-1} M[K, :] with the panel columns replaced by D^{-1};
-//   2. Rp is written, transposed and rounded to TF32, into every CTA's
-//      operand buffer (distributed shared memory), then a cluster barrier;
+//   2. Rp is written, transposed and rounded to TF32, into the owner's
+//      operand buffer; after a cluster barrier the other CTAs copy it over
+//      distributed shared memory;
 //   3. every CTA builds F = -M[rows, K] (zero on the panel rows), zeroes
 //      M[rows, K], and one thread issues D_tmem = F x Rp (M = 128 rows per
 //      MMA, N <= 256 columns, K = 8 per instruction, 4 instructions);
@@ -81,7 +82,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int C, bool TC>
-__global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
+__global__ void __launch_bounds__(TC_THREADS, 1) block_gj_tc_kernel(GJTCParams P) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (C > 1) ? (int)cluster.block_rank() : 0;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
     uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 8);
     int *sflag = reinterpret_cast<int *>(misc + 12);    // [0] bad pivot, [1] wait timeout
     float *Dm = reinterpret_cast<float *>(misc + 64);   // [PANEL][33] panel diagonal block / its inverse
+    int32_t *sidx = reinterpret_cast<int32_t *>(misc + MISC_BYTES);   // [n] block indices (sorted)
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
     if (TC && warp == 0) {
@@ -113,21 +115,56 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
         sflag[1] = 0;
         if (TC) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     }
-    // gather the local rows (float64 CSR -> float32)
+    // gather the local rows (float64 CSR -> float32).  The CTA's nonzeros
+    // are walked as one flat range (row of entry e by binary search over the
+    // row offsets), so every thread keeps independent global loads in flight;
+    // column positions by binary search in the block's sorted index list.
+    int *roff = reinterpret_cast<int *>(sidx + ((n + 3) & ~3));   // [R + 1] flat offsets
+    int *rbeg = roff + R + 1;                                      // [R] CSR start of each row
     for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
+    for (int t = tid; t < n; t += blockDim.x) sidx[t] = idx[t];
     __syncthreads();
-    for (int li = warp; li < nr; li += TC_THREADS / 32) {
-        const int g = idx[r0 + li];
-        for (int k = P.row_ptr[g] + lane; k < P.row_ptr[g + 1]; k += 32) {
-            const int c = P.col[k];
-            int lo = 0, hi = n, pos = -1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1, v = idx[mid];
-                if (v == c) { pos = mid; break; }
-                if (v < c) lo = mid + 1; else hi = mid;
+    for (int li = tid; li < nr; li += blockDim.x) {
+        const int g = sidx[r0 + li];
+        const int a = P.row_ptr[g];
+        rbeg[li] = a;
+        roff[li + 1] = P.row_ptr[g + 1] - a;                       // length, scanned below
+    }
+    __syncthreads();
+    if (warp == 0) {                                               // exclusive scan of the lengths
+        int carry = 0;
+        if (lane == 0) roff[0] = 0;
+        for (int b0 = 0; b0 < nr; b0 += 32) {
+            const int li = b0 + lane;
+            int v = li < nr ? roff[li + 1] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int w = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += w;
             }
-            if (pos >= 0) Ms[(size_t)li * ldm + pos] = (float)P.val[k];
+            if (li < nr) roff[li + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
+    }
+    __syncthreads();
+    const int total = roff[nr];
+#pragma unroll 4
+    for (int e = tid; e < total; e += blockDim.x) {
+        int lo = 0, hi = nr;                                       // largest li with roff[li] <= e
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (roff[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int k = rbeg[lo] + (e - roff[lo]);
+        const int c = P.col[k];
+        const float v = (float)P.val[k];
+        int a = 0, b = n, pos = -1;
+        while (a < b) {
+            const int mid = (a + b) >> 1, w = sidx[mid];
+            if (w == c) { pos = mid; break; }
+            if (w < c) a = mid + 1; else b = mid;
+        }
+        if (pos >= 0) Ms[(size_t)lo * ldm + pos] = v;
     }
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -150,57 +187,75 @@ __global__ void __launch_bounds__(TC_THREADS) block_gj_tc_kernel(GJTCParams P) {
             }
             __syncthreads();
             if (warp == 0) {
+                // lane j holds column j of D; row t of the pivot step and the
+                // multipliers D[u][t] come from lane t by shuffles
+                float d[PANEL];
+#pragma unroll
+                for (int u = 0; u < PANEL; ++u) d[u] = Dm[u * 33 + lane];
+                bool bad = false;
+#pragma unroll
                 for (int t = 0; t < PANEL; ++t) {
-                    float piv = Dm[t * 33 + t];
+                    float piv = __shfl_sync(0xffffffffu, d[t], t);
                     if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
-                        if (lane == 0) sflag[0] = 1;
+                        bad = true;
                         piv = 1.f;
                     }
                     const float ip = 1.f / piv;
-                    const float f = Dm[lane * 33 + t];
-                    __syncwarp();
-                    Dm[t * 33 + lane] = (lane == t) ? ip : Dm[t * 33 + lane] * ip;     // lane = column
-                    __syncwarp();
-                    if (lane != t) {
-                        for (int u = 0; u < PANEL; ++u)
-                            Dm[lane * 33 + u] = (u == t) ? -f * ip : fmaf(-f, Dm[t * 33 + u], Dm[lane * 33 + u]);
+                    const float rt = (lane == t) ? ip : d[t] * ip;
+#pragma unroll
+                    for (int u = 0; u < PANEL; ++u) {
+                        if (u == t) continue;
+                        const float f = __shfl_sync(0xffffffffu, d[u], t);
+                        d[u] = (lane == t) ? -f * ip : fmaf(-f, rt, d[u]);
                     }
-                    __syncwarp();
+                    d[t] = rt;
                 }
+#pragma unroll
+                for (int u = 0; u < PANEL; ++u) Dm[u * 33 + lane] = d[u];
+                if (bad && lane == 0) sflag[0] = 1;
             }
             __syncthreads();
             for (int j0 = 0; j0 < n; j0 += PANEL) {
-                float acc[PANEL * PANEL / TC_THREADS];
+                // thread: column j = j0 + lane, rows t = warp + 8 q (q < 4)
+                constexpr int QN = PANEL * PANEL / TC_THREADS;
+                float acc[QN];
 #pragma unroll
-                for (int q = 0; q < PANEL * PANEL / TC_THREADS; ++q) {
-                    const int e = tid + q * TC_THREADS, t = e / PANEL, j = j0 + (e & (PANEL - 1));
-                    float a = 0.f;
-                    if (t < kw && j < n)
-                        for (int u = 0; u < kw; ++u) a = fmaf(Dm[t * 33 + u], Ms[(size_t)(lb + u) * ldm + j], a);
-                    acc[q] = a;
+                for (int q = 0; q < QN; ++q) acc[q] = 0.f;
+                const int jj = j0 + lane;
+                if (jj < n) {
+                    for (int u = 0; u < kw; ++u) {
+                        const float m = Ms[(size_t)(lb + u) * ldm + jj];
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) acc[q] = fmaf(Dm[(warp + 8 * q) * 33 + u], m, acc[q]);
+                    }
                 }
                 __syncthreads();
 #pragma unroll
-                for (int q = 0; q < PANEL * PANEL / TC_THREADS; ++q) {
-                    const int e = tid + q * TC_THREADS, t = e / PANEL, j = j0 + (e & (PANEL - 1));
-                    if (t < kw && j < n)
-                        Ms[(size_t)(lb + t) * ldm + j] = (j >= k0 && j < k0 + kw) ? Dm[t * 33 + (j - k0)] : acc[q];
+                for (int q = 0; q < QN; ++q) {
+                    const int t = warp + 8 * q;
+                    if (t < kw && jj < n)
+                        Ms[(size_t)(lb + t) * ldm + jj] = (jj >= k0 && jj < k0 + kw) ? Dm[t * 33 + (jj - k0)] : acc[q];
                 }
                 __syncthreads();
             }
-            // ---- 2. Rp^T (TF32) into every CTA's B buffer, zero-padded; the
+            // ---- 2. Rp^T (TF32) into the owner's B buffer, zero-padded; the
             //         thread order walks each 8 x 16-byte core matrix contiguously
-            for (int dst = 0; dst < C; ++dst) {
-                unsigned char *bd = Bs;
-                if (C > 1) bd = reinterpret_cast<unsigned char *>(cluster.map_shared_rank(Bs, dst));
-                for (int e = tid; e < npad * PANEL; e += blockDim.x) {
-                    const int t = (e & 3) | (((e >> 5) & 7) << 2), j = ((e >> 2) & 7) | ((e >> 8) << 3);
-                    const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
-                    *reinterpret_cast<float *>(bd + cm_off(j, t)) = TC ? to_tf32(v) : v;
-                }
+            for (int e = tid; e < npad * PANEL; e += blockDim.x) {
+                const int t = (e & 3) | (((e >> 5) & 7) << 2), j = ((e >> 2) & 7) | ((e >> 8) << 3);
+                const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
+                *reinterpret_cast<float *>(Bs + cm_off(j, t)) = TC ? to_tf32(v) : v;
             }
         }
-        if (C > 1) cluster.sync(); else __syncthreads();
+        if (C > 1) {
+            cluster.sync();
+            // the other CTAs copy the owner's operand (16-byte DSMEM reads, in parallel)
+            if (rank != owner) {
+                const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(Bs, owner));
+                float4 *dstp = reinterpret_cast<float4 *>(Bs);
+                for (int e = tid; e < npad * PANEL / 4; e += blockDim.x) dstp[e] = src[e];
+            }
+        }
+        __syncthreads();
         // ---- 3. F = -M[rows, K] (0 on the panel rows), zero M[rows, K]
         const bool own = rank == owner;
         const int lb = k0 - r0;
@@ -374,7 +429,8 @@ bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out) {
         const size_t m_bytes = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
         const size_t f_bytes = (size_t)tiles * 16384;
         const size_t b_bytes = ((size_t)npad * 128 + 1023) & ~(size_t)1023;
-        size_t total = m_bytes + f_bytes + b_bytes + MISC_BYTES;
+        // misc: barrier, flags, Dm; then the block's indices and the row offsets
+        size_t total = m_bytes + f_bytes + b_bytes + MISC_BYTES + (size_t)(((n + 3) & ~3) + 2 * R + 4) * 4;
         // a cluster's CTAs must not share an SM: each holds its tensor-memory
         // columns until the last cluster barrier, so a second CTA of the same
         // cluster waiting in tcgen05.alloc on that SM would never proceed
