@@ -241,6 +241,7 @@ fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
     drop_graphs(pb);
     const int64_t n = pb.dev.back().n;
     FSI_TRY(pb.V.alloc((size_t)n * (m + 1) * 8));
+    FSI_TRY(pb.V32.alloc((size_t)n * (m + 1) * 4));
     FSI_TRY(pb.Z.alloc((size_t)n * m * 8));     // float64: the outer SpMV reads it without conversions
     FSI_TRY(pb.H.alloc((size_t)(m + 1) * m * 8));
     FSI_TRY(pb.g.alloc((size_t)(m + 2) * 8));
@@ -320,7 +321,9 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
     }
     const int nv = j + 1;
     double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
-    FSI_TRY(launch_mdot(V, n, nv, w, n, part, NRED, s));
+    float *V32 = cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr;
+    if (V32) FSI_TRY(launch_mdot32(V32, n, nv, w, n, part, NRED, s));
+    else FSI_TRY(launch_mdot(V, n, nv, w, n, part, NRED, s));
     FSI_TRY(launch_reduce_partials(part, NRED, nv, h1, 0, s));
     FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s));
     FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
@@ -328,7 +331,8 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
     FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
     FSI_TRY(launch_givens(H, m + 1, j, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s));
     FSI_CUDA(cudaMemcpyAsync(pb.h_scal, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
-    FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s));
+    FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s, nullptr, 0,
+                              V32 ? V32 + (size_t)(j + 1) * n : nullptr));
     return FSI_OK;
 }
 
@@ -356,7 +360,8 @@ fsi_status enqueue(Context &cx, Run &R) {
             FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), R.x, R.b, r, SPMV_RESID, s));
             return norm2_to_host(cx, pb, r, n, 6);
         case Run::CYCLE:
-            FSI_TRY(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, pb.scal.as<double>() + 6, n, s));
+            FSI_TRY(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, pb.scal.as<double>() + 6, n, s,
+                                      nullptr, 0, cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr));
             R.j = 0;
             // fall through: the first step of the cycle goes in the same round
         case Run::STEP: {
@@ -1026,7 +1031,9 @@ fsi_status issue_step_dev_tail(Context &cx, Problem &pb, int m, int nv_bound, cu
     double *V = pb.V.as<double>(), *H = pb.H.as<double>(), *g = pb.g.as<double>();
     double *w = pb.w.as<double>(), *scal = pb.scal.as<double>();
     double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
-    FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NRED, s, fg));
+    float *V32 = cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr;
+    if (V32) FSI_TRY(launch_mdot32(V32, n, nv_bound, w, n, part, NRED, s, fg));
+    else FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NRED, s, fg));
     FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h1, 0, s, fg));
     FSI_TRY(launch_update_dot(w, V, n, nv_bound, h1, n, part, NRED, 0, s, fg));
     FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h2, 0, s, fg));
@@ -1034,7 +1041,7 @@ fsi_status issue_step_dev_tail(Context &cx, Problem &pb, int m, int nv_bound, cu
     FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
     FSI_TRY(launch_givens(H, m + 1, 0, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s, fg,
                           loop));
-    FSI_TRY(launch_scale_copy(w, V, scal, 1, n, s, fg, n));
+    FSI_TRY(launch_scale_copy(w, V, scal, 1, n, s, fg, n, V32));
     return FSI_OK;
 }
 
@@ -1120,7 +1127,8 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
     FSI_CAPCUDA(cudaStreamBeginCaptureToGraph(s1, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     capturing = 2;
     cx.stream = s1;
-    FSI_CAP(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, scal + 6, n, s1, fg, h_in));
+    FSI_CAP(launch_init_basis(r, pb.V.as<double>(), pb.g.as<double>(), m, scal + 6, n, s1, fg, h_in,
+                              cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr));
     FSI_CAP(add_conditional(s1, h_in, cudaGraphCondTypeWhile, 1, &w_in, &body_in));
     // inner loop: Arnoldi steps
     const int64_t c2 = launches_so_far();

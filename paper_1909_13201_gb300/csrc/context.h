@@ -123,6 +123,7 @@ struct Problem {
     // Krylov workspace (fine level)
     int m_alloc = 0;
     DevBuf V, Z, H, g, cs, sn, y, w, rvec, xwork, partials, scal, h1, h2;
+    DevBuf V32;                      // float32 copy of the basis (first Gram-Schmidt pass, mixed modes)
     // one CUDA graph per Arnoldi step j (index 0: forward, 1: transposed)
     std::vector<cudaGraphExec_t> graphs[2];
     cudaStream_t stream = nullptr;   // the problem's own solve stream
@@ -220,8 +221,12 @@ fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, d
 fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2,
                          const double *hn2, double *cs, double *sn, double *g, double *scal,
                          cudaStream_t s, FgState *fg = nullptr, cudaGraphConditionalHandle loop = 0);
+// v = w / scal[idx] (and its float32 copy v32 when non-null)
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
-                             cudaStream_t s, const FgState *fg = nullptr, int64_t ld = 0);
+                             cudaStream_t s, const FgState *fg = nullptr, int64_t ld = 0, float *v32 = nullptr);
+// first Gram-Schmidt pass from the float32 copy of the basis (mixed modes)
+fsi_status launch_mdot32(const float *V, int64_t ld, int nv, const double *w, int64_t n, double *partials,
+                         int nblocks, cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_backsolve(const double *H, int ld, int k, const double *g, double *y,
                             cudaStream_t s, const FgState *fg = nullptr);
 template <class T>
@@ -229,7 +234,7 @@ fsi_status launch_combine(double *x, const T *Z, int64_t ld, int k, const double
                           cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2,
                              int64_t n, cudaStream_t s, FgState *fg = nullptr,
-                             cudaGraphConditionalHandle loop = 0);
+                             cudaGraphConditionalHandle loop = 0, float *v0f = nullptr);
 // device-loop helpers: dst = (TO) V[:, fg->k]; zfix = Z[:, fg->k] = (double) z
 // take_column also selects the Gram-Schmidt variant of the step (SWITCH
 // node `sel`, value nv_class(fg->k + 1)) when sel is nonzero

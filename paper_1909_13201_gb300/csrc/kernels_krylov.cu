@@ -60,6 +60,33 @@ __global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, 
     block_reduce_store<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
 }
 
+// First Gram-Schmidt pass of the mixed modes: h1 = V^T w from the float32
+// copy of the basis and w rounded to float32, float32 products and sums.
+// The second pass (float64) removes whatever this pass leaves, so h = h1 + h2
+// and the new basis vector keep float64 accuracy; the float32 pipe and the
+// halved basis bytes replace the float64 multiply-adds of a full pass.
+template <int NV>
+__global__ void __launch_bounds__(KT) mdot32_kernel(const float *__restrict__ V, int64_t ld, int nv,
+                                                    const double *__restrict__ w, int64_t n,
+                                                    double *__restrict__ partials, const FgState *fg) {
+    if (fg) nv = min(fg->k + 1, NV);
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+        const float wr = (float)w[r];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) acc[i] = fmaf(V[(size_t)i * ld + r], wr, acc[i]);
+    }
+    double accd[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) accd[i] = (double)acc[i];
+    block_reduce_store<NV>(accd, nv, partials + (size_t)blockIdx.x * KMAX);
+}
+
 template <int NV>
 __global__ void __launch_bounds__(KT) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
                                                         int64_t ld, int nv, const double *__restrict__ h,
@@ -176,28 +203,37 @@ __global__ void givens_kernel(double *H, int ld, int j, const double *h1, const 
 
 // v = w / scal[idx]; with a control block v is column fg->k of the basis
 // whose first column is v (leading dimension ld)
-__global__ void scale_copy_kernel(const double *__restrict__ w, double *__restrict__ v,
+__global__ void scale_copy_kernel(const double *__restrict__ w, double *__restrict__ v, float *__restrict__ v32,
                                   const double *__restrict__ scal, int idx, int64_t n, const FgState *fg,
                                   int64_t ld) {
-    if (fg) v += (size_t)fg->k * ld;
+    if (fg) {
+        v += (size_t)fg->k * ld;
+        if (v32) v32 += (size_t)fg->k * ld;
+    }
     const double inv = 1.0 / scal[idx];
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        v[r] = w[r] * inv;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double a = w[r] * inv;
+        v[r] = a;
+        if (v32) v32[r] = (float)a;
+    }
 }
 
 // start of a cycle: beta = sqrt(nrm2), v0 = r / beta, g = (beta, 0, ...)
 // (device-side loop: also k = 0 and the inner loop's condition set)
-__global__ void init_basis_kernel(const double *__restrict__ r, double *__restrict__ v0, double *__restrict__ g,
-                                  int m, const double *__restrict__ nrm2, int64_t n, FgState *fg,
-                                  cudaGraphConditionalHandle loop) {
+__global__ void init_basis_kernel(const double *__restrict__ r, double *__restrict__ v0, float *__restrict__ v0f,
+                                  double *__restrict__ g, int m, const double *__restrict__ nrm2, int64_t n,
+                                  FgState *fg, cudaGraphConditionalHandle loop) {
     if (fg && blockIdx.x == 0 && threadIdx.x == 0) {
         fg->k = 0;
         cudaGraphSetConditional(loop, 1u);
     }
     const double beta = sqrt(nrm2[0]);
     const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v0[i] = r[i] * inv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = r[i] * inv;
+        v0[i] = a;
+        if (v0f) v0f[i] = (float)a;
+    }
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta : 0.0;
 }
@@ -310,6 +346,17 @@ fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int
     return FSI_OK;
 }
 
+fsi_status launch_mdot32(const float *V, int64_t ld, int nv, const double *w, int64_t n, double *partials,
+                         int nblocks, cudaStream_t s, const FgState *fg) {
+    if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
+#define CALL_MDOT32(NV) mdot32_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials, fg)
+    FSI_NV_SWITCH(nv, CALL_MDOT32);
+#undef CALL_MDOT32
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
 fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
                              int64_t n, double *partials, int nblocks, int norm_only, cudaStream_t s,
                              const FgState *fg) {
@@ -340,16 +387,16 @@ fsi_status launch_givens(double *H, int ld, int j, const double *h1, const doubl
 }
 
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
-                             cudaStream_t s, const FgState *fg, int64_t ld) {
-    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, scal, idx, n, fg, ld);
+                             cudaStream_t s, const FgState *fg, int64_t ld, float *v32) {
+    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, v32, scal, idx, n, fg, ld);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, const double *nrm2, int64_t n,
-                             cudaStream_t s, FgState *fg, cudaGraphConditionalHandle loop) {
-    init_basis_kernel<<<egrid(n), 256, 0, s>>>(r, v0, g, m, nrm2, n, fg, loop);
+                             cudaStream_t s, FgState *fg, cudaGraphConditionalHandle loop, float *v0f) {
+    init_basis_kernel<<<egrid(n), 256, 0, s>>>(r, v0, v0f, g, m, nrm2, n, fg, loop);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;

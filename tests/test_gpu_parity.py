@@ -403,3 +403,26 @@ def test_float32_blocked_inversion(name):
         assert abs(st8["iterations"] - st64["iterations"]) <= 2, (st8["iterations"], st64["iterations"])
     with pytest.raises(binding.FSIError):
         binding.FSISolver(p).setup_smoothers(precision=binding.FSI_FP64, factor=binding.FSI_FACTOR_TF32)
+
+
+def test_batch_larger_than_hardware_queues():
+    """Ten systems (more than the 8 default hardware work queues) advance in
+    host-driven rounds; each result matches its own single solve."""
+    probs = [I.make_channel_2d(16 + 8 * (i % 3), 3, 1, 600 + i, band_width=0.15 + 0.02 * i,
+                               mu_s=100.0 + 40.0 * i) for i in range(10)]
+    sb = binding.FSISolver(probs)
+    sb.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    bs, refs, singles = [], [], []
+    for i, p in enumerate(probs):
+        H = gmg.Hierarchy(p)
+        b = _rhs(p, H, 70 + i)
+        bs.append(_cuda(b))
+        refs.append(_direct(H.fine, b))
+        s1 = binding.FSISolver(p)
+        s1.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+        singles.append(s1.solve(_cuda(b), rtol=1e-10)[1]["iterations"])
+    xs, sts = sb.solve_batched(bs, rtol=1e-10)
+    for x, ref, st, it1 in zip(xs, refs, sts, singles):
+        assert st["converged"]
+        assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+        assert abs(st["iterations"] - it1) <= 1
