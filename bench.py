@@ -200,8 +200,8 @@ def ncu_traffic():
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
             vals[k.strip()] = v.strip().split()[0]
     if vals.get("kernels_block.cu sha256[:16]") != sha:
         return None
