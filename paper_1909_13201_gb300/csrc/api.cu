@@ -65,7 +65,8 @@ fsi_status upload_csr(DevCSR &D, const HostCSR &H, cudaStream_t s) {
 fsi_status make_f32(DevCSR &D, cudaStream_t s) {
     if (D.val32.p || D.nnz == 0) return FSI_OK;
     FSI_TRY(D.val32.alloc((size_t)D.nnz * 4));
-    return launch_cast_f64_f32(D.val64.as<double>(), D.val32.as<float>(), D.nnz, s);
+    FSI_TRY(launch_cast_f64_f32(D.val64.as<double>(), D.val32.as<float>(), D.nnz, s));
+    return ell_fill_f32(D, s);
 }
 
 // device CSR -> host CSR (with values)
@@ -583,12 +584,15 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
         FSI_TRY(download_csr(L.A, A, s));
         transpose_csr(A, AT);
         FSI_TRY(upload_csr(L.AT, AT, s));
+        FSI_TRY(build_ell(L.AT, s, cx.probs.size() > 1));
         if (l >= 1) {
             HostCSR PT, RT;
             transpose_csr(pb.hP[l], PT);
             transpose_csr(pb.hR[l], RT);
             FSI_TRY(upload_csr(L.PT, PT, s));
             FSI_TRY(upload_csr(L.RT, RT, s));
+            FSI_TRY(build_ell(L.PT, s, cx.probs.size() > 1));
+            FSI_TRY(build_ell(L.RT, s, cx.probs.size() > 1));
         }
         if (cx.precision != FSI_FP64) {
             FSI_TRY(make_f32(L.AT, s));
@@ -664,12 +668,15 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
         FSI_TRY(upload_csr(D.A, H.pattern, s));
         FSI_TRY(D.A.val64.alloc((size_t)D.A.nnz * 8));
         FSI_TRY(launch_assemble(H, d, ref, D.A, false, D.A.val64.as<double>(), s));
+        FSI_TRY(build_ell(D.A, s, cx.probs.size() > 1));
         FSI_TRY(upload(D.fixed, H.fixed.data(), H.fixed.size(), s));
         if (l >= 1) {
             build_prolongation(H, pb.host[l - 1], pb.hP[l]);
             build_restriction(pb.hP[l], H, pb.host[l - 1], cx.restriction == 1, pb.hR[l]);
             FSI_TRY(upload_csr(D.P, pb.hP[l], s));
             FSI_TRY(upload_csr(D.R, pb.hR[l], s));
+            FSI_TRY(build_ell(D.P, s, cx.probs.size() > 1));
+            FSI_TRY(build_ell(D.R, s, cx.probs.size() > 1));
         }
     }
     // dA/dmu_s on the fine pattern (adjoint gradient)

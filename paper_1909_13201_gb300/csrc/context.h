@@ -60,12 +60,41 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Length-binned ELL copy of a CSR operator, the layout the solve-path
+// products stream.  Rows are sorted by their number of nonzeros (stable, so
+// rows of one length keep their order) and grouped into bins of equal
+// length; bin b stores its rows column-major, entry k of sorted row t at
+// off + k * stride + t with stride = rows rounded up to 32, so a warp of 32
+// consecutive rows reads every entry position as one coalesced 128-byte
+// line and needs no row pointers.  Padding entries hold column 0, value 0.
+// A warp takes one slab of 32 / G rows, G lanes per row.
+struct EllBin {
+    int64_t off;          // first stored entry of the bin
+    int32_t rows, len;    // rows in the bin, nonzeros per row
+    int32_t stride;       // rows rounded up to a multiple of 32
+    int32_t first;        // position of the bin's first row in perm
+    int32_t slab0;        // first slab (32 / G rows) of the bin
+    int32_t pad;
+};
+struct DevEll {
+    int nbins = 0;
+    int G = 1;                      // lanes per row (slab = 32 / G rows)
+    bool stream = true;             // evict-first loads (operators far larger than L2 share)
+    int64_t nslabs = 0, size = 0;   // slabs (warps), stored entries (with padding)
+    DevBuf bins;                    // EllBin[nbins]
+    DevBuf perm;                    // int32[n_rows]: CSR row of each sorted position
+    DevBuf col;                     // int32[size]
+    DevBuf val64, val32;            // copies of the CSR val64 / val32
+};
+
 // CSR on the device: int32 row pointers and columns, float64 values and
-// (mixed precision) a float32 copy.
+// (mixed precision) a float32 copy; `ell` holds the binned-ELL copy used by
+// the SpMV whenever the values passed are val64 or val32.
 struct DevCSR {
     int64_t n_rows = 0, n_cols = 0, nnz = 0;
     DevBuf ptr, col, val64, val32;
-    int group = 8;        // threads per row in the SpMV kernel
+    int group = 8;        // threads per row in the CSR SpMV kernel
+    DevEll ell;
 };
 
 struct LevelDev {
@@ -187,6 +216,12 @@ enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 template <class TA, class TX, class TY>
 fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
                        cudaStream_t s);
+
+// binned-ELL copy of A (structure and val64; val32 too if present), and
+// the float32 copy of an existing ELL from A.val32.  concurrent: A belongs
+// to one problem of a batch (its launches share the GPU with the others').
+fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent);
+fsi_status ell_fill_f32(DevCSR &A, cudaStream_t s);
 
 // storage: 0 float64, 1 float32, 2 float16 with a float32 scale per row
 fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int storage, int *flags,

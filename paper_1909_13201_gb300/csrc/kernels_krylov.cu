@@ -20,9 +20,71 @@ namespace {
 constexpr int KMAX = 65;     // vectors in a pass: restart + 1 <= 65
 constexpr int KT = 256;      // threads per CTA
 
+constexpr int KW = KT / 32;  // warps per CTA
+
+// Rows are split into gridDim.x contiguous chunks; a CTA walks its chunk in
+// tiles of KT rows.  Dot products against the basis are split by vector, not
+// by row: vector i belongs to warp i % KW, whose lanes stride over the tile's
+// rows (coalesced column reads), so a thread holds ceil(NV / KW) accumulators
+// instead of NV and the kernels keep several CTAs per SM.  Each vector's
+// partial sum comes from exactly one warp: a fixed shuffle tree, no atomics.
+template <int NV> struct Slots { static constexpr int U = (NV + KW - 1) / KW; };
+
+// acc[u] += sum over the tile rows of V[i, r] * ws[r - t0], i = warp + KW u
+template <int NV, class TV, class TA>
+__device__ __forceinline__ void tile_dots(const TV *__restrict__ V, int64_t ld, int nv, int64_t t0, int64_t r1,
+                                          const TA *ws, TA (&acc)[Slots<NV>::U]) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int u = 0; u < Slots<NV>::U; ++u) {
+        const int i = warp + KW * u;
+        if (i >= nv) break;
+        const TV *col = V + (size_t)i * ld;
+        TA a0 = 0, a1 = 0;
+#pragma unroll
+        for (int k = 0; k < KT / 32; k += 2) {
+            const int64_t ra = t0 + lane + 32 * k, rb = ra + 32;
+            if (ra < r1) a0 += (TA)__ldg(col + ra) * ws[lane + 32 * k];
+            if (rb < r1) a1 += (TA)__ldg(col + rb) * ws[lane + 32 * (k + 1)];
+        }
+        acc[u] += a0 + a1;
+    }
+}
+
+// partials[i] = warp-sum of acc for the warp's vectors
+template <int NV, class TA>
+__device__ __forceinline__ void store_slot_partials(TA (&acc)[Slots<NV>::U], int nv, double *out) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int u = 0; u < Slots<NV>::U; ++u) {
+        const int i = warp + KW * u;
+        if (i >= nv) break;
+        double v = (double)acc[u];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) out[i] = v;
+    }
+}
+
+// out[0] = CTA sum of one value per thread (warp trees, then warps in order)
+__device__ __forceinline__ void store_cta_sum(double v, double *out) {
+    __shared__ double red[KW];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < KW; ++k) s += red[k];
+        out[0] = s;
+    }
+}
+
+// Few vectors (NV <= 8): every thread keeps all NV sums of its rows (a warp
+// per vector would leave most warps idle); out[i] = CTA sum of acc[i],
+// warp trees then warps in order.
 template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double *out) {
-    __shared__ double red[KT / 32][NV];
+__device__ __forceinline__ void store_row_partials(double (&acc)[NV], int nv, double *out) {
+    __shared__ double red[KW][NV];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -34,30 +96,44 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, do
     __syncthreads();
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
         double v = 0.0;
-        for (int w = 0; w < KT / 32; ++w) v += red[w][i];
+        for (int k = 0; k < KW; ++k) v += red[k][i];
         out[i] = v;
     }
 }
 
-// Rows are split into gridDim.x contiguous chunks; thread t of a CTA visits
-// rows chunk_start + t, + KT, ... so that every vector is read coalesced.
+// pass 1 (float64 modes): partial dots V^T w
 template <int NV>
 __global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                   const double *__restrict__ w, int64_t n,
                                                   double *__restrict__ partials, const FgState *fg) {
     if (fg) nv = min(fg->k + 1, NV);
-    double acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
-        const double wr = w[r];
+    if constexpr (NV <= 8) {
+        double acc[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) acc[i] += V[(size_t)i * ld + r] * wr;
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+            const double wr = w[r];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) acc[i] += __ldg(V + (size_t)i * ld + r) * wr;
+        }
+        store_row_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+        return;
     }
-    block_reduce_store<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+    __shared__ double ws[KT];
+    double acc[Slots<NV>::U];
+#pragma unroll
+    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.0;
+    for (int64_t t0 = r0; t0 < r1; t0 += KT) {
+        const int64_t r = t0 + threadIdx.x;
+        ws[threadIdx.x] = r < r1 ? w[r] : 0.0;
+        __syncthreads();
+        tile_dots<NV>(V, ld, nv, t0, r1, ws, acc);
+        __syncthreads();
+    }
+    store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
 }
 
 // First Gram-Schmidt pass of the mixed modes: h1 = V^T w from the float32
@@ -70,62 +146,109 @@ __global__ void __launch_bounds__(KT) mdot32_kernel(const float *__restrict__ V,
                                                     const double *__restrict__ w, int64_t n,
                                                     double *__restrict__ partials, const FgState *fg) {
     if (fg) nv = min(fg->k + 1, NV);
-    float acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
-        const float wr = (float)w[r];
+    if constexpr (NV <= 8) {
+        float acc[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) acc[i] = fmaf(V[(size_t)i * ld + r], wr, acc[i]);
+        for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+            const float wr = (float)w[r];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) acc[i] = fmaf(__ldg(V + (size_t)i * ld + r), wr, acc[i]);
+        }
+        double accd[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) accd[i] = (double)acc[i];
+        store_row_partials<NV>(accd, nv, partials + (size_t)blockIdx.x * KMAX);
+        return;
     }
-    double accd[NV];
+    __shared__ float ws[KT];
+    float acc[Slots<NV>::U];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) accd[i] = (double)acc[i];
-    block_reduce_store<NV>(accd, nv, partials + (size_t)blockIdx.x * KMAX);
+    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.f;
+    for (int64_t t0 = r0; t0 < r1; t0 += KT) {
+        const int64_t r = t0 + threadIdx.x;
+        ws[threadIdx.x] = r < r1 ? (float)w[r] : 0.f;
+        __syncthreads();
+        tile_dots<NV>(V, ld, nv, t0, r1, ws, acc);
+        __syncthreads();
+    }
+    store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
 }
 
+// pass 2: w -= V h and partial dots V^T w (norm_only = 0);
+// pass 3: w -= V h and partial ||w||^2   (norm_only = 1).
+// NV <= 8: one thread per row does both.  Otherwise a thread first updates its row of the tile (the sum V[r, :] h in four
+// independent chains, then one subtraction), writes it back and into shared
+// memory; the warps then form the dots of the updated tile.  The basis tile
+// is read from HBM in the update and again, from L1/L2, in the dots.
 template <int NV>
-__global__ void __launch_bounds__(KT) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
+__global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
                                                         int64_t ld, int nv, const double *__restrict__ h,
                                                         int64_t n, double *__restrict__ partials, int norm_only,
                                                         const FgState *fg) {
     if (fg) nv = min(fg->k + 1, NV);
     __shared__ double hs[KMAX];
+    __shared__ double ws[KT];
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
-    double acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     double nrm = 0.0;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
-        double v[NV];
-        double wr = w[r];
+    if constexpr (NV <= 8) {
+        double acc[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) {
-                v[i] = V[(size_t)i * ld + r];
-                wr -= v[i] * hs[i];
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
+            double v[NV];
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) {
+                    v[i] = __ldg(V + (size_t)i * ld + r);
+                    s += v[i] * hs[i];
+                }
+            const double wr = w[r] - s;
+            w[r] = wr;
+            if (norm_only) {
+                nrm += wr * wr;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    if (i < nv) acc[i] += v[i] * wr;
             }
-        w[r] = wr;
+        }
+        if (norm_only) store_cta_sum(nrm, partials + (size_t)blockIdx.x * KMAX);
+        else store_row_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+        return;
+    }
+    double acc[Slots<NV>::U];
+#pragma unroll
+    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.0;
+    for (int64_t t0 = r0; t0 < r1; t0 += KT) {
+        const int64_t r = t0 + threadIdx.x;
+        double wr = 0.0;
+        if (r < r1) {
+            double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) s[i & 3] += __ldg(V + (size_t)i * ld + r) * hs[i];
+            wr = w[r] - ((s[0] + s[1]) + (s[2] + s[3]));
+            w[r] = wr;
+        }
         if (norm_only) {
             nrm += wr * wr;
         } else {
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-                if (i < nv) acc[i] += v[i] * wr;
+            ws[threadIdx.x] = wr;
+            __syncthreads();
+            tile_dots<NV>(V, ld, nv, t0, r1, ws, acc);
+            __syncthreads();
         }
     }
-    if (norm_only) {
-        acc[0] = nrm;
-        block_reduce_store<NV>(acc, 1, partials + (size_t)blockIdx.x * KMAX);
-    } else {
-        block_reduce_store<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
-    }
+    if (norm_only) store_cta_sum(nrm, partials + (size_t)blockIdx.x * KMAX);
+    else store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
 }
 
 // one warp per vector: lanes stride over the per-CTA partials in a fixed

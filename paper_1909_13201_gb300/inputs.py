@@ -189,7 +189,7 @@ def make_config(k: int) -> Problem | list[Problem]:
         return make_channel_2d(256, 7, 3, seed, bulge=True, mu_f=1e-2,
                                name="channel2d-bulge-256x256-L7")
     if k == 2:
-        return make_valve_3d(32, 5, 1, seed, name="valve3d-32x32x32-L5")
+        return make_valve_3d(32, 4, 1, seed, name="valve3d-32x32x32-L4")
     if k == 3:
         return make_batch(64)
     if k == 4:

@@ -76,11 +76,16 @@ def test_operator_values_all_levels(case):
 
 
 def test_spmv(case):
+    """y = A_l x on every level (binned-ELL copy of the operator: bins of
+    every row length, each a ragged number of 32-row slabs)."""
     name, p, H, s = case
-    x = np.random.default_rng(1).standard_normal(H.fine.shape[0])
-    y = s.apply_operator(len(H.A) - 1, _cuda(x)).cpu().numpy()
-    ref = H.fine @ x
-    assert np.abs(y - ref).max() <= 1e-13 * np.abs(H.fine).max() * np.abs(x).max() * 50
+    rng = np.random.default_rng(1)
+    for l, A in enumerate(H.A):
+        x = rng.standard_normal(A.shape[0])
+        y = s.apply_operator(l, _cuda(x)).cpu().numpy()
+        ref = A @ x
+        bound = 1e-15 * 60 * (abs(A) @ np.abs(x))   # float64 sum of <= ~110 terms per row
+        assert np.all(np.abs(y - ref) <= bound + 1e-300), (name, l)
 
 
 @pytest.mark.parametrize("transpose", [False, True])
@@ -407,7 +412,11 @@ def test_float32_blocked_inversion(name):
 
 def test_batch_larger_than_hardware_queues():
     """Ten systems (more than the 8 default hardware work queues) advance in
-    host-driven rounds; each result matches its own single solve."""
+    host-driven rounds; each result matches the direct solution, and each
+    iteration count its own single solve.  Counts are compared at rtol 1e-8:
+    1e-10 lies at the attainable accuracy of these systems (the sparse LU
+    itself leaves ~5e-11), where the count of the float32 cycle, whose
+    overlapping scatter-add uses atomics, moves with rounding."""
     probs = [I.make_channel_2d(16 + 8 * (i % 3), 3, 1, 600 + i, band_width=0.15 + 0.02 * i,
                                mu_s=100.0 + 40.0 * i) for i in range(10)]
     sb = binding.FSISolver(probs)
@@ -420,9 +429,11 @@ def test_batch_larger_than_hardware_queues():
         refs.append(_direct(H.fine, b))
         s1 = binding.FSISolver(p)
         s1.setup_smoothers(precision=binding.FSI_MIXED_HALF)
-        singles.append(s1.solve(_cuda(b), rtol=1e-10)[1]["iterations"])
+        singles.append(s1.solve(_cuda(b), rtol=1e-8)[1]["iterations"])
     xs, sts = sb.solve_batched(bs, rtol=1e-10)
-    for x, ref, st, it1 in zip(xs, refs, sts, singles):
+    for x, ref, st in zip(xs, refs, sts):
         assert st["converged"]
         assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
-        assert abs(st["iterations"] - it1) <= 1
+    _, sts8 = sb.solve_batched(bs, rtol=1e-8)
+    for st, it1 in zip(sts8, singles):
+        assert st["converged"] and abs(st["iterations"] - it1) <= 1, (st["iterations"], it1)
