@@ -169,8 +169,8 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# GB300 float64 rate (nominal, no measured figure exists on this machine): the
-# outer product and the Gram-Schmidt passes are bound by it, not by HBM
+# GB300 float64 rate (nominal; the bench also measures it, fsi_profile mode
+# 3): the outer product and the Gram-Schmidt passes are bound by it, not by HBM
 FP64_NOMINAL_GFLOPS = 1250.0
 
 
@@ -300,6 +300,9 @@ def run_ours(args, rank, world, local):
     outer_ms = prof["outer_ms"] / max(prof["outer_launches"], 1)
     outer_gbs = prof["outer_bytes"] / (outer_ms * 1e-3) / 1e9
     outer_gflops = 2.0 * prof["outer_fma"] / (outer_ms * 1e-3) / 1e9
+    gs64_gflops = 2.0 * prof["gs64_fma"] / (prof["gs64_ms"] * 1e-3) / 1e9 if prof["gs64_ms"] > 0 else None
+    gs1_gbs = prof["gs1_bytes"] / (prof["gs1_ms"] * 1e-3) / 1e9 if prof["gs1_ms"] > 0 else None
+    fp64_peak = s.profile(3)["fp64_gflops"]          # measured float64 FMA rate of this GPU
     peak, peak_kind = measured_peaks()
     # ---- end to end through the public call with host buffers (mixed)
     b_pin = torch.from_numpy(b_host).pin_memory()
@@ -484,10 +487,21 @@ def run_ours(args, rank, world, local):
                      "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms},
                      "restriction_fine": {"achieved": rst_gbs, "frac": rst_gbs / peak, "mean_launch_ms": rst_ms},
                      "prolongation_fine": {"achieved": pro_gbs, "frac": pro_gbs / peak, "mean_launch_ms": pro_ms},
+                     "fp64_peak_gflops": {"measured": fp64_peak, "nominal": FP64_NOMINAL_GFLOPS,
+                                          "how": "fsi_profile mode 3: 8 independent FMA chains per thread, "
+                                                 "8 CTAs x 256 threads per SM, best of 3 timed launches"},
                      "outer_spmv_f64": {"achieved_gbs": outer_gbs, "frac_hbm": outer_gbs / peak,
                                         "achieved_fp64_gflops": outer_gflops,
+                                        "frac_fp64_measured": outer_gflops / fp64_peak if fp64_peak else None,
                                         "frac_fp64_nominal": outer_gflops / FP64_NOMINAL_GFLOPS,
-                                        "mean_launch_ms": outer_ms}},
+                                        "mean_launch_ms": outer_ms},
+                     "gram_schmidt_f64": {"bound": "fp64", "achieved_gflops": gs64_gflops,
+                                          "frac_fp64_measured": (gs64_gflops / fp64_peak
+                                                                 if gs64_gflops and fp64_peak else None),
+                                          "launches_timed": prof["gs64_launches"]},
+                     "gram_schmidt_first_pass_f32": {"bound": "hbm", "achieved_gbs": gs1_gbs,
+                                                     "frac": gs1_gbs / peak if gs1_gbs else None,
+                                                     "launches_timed": prof["gs1_launches"]}},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,

@@ -231,8 +231,9 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
 /* Kernel profiling (no counterpart in the paper; measurement support).
  * mode 1: reset the counters and start recording CUDA events around the
  * fine-level smoother apply and fine-level residual SpMV launches of the
- * following solves; mode 0: stop recording; mode 2: read only.
- * out (host, 24 doubles): [0] smoother launches timed, [1] their total ms,
+ * following solves; mode 0: stop recording; mode 2: read only; mode 3: read,
+ * and measure the device's float64 FMA throughput into out[21].
+ * out (host, 32 doubles): [0] smoother launches timed, [1] their total ms,
  * [2] algorithmic bytes per smoother launch (block inverses, index, weight,
  * gather and scatter traffic), [3] SpMV launches timed, [4] their total ms,
  * [5] algorithmic bytes per SpMV launch, [6] kernels launched by the library
@@ -243,7 +244,13 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * one fine-level inversion (2 n_j^3 summed over blocks), [14] fine blocks,
  * [15] fine-level restrictions timed, [16] their ms, [17] algorithmic bytes
  * per restriction, [18] fine-level prolongations timed, [19] their ms,
- * [20] algorithmic bytes per prolongation, [21..23] reserved.  Problem 0. */
+ * [20] algorithmic bytes per prolongation, [21] float64 GFLOP/s measured
+ * by mode 3 (independent FMA chains on every SM; 0 otherwise), [22] float64
+ * Gram-Schmidt passes timed (update and dots, update and norm), [23] their
+ * ms, [24] their float64 FMAs in total, [25] first Gram-Schmidt passes timed,
+ * [26] their ms, [27] their bytes in total, [28..31] reserved.  The
+ * Gram-Schmidt passes are timed in host-driven solves only (solves run
+ * host-driven while recording).  Problem 0. */
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
 
 /* Host-only inspection context: builds the levels, numbering, operator

@@ -251,9 +251,9 @@ class FSISolver:
         return list(chosen), times.reshape(n, len(candidates))
 
     def profile(self, mode):
-        """mode 1 start (reset), 0 stop, 2 read.  Returns the counters of
-        fsi_profile as a dict."""
-        out = np.zeros(24, np.float64)
+        """mode 1 start (reset), 0 stop, 2 read, 3 read and measure the
+        float64 FMA rate.  Returns the counters of fsi_profile as a dict."""
+        out = np.zeros(32, np.float64)
         _check(load_library().fsi_profile(self.ctx, mode, _ptr(out, C.c_double)))
         return {"smoother_launches": int(out[0]), "smoother_ms": out[1], "smoother_bytes": out[2],
                 "spmv_launches": int(out[3]), "spmv_ms": out[4], "spmv_bytes": out[5],
@@ -261,7 +261,9 @@ class FSISolver:
                 "outer_bytes": out[9], "outer_fma": out[10], "invert_launches": int(out[11]),
                 "invert_ms": out[12], "invert_flops": out[13], "fine_blocks": int(out[14]),
                 "restrict_launches": int(out[15]), "restrict_ms": out[16], "restrict_bytes": out[17],
-                "prolong_launches": int(out[18]), "prolong_ms": out[19], "prolong_bytes": out[20]}
+                "prolong_launches": int(out[18]), "prolong_ms": out[19], "prolong_bytes": out[20],
+                "fp64_gflops": out[21], "gs64_launches": int(out[22]), "gs64_ms": out[23], "gs64_fma": out[24],
+                "gs1_launches": int(out[25]), "gs1_ms": out[26], "gs1_bytes": out[27]}
 
     # ------------------------------------------------------------ accessors
     @property

@@ -27,6 +27,7 @@ int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 namespace {
 
 constexpr int NRED = 304;           // CTAs of the Krylov reductions (2 per SM)
+constexpr int NDOT = 608;           // CTAs of the streaming first Gram-Schmidt pass (4 per SM)
 
 // lanes per row of the SpMV kernel from the mean row length
 int pick_group(int64_t rows, int64_t nnz) {
@@ -251,7 +252,7 @@ fsi_status ensure_workspace(Context &cx, Problem &pb, int m) {
     FSI_TRY(pb.y.alloc((size_t)(m + 1) * 8));
     FSI_TRY(pb.w.alloc((size_t)n * 8));
     FSI_TRY(pb.rvec.alloc((size_t)n * 8));
-    FSI_TRY(pb.partials.alloc((size_t)NRED * 65 * 8));
+    FSI_TRY(pb.partials.alloc((size_t)NDOT * 65 * 8));
     FSI_TRY(pb.scal.alloc(64 * 8));
     FSI_TRY(pb.h1.alloc((size_t)(m + 1) * 8));
     FSI_TRY(pb.h2.alloc((size_t)(m + 1) * 8));
@@ -323,12 +324,24 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
     const int nv = j + 1;
     double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
     float *V32 = cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr;
-    if (V32) FSI_TRY(launch_mdot32(V32, n, nv, w, n, part, NRED, s));
-    else FSI_TRY(launch_mdot(V, n, nv, w, n, part, NRED, s));
-    FSI_TRY(launch_reduce_partials(part, NRED, nv, h1, 0, s));
-    FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s));
+    {
+        ProfMark pm(cx, 7, true);       // first pass: bytes of the basis (copy) and w
+        if (cx.profile) cx.prof_work[7] += (double)nv * n * (V32 ? 4.0 : 8.0) + (double)n * 8.0;
+        if (V32) FSI_TRY(launch_mdot32(V32, n, nv, w, n, part, NDOT, s));
+        else FSI_TRY(launch_mdot(V, n, nv, w, n, part, NDOT, s));
+    }
+    FSI_TRY(launch_reduce_partials(part, NDOT, nv, h1, 0, s));
+    {
+        ProfMark pm(cx, 6, true);       // float64 update + dots: 2 nv FMAs per row
+        if (cx.profile) cx.prof_work[6] += 2.0 * nv * n;
+        FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s));
+    }
     FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
-    FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
+    {
+        ProfMark pm(cx, 6, true);       // float64 update + norm: nv + 1 FMAs per row
+        if (cx.profile) cx.prof_work[6] += (nv + 1.0) * n;
+        FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
+    }
     FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
     FSI_TRY(launch_givens(H, m + 1, j, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s));
     FSI_CUDA(cudaMemcpyAsync(pb.h_scal, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
@@ -761,7 +774,10 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                                     mixed ? nullptr : D.jac_inv.as<double>(),
                                     mixed ? D.jac_inv.as<float>() : nullptr, s));
         // apply work items: whole blocks when there are enough of them to fill
-        // the GPU, otherwise row chunks (multiples of 16 rows)
+        // the GPU, otherwise row chunks (multiples of 16 rows).  Splitting
+        // blocks further (>= 64 items per SM) was measured slower on every
+        // level it touched (128^2: 43 -> 52 us; 64^2: 17 -> 32 us): each chunk
+        // gathers its block's residual again.
         {
             const int64_t want = 4 * (int64_t)cx.num_sms;
             const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
@@ -873,9 +889,7 @@ template <class T>
 fsi_status apply_vcycle_t(Context &cx, Problem &pb, const double *v, double *z, int tr) {
     cudaStream_t s = cx.stream;
     LevelDev &F = pb.dev.back();
-    DevBuf bt, xt;
-    FSI_TRY(bt.alloc((size_t)F.n * sizeof(T)));
-    FSI_TRY(xt.alloc((size_t)F.n * sizeof(T)));
+    DevBuf &bt = F.b, &xt = F.x;     // the fine cycle vectors, as inside a solve
     if (std::is_same<T, float>::value) FSI_TRY(launch_cast_f64_f32(v, bt.as<float>(), F.n, s));
     else FSI_CUDA(cudaMemcpyAsync(bt.p, v, (size_t)F.n * 8, cudaMemcpyDeviceToDevice, s));
     FSI_TRY(vcycle<T>(cx, pb, (int)pb.dev.size() - 1, bt.as<T>(), xt.as<T>(), tr != 0));
@@ -1039,9 +1053,9 @@ fsi_status issue_step_dev_tail(Context &cx, Problem &pb, int m, int nv_bound, cu
     double *w = pb.w.as<double>(), *scal = pb.scal.as<double>();
     double *part = pb.partials.as<double>(), *h1 = pb.h1.as<double>(), *h2 = pb.h2.as<double>();
     float *V32 = cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr;
-    if (V32) FSI_TRY(launch_mdot32(V32, n, nv_bound, w, n, part, NRED, s, fg));
-    else FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NRED, s, fg));
-    FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h1, 0, s, fg));
+    if (V32) FSI_TRY(launch_mdot32(V32, n, nv_bound, w, n, part, NDOT, s, fg));
+    else FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NDOT, s, fg));
+    FSI_TRY(launch_reduce_partials(part, NDOT, nv_bound, h1, 0, s, fg));
     FSI_TRY(launch_update_dot(w, V, n, nv_bound, h1, n, part, NRED, 0, s, fg));
     FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h2, 0, s, fg));
     FSI_TRY(launch_update_dot(w, V, n, nv_bound, h2, n, part, NRED, 1, s, fg));
@@ -1395,12 +1409,18 @@ fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *l
 
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     Context *cx = reinterpret_cast<Context *>(ctx);
-    if (!cx || !out || mode < 0 || mode > 2) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!cx || !out || mode < 0 || mode > 3) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    double fp64_gflops = 0.0;
+    if (mode == 3) {
+        DeviceGuard guard(cx->device);
+        FSI_TRY(measure_fp64_rate(cx->num_sms, cx->stream, &fp64_gflops));
+    }
     if (mode == 1) {
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 8; ++k) {
             cx->prof_ms[k] = 0;
             cx->prof_n[k] = 0;
+            cx->prof_work[k] = 0;
         }
         cx->launch_base = launches_so_far();
         cx->profile = true;
@@ -1448,7 +1468,14 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     out[18] = (double)cx->prof_n[5];
     out[19] = cx->prof_ms[5];
     out[20] = (double)F.P.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)Cl.n * ts + 2.0 * (double)F.n * ts;
-    out[21] = out[22] = out[23] = 0.0;
+    out[21] = fp64_gflops;
+    out[22] = (double)cx->prof_n[6];
+    out[23] = cx->prof_ms[6];
+    out[24] = cx->prof_work[6];
+    out[25] = (double)cx->prof_n[7];
+    out[26] = cx->prof_ms[7];
+    out[27] = cx->prof_work[7];
+    for (int k = 28; k < 32; ++k) out[k] = 0.0;
     return FSI_OK;
 }
 

@@ -64,14 +64,14 @@ struct DevBuf {
 // products stream.  Rows are sorted by their number of nonzeros (stable, so
 // rows of one length keep their order) and grouped into bins of equal
 // length; bin b stores its rows column-major, entry k of sorted row t at
-// off + k * stride + t with stride = rows rounded up to 32, so a warp of 32
-// consecutive rows reads every entry position as one coalesced 128-byte
-// line and needs no row pointers.  Padding entries hold column 0, value 0.
-// A warp takes one slab of 32 / G rows, G lanes per row.
+// off + k * stride + t with stride = rows rounded up to a slab of 32 / G
+// rows (G lanes per row), so with G = 1 a warp of 32 consecutive rows reads
+// every entry position as one coalesced 128-byte line and needs no row
+// pointers.  Padding entries hold column 0, value 0.
 struct EllBin {
     int64_t off;          // first stored entry of the bin
     int32_t rows, len;    // rows in the bin, nonzeros per row
-    int32_t stride;       // rows rounded up to a multiple of 32
+    int32_t stride;       // rows rounded up to a multiple of 32 / G
     int32_t first;        // position of the bin's first row in perm
     int32_t slab0;        // first slab (32 / G rows) of the bin
     int32_t pad;
@@ -192,9 +192,11 @@ struct Context {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;   // kind, start/stop
     // fine smoother, fine residual SpMV, outer float64 A z, fine block
-    // inversion (set-up), fine restriction, fine prolongation
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-    int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
+    // inversion (set-up), fine restriction, fine prolongation, float64
+    // Gram-Schmidt passes (work: FMAs), first Gram-Schmidt pass (work: bytes)
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t launch_base = 0;
     // solves run on a context-owned non-blocking stream
     cudaStream_t work = nullptr;
@@ -238,6 +240,7 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
                                   cudaStream_t s);
 
 fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s);
+
 template <class T>
 fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int transpose,
                              cudaStream_t s);
@@ -259,6 +262,8 @@ fsi_status launch_givens(double *H, int ld, int j, const double *h1, const doubl
 // v = w / scal[idx] (and its float32 copy v32 when non-null)
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
                              cudaStream_t s, const FgState *fg = nullptr, int64_t ld = 0, float *v32 = nullptr);
+// float64 FMA throughput of the device (GFLOP/s, 2 flops per FMA)
+fsi_status measure_fp64_rate(int num_sms, cudaStream_t s, double *gflops);
 // first Gram-Schmidt pass from the float32 copy of the basis (mixed modes)
 fsi_status launch_mdot32(const float *V, int64_t ld, int nv, const double *w, int64_t n, double *partials,
                          int nblocks, cudaStream_t s, const FgState *fg = nullptr);

@@ -11,6 +11,8 @@
 // Each pass writes one partial sum per CTA and vector; a one-CTA kernel adds
 // them in a fixed order (deterministic).  The Givens update of the Hessenberg
 // column and the residual estimate run in one thread on the device.
+#include <algorithm>
+
 #include "context.h"
 
 namespace fsi {
@@ -101,39 +103,85 @@ __device__ __forceinline__ void store_row_partials(double (&acc)[NV], int nv, do
     }
 }
 
+// Pass 1: partial dots V^T w, streamed without barriers.  TV is the basis
+// type (float64, or the float32 copy in the mixed modes, where w is rounded
+// to float32 and products and sums are float32), TA the accumulator.
+// NV <= 8: a thread keeps all NV sums of its rows and loads 4 rows per pass;
+// otherwise vector i belongs to warp i % KW, whose lanes take the rows of the
+// CTA's chunk 8 x 32 (float64 basis: 4 x 32) at a time (w is re-read from L1
+// by every warp).  Either way a lane has 4 (NV + 1) or 8 (Slots + 1)
+// independent loads in flight:
+// each pass of the loop costs one memory latency, so the bytes a pass keeps
+// in flight (and the CTAs per SM) set the bandwidth.
+template <int NV, class TV, class TA>
+__device__ __forceinline__ void stream_dots(const TV *__restrict__ V, int64_t ld, int nv,
+                                            const double *__restrict__ w, int64_t r0, int64_t r1,
+                                            double *__restrict__ out) {
+    if constexpr (NV <= 8) {
+        TA acc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = 0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += 4 * KT) {
+            TA wr[4];
+            TV v[4][NV];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t rq = r + (int64_t)q * KT;
+                wr[q] = rq < r1 ? (TA)__ldg(w + rq) : TA(0);
+#pragma unroll
+                for (int i = 0; i < NV; ++i) v[q][i] = (i < nv && rq < r1) ? __ldg(V + (size_t)i * ld + rq) : TV(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int i = 0; i < NV; ++i) acc[i] += (TA)v[q][i] * wr[q];
+        }
+        double accd[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) accd[i] = (double)acc[i];
+        store_row_partials<NV>(accd, nv, out);
+    } else {
+        constexpr int U = Slots<NV>::U;
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+        TA acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = 0;
+        constexpr int RB = sizeof(TV) == 4 ? 8 : 4;  // row batches of 32 per pass
+        for (int64_t r = r0 + lane; r < r1; r += 32 * RB) {
+            TA wr[RB];
+            TV v[U][RB];
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                const int64_t rq = r + 32 * q;
+                wr[q] = rq < r1 ? (TA)__ldg(w + rq) : TA(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = warp + KW * u;
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    const int64_t rq = r + 32 * q;
+                    v[u][q] = (i < nv && rq < r1) ? __ldg(V + (size_t)i * ld + rq) : TV(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int q = 0; q < RB; ++q) acc[u] += (TA)v[u][q] * wr[q];
+        }
+        store_slot_partials<NV>(acc, nv, out);
+    }
+}
+
 // pass 1 (float64 modes): partial dots V^T w
 template <int NV>
-__global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
+__global__ void __launch_bounds__(KT, 2) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                   const double *__restrict__ w, int64_t n,
                                                   double *__restrict__ partials, const FgState *fg) {
     if (fg) nv = min(fg->k + 1, NV);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    if constexpr (NV <= 8) {
-        double acc[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
-            const double wr = w[r];
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-                if (i < nv) acc[i] += __ldg(V + (size_t)i * ld + r) * wr;
-        }
-        store_row_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
-        return;
-    }
-    __shared__ double ws[KT];
-    double acc[Slots<NV>::U];
-#pragma unroll
-    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.0;
-    for (int64_t t0 = r0; t0 < r1; t0 += KT) {
-        const int64_t r = t0 + threadIdx.x;
-        ws[threadIdx.x] = r < r1 ? w[r] : 0.0;
-        __syncthreads();
-        tile_dots<NV>(V, ld, nv, t0, r1, ws, acc);
-        __syncthreads();
-    }
-    store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+    stream_dots<NV, double, double>(V, ld, nv, w, r0, r1, partials + (size_t)blockIdx.x * KMAX);
 }
 
 // First Gram-Schmidt pass of the mixed modes: h1 = V^T w from the float32
@@ -142,40 +190,13 @@ __global__ void __launch_bounds__(KT) mdot_kernel(const double *__restrict__ V, 
 // and the new basis vector keep float64 accuracy; the float32 pipe and the
 // halved basis bytes replace the float64 multiply-adds of a full pass.
 template <int NV>
-__global__ void __launch_bounds__(KT) mdot32_kernel(const float *__restrict__ V, int64_t ld, int nv,
+__global__ void __launch_bounds__(KT, 4) mdot32_kernel(const float *__restrict__ V, int64_t ld, int nv,
                                                     const double *__restrict__ w, int64_t n,
                                                     double *__restrict__ partials, const FgState *fg) {
     if (fg) nv = min(fg->k + 1, NV);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    if constexpr (NV <= 8) {
-        float acc[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
-            const float wr = (float)w[r];
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-                if (i < nv) acc[i] = fmaf(__ldg(V + (size_t)i * ld + r), wr, acc[i]);
-        }
-        double accd[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) accd[i] = (double)acc[i];
-        store_row_partials<NV>(accd, nv, partials + (size_t)blockIdx.x * KMAX);
-        return;
-    }
-    __shared__ float ws[KT];
-    float acc[Slots<NV>::U];
-#pragma unroll
-    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.f;
-    for (int64_t t0 = r0; t0 < r1; t0 += KT) {
-        const int64_t r = t0 + threadIdx.x;
-        ws[threadIdx.x] = r < r1 ? (float)w[r] : 0.f;
-        __syncthreads();
-        tile_dots<NV>(V, ld, nv, t0, r1, ws, acc);
-        __syncthreads();
-    }
-    store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
+    stream_dots<NV, float, float>(V, ld, nv, w, r0, r1, partials + (size_t)blockIdx.x * KMAX);
 }
 
 // pass 2: w -= V h and partial dots V^T w (norm_only = 0);
@@ -445,7 +466,47 @@ inline int egrid(int64_t n) {
     return (int)g;
 }
 
+// Float64 FMA throughput of this GPU (measurement support for the roofline
+// of the float64-bound kernels): 8 independent FMA chains per thread, one
+// store per thread so that nothing is optimised away.
+__global__ void __launch_bounds__(256) fp64_rate_kernel(double *out, double a, double b, int iters) {
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (double)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = fma(acc[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += acc[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+fsi_status measure_fp64_rate(int num_sms, cudaStream_t s, double *gflops) {
+    const int blocks = num_sms * 8, threads = 256, iters = 2048;
+    DevBuf out;
+    FSI_TRY(out.alloc((size_t)blocks * threads * 8));
+    cudaEvent_t e0, e1;
+    FSI_CUDA(cudaEventCreate(&e0));
+    FSI_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        FSI_CUDA(cudaEventRecord(e0, s));
+        fp64_rate_kernel<<<blocks, threads, 0, s>>>(out.as<double>(), 0.999999, 1e-7, iters);
+        FSI_CUDA(cudaEventRecord(e1, s));
+        FSI_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FSI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);     // first launch warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *gflops = 2.0 * (double)blocks * threads * iters * 8 / (best * 1e-3) / 1e9;
+    return FSI_OK;
+}
 
 #define FSI_NV_SWITCH(nv, CALL)                          \
     do {                                                 \

@@ -275,7 +275,8 @@ fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent) {
         B.off = off;
         B.rows = (int32_t)(j - i);
         B.len = len;
-        B.stride = (int32_t)((B.rows + 31) / 32 * 32);
+        const int64_t rps = 32 / G;               // rows per slab
+        B.stride = (int32_t)((B.rows + rps - 1) / rps * rps);
         B.first = (int32_t)i;
         B.slab0 = (int32_t)slabs;
         for (int64_t t = i; t < j; ++t) {
