@@ -23,6 +23,20 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 static std::atomic<int64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+// programmatic launches only inside a V-cycle, where every launch follows
+// another kernel of the cycle (or the zeroing kernel at its top)
+static thread_local int g_pdl_depth = 0;
+struct PdlScope {
+    PdlScope() { ++g_pdl_depth; }
+    ~PdlScope() { --g_pdl_depth; }
+};
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("FSI_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on && g_pdl_depth > 0;
+}
 
 namespace {
 
@@ -180,7 +194,7 @@ fsi_status smooth_apply(Context &cx, LevelDev &L, const T *r, T *x, bool tr, boo
 
 // x_l = M_l^{-1} b_l from a zero guess (transposed cycle if tr)
 template <class T>
-fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
+fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr, bool x_zeroed = false) {
     cudaStream_t s = cx.stream;
     if (l == 0) return launch_dense_gemv<T>(pb.coarse_inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
     LevelDev &L = pb.dev[l];
@@ -191,7 +205,8 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
     const int npre = tr ? cx.nu_post : cx.nu_pre, npost = tr ? cx.nu_pre : cx.nu_post;
     const bool fine = l == (int)pb.dev.size() - 1;
     T *r = L.r.as<T>();
-    FSI_CUDA(cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), s));
+    if (!x_zeroed) FSI_TRY(launch_zero<T>(x, L.n, s));
+    PdlScope pdl;
     for (int k = 0; k < npre; ++k) {
         if (k == 0) {
             FSI_TRY(smooth_apply<T>(cx, L, b, x, tr, fine));
@@ -206,9 +221,11 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr) {
     }
     {
         ProfMark pm(cx, 4, fine);
-        FSI_TRY(launch_spmv<T, T, T>(Rm, mval<T>(Rm), r, (const T *)nullptr, C.b.as<T>(), SPMV_SET, s));
+        // b_{l-1} = R r, and x_{l-1} = 0 in the same launch (level 0 is written whole)
+        FSI_TRY(launch_spmv<T, T, T>(Rm, mval<T>(Rm), r, (const T *)nullptr, C.b.as<T>(), SPMV_SET, s,
+                                     l - 1 > 0 ? C.x.as<T>() : (T *)nullptr));
     }
-    FSI_TRY(vcycle<T>(cx, pb, l - 1, C.b.as<T>(), C.x.as<T>(), tr));
+    FSI_TRY(vcycle<T>(cx, pb, l - 1, C.b.as<T>(), C.x.as<T>(), tr, true));
     {
         ProfMark pm(cx, 5, fine);
         FSI_TRY(launch_spmv<T, T, T>(Pm, mval<T>(Pm), C.x.as<T>(), (const T *)nullptr, x, SPMV_ADD, s));

@@ -172,6 +172,33 @@ struct Problem {
 void count_launch(int n = 1);
 int64_t launches_so_far();
 
+// Programmatic dependent launch (V-cycle kernels).  A kernel launched with
+// launch_pdl may start while its predecessor on the stream is still
+// running: it calls pdl_trigger() on entry (so that its own successor can
+// be scheduled as soon as all of its CTAs run), does only work that reads
+// no data of earlier kernels (static matrices, block inverses, work items),
+// then pdl_wait(), which returns once every earlier kernel has completed
+// and its writes are visible.  Nothing is written before pdl_wait().  Both
+// are no-ops for a normal launch.  FSI_PDL=0 turns the attribute off.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+bool pdl_enabled();
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 struct Context {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -215,9 +242,14 @@ fsi_status launch_cast_f32_f64(const float *src, double *dst, int64_t n, cudaStr
 
 enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 // y = A x | y = b - A x | y += A x ; matrix precision follows TA, vectors TX/TY
+// zero_out (optional, length n_rows): set to 0 by the same launch (folds the
+// zeroing of the next level's correction into the restriction)
 template <class TA, class TX, class TY>
 fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
-                       cudaStream_t s);
+                       cudaStream_t s, TY *zero_out = nullptr);
+// v = 0 (normal launch; triggers its programmatic dependents at entry)
+template <class T>
+fsi_status launch_zero(T *v, int64_t n, cudaStream_t s);
 
 // binned-ELL copy of A (structure and val64; val32 too if present), and
 // the float32 copy of an existing ELL from A.val32.  concurrent: A belongs

@@ -206,8 +206,10 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_kernel(const int4 *
     using V = typename Vec<T>::type;
     constexpr int VW = Vec<T>::w;
     __shared__ __align__(16) T rs[MAX_BLOCK];
+    pdl_trigger();
     const int4 it = items[blockIdx.x];
     const int blk = it.x, r0 = it.y, r1 = it.z;
+    pdl_wait();
     if (blk < 0) {               // Jacobi rows [r0, r1) of the jac list (u^s and fixed dofs)
         for (int k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
             const int i = jac_idx[k];
@@ -260,8 +262,10 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_t_kernel(const int4
                                                                       T omega) {
     constexpr int VW = Vec<T>::w;
     __shared__ T rs[MAX_BLOCK];
+    pdl_trigger();
     const int4 it = items[blockIdx.x];
     const int blk = it.x, c0 = it.y, c1 = it.z;
+    pdl_wait();
     if (blk < 0) {               // Jacobi rows: diagonal, its own transpose
         for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
             const int i = jac_idx[k];
@@ -303,8 +307,10 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4
                                                                       const float *__restrict__ r, float *__restrict__ x,
                                                                       float omega) {
     __shared__ __align__(16) float rs[MAX_BLOCK];
+    pdl_trigger();
     const int4 it = items[blockIdx.x];
     const int blk = it.x, r0 = it.y, r1 = it.z;
+    pdl_wait();
     if (blk < 0) {
         for (int k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
             const int i = jac_idx[k];
@@ -363,9 +369,11 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_pipe_kernel(const
                                                                            const float *__restrict__ r,
                                                                            float *__restrict__ x, float omega) {
     __shared__ __align__(16) float rs[256];
+    pdl_trigger();
     const int4 it = items[blockIdx.x];
     const int blk = it.x, r0 = it.y, r1 = it.z;
     if (blk < 0) {
+        pdl_wait();
         for (int k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
             const int i = jac_idx[k];
             x[i] += omega * r[i] * jac_inv[k];
@@ -385,6 +393,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_pipe_kernel(const
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         m[q] = (col_ok && i + q < r1) ? __ldcs(M + (size_t)(i + q) * nv + lane) : make_uint4(0, 0, 0, 0);
+    pdl_wait();                                 // the inverse rows above are static; r is not
     for (int k = threadIdx.x; k < ld; k += blockDim.x) rs[k] = (k < n) ? r[blk_idx[s0 + k]] : 0.0f;
     __syncthreads();
     const float4 *rv = reinterpret_cast<const float4 *>(rs);
@@ -423,8 +432,10 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const in
                                                                         const float *__restrict__ r, float *__restrict__ x,
                                                                         float omega) {
     __shared__ float rs[MAX_BLOCK];
+    pdl_trigger();
     const int4 it = items[blockIdx.x];
     const int blk = it.x, c0 = it.y, c1 = it.z;
+    pdl_wait();
     if (blk < 0) {
         for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
             const int i = jac_idx[k];
@@ -739,6 +750,8 @@ __global__ void coarse_extract_kernel(const double *M, int64_t n, double *inv) {
 
 template <class T>
 __global__ void dense_gemv_kernel(const double *__restrict__ M, int64_t n, const T *__restrict__ x, T *__restrict__ y) {
+    pdl_trigger();
+    pdl_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
     const int nwarps = gridDim.x * blockDim.x / 32;
     for (int64_t i = warp; i < n; i += nwarps) {
@@ -750,6 +763,8 @@ __global__ void dense_gemv_kernel(const double *__restrict__ M, int64_t n, const
 }
 template <class T>
 __global__ void dense_gemv_t_kernel(const double *__restrict__ M, int64_t n, const T *__restrict__ x, T *__restrict__ y) {
+    pdl_trigger();
+    pdl_wait();
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int64_t i = 0; i < n; ++i) acc += M[i * n + j] * (double)x[i];
@@ -871,32 +886,32 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
         if (transpose)
-            block_apply_h_t_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+            FSI_CUDA(launch_pdl(block_apply_h_t_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega);
+                lev.jac_inv.as<float>(), rf, xf, (float)omega));
         else if (lev.max_block <= 256)
-            block_apply_h_pipe_kernel<<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+            FSI_CUDA(launch_pdl(block_apply_h_pipe_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega);
+                lev.jac_inv.as<float>(), rf, xf, (float)omega));
         else
-            block_apply_h_kernel<4><<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+            FSI_CUDA(launch_pdl(block_apply_h_kernel<4>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega);
+                lev.jac_inv.as<float>(), rf, xf, (float)omega));
         count_launch();
         FSI_CUDA(cudaGetLastError());
         return FSI_OK;
     }
     if (transpose)
-        block_apply_t_kernel<T><<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+        FSI_CUDA(launch_pdl(block_apply_t_kernel<T>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
             lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
-            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega);
+            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
     else
-        block_apply_kernel<T><<<(unsigned)lev.n_items, APPLY_THREADS, 0, s>>>(
+        FSI_CUDA(launch_pdl(block_apply_kernel<T>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
             lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
-            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega);
+            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -939,12 +954,12 @@ fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, 
 template <class T>
 fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int transpose, cudaStream_t s) {
     if (transpose) {
-        dense_gemv_t_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(M, n, x, y);
+        FSI_CUDA(launch_pdl(dense_gemv_t_kernel<T>, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, s, M, n, x, y));
         count_launch();
     } else {
         int64_t blocks = (n * 32 + 255) / 256;
         if (blocks > 1024) blocks = 1024;
-        dense_gemv_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(M, n, x, y);
+        FSI_CUDA(launch_pdl(dense_gemv_kernel<T>, dim3((unsigned)blocks), dim3(256), 0, s, M, n, x, y));
         count_launch();
     }
     FSI_CUDA(cudaGetLastError());

@@ -38,8 +38,11 @@ template <int G, int U, class TA, class TX, class TY>
 __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int32_t *__restrict__ ptr,
                                                    const int32_t *__restrict__ col,
                                                    const TA *__restrict__ val, const TX *__restrict__ x,
-                                                   const TY *__restrict__ b, TY *__restrict__ y, int mode) {
+                                                   const TY *__restrict__ b, TY *__restrict__ y, int mode,
+                                                   TY *__restrict__ zero_out) {
     using AT = typename Acc<TA, TX>::type;
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x % G;
     const int64_t rows_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -74,19 +77,21 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int32_t *__r
             if (mode == SPMV_SET) y[row] = (TY)acc;
             else if (mode == SPMV_RESID) y[row] = (TY)((AT)b[row] - acc);
             else y[row] = (TY)((AT)y[row] + acc);
+            if (zero_out) zero_out[row] = TY(0);
         }
         row += rows_per_grid;
     }
 }
 
 template <int G, int U, class TA, class TX, class TY>
-fsi_status run(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s) {
+fsi_status run(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s,
+               TY *zero_out) {
     const int threads = 256;
     int64_t blocks = (A.n_rows * G + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    spmv_kernel<G, U, TA, TX, TY><<<(unsigned)blocks, threads, 0, s>>>(A.n_rows, A.ptr.as<int32_t>(),
-                                                                       A.col.as<int32_t>(), val, x, b, y, mode);
+    FSI_CUDA(launch_pdl(spmv_kernel<G, U, TA, TX, TY>, dim3((unsigned)blocks), dim3(threads), 0, s, A.n_rows,
+                        A.ptr.as<int32_t>(), A.col.as<int32_t>(), val, x, b, y, mode, zero_out));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -105,8 +110,10 @@ __global__ void __launch_bounds__(256) ell_spmv_kernel(const EllBin *__restrict_
                                                        const int32_t *__restrict__ perm,
                                                        const int32_t *__restrict__ col,
                                                        const TA *__restrict__ val, const TX *__restrict__ x,
-                                                       const TY *__restrict__ b, TY *__restrict__ y, int mode) {
+                                                       const TY *__restrict__ b, TY *__restrict__ y, int mode,
+                                                       TY *__restrict__ zero_out) {
     using AT = typename Acc<TA, TX>::type;
+    pdl_trigger();
     const int64_t slab = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (slab >= nslabs) return;                      // whole warps
     const int lane = threadIdx.x % 32, sub = lane % G;
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(256) ell_spmv_kernel(const EllBin *__restrict_
     const int t = (int)(slab - slab0) * (32 / G) + lane / G;   // < stride
     const int32_t *cp = col + off + t;
     const TA *vp = val + off + t;
+    pdl_wait();                                      // x, b, y belong to earlier kernels
     AT a0 = 0, a1 = 0;
     if constexpr (G == 1) {
         // large operators: full chunks, then the remainder one by one
@@ -182,36 +190,47 @@ __global__ void __launch_bounds__(256) ell_spmv_kernel(const EllBin *__restrict_
         if (mode == SPMV_SET) y[r] = (TY)acc;
         else if (mode == SPMV_RESID) y[r] = (TY)((AT)b[r] - acc);
         else y[r] = (TY)((AT)y[r] + acc);
+        if (zero_out) zero_out[r] = TY(0);
     }
 }
 
 template <int G, bool STREAM, class TA, class TX, class TY>
-fsi_status run_ell_g(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s) {
+fsi_status run_ell_g(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s,
+                     TY *zero_out) {
     const int threads = 256;
     const int64_t blocks = (E.nslabs * 32 + threads - 1) / threads;
     if (blocks < 1) return FSI_OK;
     constexpr int UNR = sizeof(TA) == 8 ? 6 : 8;
-    ell_spmv_kernel<G, STREAM, UNR, TA, TX, TY><<<(unsigned)blocks, threads, 0, s>>>(
-        E.bins.as<EllBin>(), E.nbins, E.nslabs, E.perm.as<int32_t>(), E.col.as<int32_t>(), val, x, b, y, mode);
+    FSI_CUDA(launch_pdl(ell_spmv_kernel<G, STREAM, UNR, TA, TX, TY>, dim3((unsigned)blocks), dim3(threads), 0, s,
+                        E.bins.as<EllBin>(), E.nbins, E.nslabs, E.perm.as<int32_t>(), E.col.as<int32_t>(), val, x,
+                        b, y, mode, zero_out));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
 template <class TA, class TX, class TY>
-fsi_status run_ell(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s) {
+fsi_status run_ell(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s,
+                   TY *z) {
     if (E.stream) {
         switch (E.G) {
-            case 1: return run_ell_g<1, true>(E, val, x, b, y, mode, s);
-            default: return run_ell_g<4, true>(E, val, x, b, y, mode, s);
+            case 1: return run_ell_g<1, true>(E, val, x, b, y, mode, s, z);
+            default: return run_ell_g<4, true>(E, val, x, b, y, mode, s, z);
         }
     }
     switch (E.G) {
-        case 1: return run_ell_g<1, false>(E, val, x, b, y, mode, s);
-        case 4: return run_ell_g<4, false>(E, val, x, b, y, mode, s);
-        case 8: return run_ell_g<8, false>(E, val, x, b, y, mode, s);
-        default: return run_ell_g<16, false>(E, val, x, b, y, mode, s);
+        case 1: return run_ell_g<1, false>(E, val, x, b, y, mode, s, z);
+        case 4: return run_ell_g<4, false>(E, val, x, b, y, mode, s, z);
+        case 8: return run_ell_g<8, false>(E, val, x, b, y, mode, s, z);
+        default: return run_ell_g<16, false>(E, val, x, b, y, mode, s, z);
     }
+}
+
+template <class T>
+__global__ void zero_kernel(T *__restrict__ v, int64_t n) {
+    pdl_trigger();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = T(0);
 }
 
 // one thread per CSR row: copy its entries to their ELL positions
@@ -365,13 +384,13 @@ fsi_status ell_fill_f32(DevCSR &A, cudaStream_t s) {
 
 template <class TA, class TX, class TY>
 fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, int mode,
-                       cudaStream_t s) {
+                       cudaStream_t s, TY *zero_out) {
     if (A.n_rows == 0) return FSI_OK;
     if (A.ell.nbins > 0) {
         const void *ev = nullptr;
         if ((const void *)val == A.val64.p) ev = A.ell.val64.p;
         else if ((const void *)val == A.val32.p) ev = A.ell.val32.p;
-        if (ev) return run_ell<TA, TX, TY>(A.ell, static_cast<const TA *>(ev), x, b, y, mode, s);
+        if (ev) return run_ell<TA, TX, TY>(A.ell, static_cast<const TA *>(ev), x, b, y, mode, s, zero_out);
     }
     // float64 accumulation: at most 4 lanes per row, so the shuffle tree adds
     // 2 float64 steps per lane instead of 5 (float64 issue rate is the limit;
@@ -384,10 +403,10 @@ fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b,
     const int U = need <= 2 ? 2 : (need <= 4 ? 4 : (need <= 6 ? 6 : 8));
 #define FSI_SPMV_U(GG)                                              \
     switch (U) {                                                    \
-        case 2: return run<GG, 2>(A, val, x, b, y, mode, s);        \
-        case 4: return run<GG, 4>(A, val, x, b, y, mode, s);        \
-        case 6: return run<GG, 6>(A, val, x, b, y, mode, s);        \
-        default: return run<GG, 8>(A, val, x, b, y, mode, s);       \
+        case 2: return run<GG, 2>(A, val, x, b, y, mode, s, zero_out);  \
+        case 4: return run<GG, 4>(A, val, x, b, y, mode, s, zero_out);  \
+        case 6: return run<GG, 6>(A, val, x, b, y, mode, s, zero_out);  \
+        default: return run<GG, 8>(A, val, x, b, y, mode, s, zero_out); \
     }
     switch (G) {
         case 1: FSI_SPMV_U(1);
@@ -400,8 +419,21 @@ fsi_status launch_spmv(const DevCSR &A, const TA *val, const TX *x, const TY *b,
 }
 
 template fsi_status launch_spmv<double, double, double>(const DevCSR &, const double *, const double *,
-                                                        const double *, double *, int, cudaStream_t);
+                                                        const double *, double *, int, cudaStream_t, double *);
 template fsi_status launch_spmv<float, float, float>(const DevCSR &, const float *, const float *,
-                                                     const float *, float *, int, cudaStream_t);
+                                                     const float *, float *, int, cudaStream_t, float *);
+
+template <class T>
+fsi_status launch_zero(T *v, int64_t n, cudaStream_t s) {
+    if (n == 0) return FSI_OK;
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    zero_kernel<T><<<(unsigned)g, 256, 0, s>>>(v, n);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+template fsi_status launch_zero<float>(float *, int64_t, cudaStream_t);
+template fsi_status launch_zero<double>(double *, int64_t, cudaStream_t);
 
 }  // namespace fsi
