@@ -347,20 +347,23 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
         if (V32) FSI_TRY(launch_mdot32(V32, n, nv, w, n, part, NDOT, s));
         else FSI_TRY(launch_mdot(V, n, nv, w, n, part, NDOT, s));
     }
-    FSI_TRY(launch_reduce_partials(part, NDOT, nv, h1, 0, s));
     {
-        ProfMark pm(cx, 6, true);       // float64 update + dots: 2 nv FMAs per row
-        if (cx.profile) cx.prof_work[6] += 2.0 * nv * n;
-        FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s));
+        PdlScope pdl;                   // programmatic launches up to the Givens step
+        FSI_TRY(launch_reduce_partials(part, NDOT, nv, h1, 0, s));
+        {
+            ProfMark pm(cx, 6, true);       // float64 update (+ float64 dots): nv (2 nv) FMAs per row
+            if (cx.profile) cx.prof_work[6] += (V32 ? 1.0 : 2.0) * nv * n;
+            FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s, nullptr, V32));
+        }
+        FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
+        {
+            ProfMark pm(cx, 6, true);       // float64 update + norm: nv + 1 FMAs per row
+            if (cx.profile) cx.prof_work[6] += (nv + 1.0) * n;
+            FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
+        }
+        FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
+        FSI_TRY(launch_givens(H, m + 1, j, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s));
     }
-    FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
-    {
-        ProfMark pm(cx, 6, true);       // float64 update + norm: nv + 1 FMAs per row
-        if (cx.profile) cx.prof_work[6] += (nv + 1.0) * n;
-        FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
-    }
-    FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
-    FSI_TRY(launch_givens(H, m + 1, j, h1, h2, scal + 7, pb.cs.as<double>(), pb.sn.as<double>(), g, scal, s));
     FSI_CUDA(cudaMemcpyAsync(pb.h_scal, scal, 5 * 8, cudaMemcpyDeviceToHost, s));
     FSI_TRY(launch_scale_copy(w, V + (size_t)(j + 1) * n, scal, 1, n, s, nullptr, 0,
                               V32 ? V32 + (size_t)(j + 1) * n : nullptr));
@@ -1057,6 +1060,7 @@ fsi_status issue_step_dev_head(Context &cx, Problem &pb, bool tr, cudaGraphCondi
     double *zf = pb.zbuf.as<double>();
     FSI_TRY(launch_take_column<double, T>(V, n, fg, F.b.as<T>(), n, s, sel));
     FSI_TRY(vcycle<T>(cx, pb, L - 1, F.b.as<T>(), F.x.as<T>(), tr));
+    PdlScope pdl;                     // both follow a kernel of the cycle
     FSI_TRY(launch_store_column<T>(F.x.as<T>(), zf, Z, n, fg, n, s));
     FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zf, (const double *)nullptr, w, SPMV_SET, s));
     return FSI_OK;
@@ -1072,8 +1076,9 @@ fsi_status issue_step_dev_tail(Context &cx, Problem &pb, int m, int nv_bound, cu
     float *V32 = cx.precision != FSI_FP64 ? pb.V32.as<float>() : nullptr;
     if (V32) FSI_TRY(launch_mdot32(V32, n, nv_bound, w, n, part, NDOT, s, fg));
     else FSI_TRY(launch_mdot(V, n, nv_bound, w, n, part, NDOT, s, fg));
+    PdlScope pdl;                     // the rest of the step follows kernels of this body
     FSI_TRY(launch_reduce_partials(part, NDOT, nv_bound, h1, 0, s, fg));
-    FSI_TRY(launch_update_dot(w, V, n, nv_bound, h1, n, part, NRED, 0, s, fg));
+    FSI_TRY(launch_update_dot(w, V, n, nv_bound, h1, n, part, NRED, 0, s, fg, V32));
     FSI_TRY(launch_reduce_partials(part, NRED, nv_bound, h2, 0, s, fg));
     FSI_TRY(launch_update_dot(w, V, n, nv_bound, h2, n, part, NRED, 1, s, fg));
     FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));

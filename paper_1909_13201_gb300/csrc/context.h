@@ -283,9 +283,10 @@ fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int t
 // a device-side loop; the host argument then only bounds the template size.
 fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
                        double *partials, int nblocks, cudaStream_t s, const FgState *fg = nullptr);
+// V32 (optional, mixed modes): float32 copy of the basis for float32 dots in pass 2
 fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
                              int64_t n, double *partials, int nblocks, int norm_only,
-                             cudaStream_t s, const FgState *fg = nullptr);
+                             cudaStream_t s, const FgState *fg = nullptr, const float *V32 = nullptr);
 fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out,
                                   int accumulate, cudaStream_t s, const FgState *fg = nullptr);
 fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2,

@@ -178,6 +178,8 @@ template <int NV>
 __global__ void __launch_bounds__(KT, 2) mdot_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                   const double *__restrict__ w, int64_t n,
                                                   double *__restrict__ partials, const FgState *fg) {
+    pdl_trigger();
+    pdl_wait();
     if (fg) nv = min(fg->k + 1, NV);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
@@ -193,6 +195,8 @@ template <int NV>
 __global__ void __launch_bounds__(KT, 4) mdot32_kernel(const float *__restrict__ V, int64_t ld, int nv,
                                                     const double *__restrict__ w, int64_t n,
                                                     double *__restrict__ partials, const FgState *fg) {
+    pdl_trigger();
+    pdl_wait();
     if (fg) nv = min(fg->k + 1, NV);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
@@ -201,6 +205,12 @@ __global__ void __launch_bounds__(KT, 4) mdot32_kernel(const float *__restrict__
 
 // pass 2: w -= V h and partial dots V^T w (norm_only = 0);
 // pass 3: w -= V h and partial ||w||^2   (norm_only = 1).
+// With V32 (mixed modes) the dots of pass 2 are float32, from the float32
+// copy of the basis and w rounded to float32: they only measure the small
+// residue the first pass left, so their rounding leaves the basis orthogonal
+// to ~1e-6 instead of 1e-15, while both updates stay float64 and keep the
+// Arnoldi relation A Z = V H exact; half of the float64 multiply-adds of
+// the pass go to the float32 pipe.
 // NV <= 8: one thread per row does both.  Otherwise a thread first updates its row of the tile (the sum V[r, :] h in four
 // independent chains, then one subtraction), writes it back and into shared
 // memory; the warps then form the dots of the updated tile.  The basis tile
@@ -209,7 +219,9 @@ template <int NV>
 __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ w, const double *__restrict__ V,
                                                         int64_t ld, int nv, const double *__restrict__ h,
                                                         int64_t n, double *__restrict__ partials, int norm_only,
-                                                        const FgState *fg) {
+                                                        const FgState *fg, const float *__restrict__ V32) {
+    pdl_trigger();
+    pdl_wait();
     if (fg) nv = min(fg->k + 1, NV);
     __shared__ double hs[KMAX];
     __shared__ double ws[KT];
@@ -220,8 +232,12 @@ __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ 
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
     if constexpr (NV <= 8) {
         double acc[NV];
+        float accf[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        for (int i = 0; i < NV; ++i) {
+            acc[i] = 0.0;
+            accf[i] = 0.f;
+        }
         for (int64_t r = r0 + threadIdx.x; r < r1; r += KT) {
             double v[NV];
             double s = 0.0;
@@ -235,19 +251,32 @@ __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ 
             w[r] = wr;
             if (norm_only) {
                 nrm += wr * wr;
+            } else if (V32) {
+                const float wf = (float)wr;
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    if (i < nv) accf[i] = fmaf(__ldg(V32 + (size_t)i * ld + r), wf, accf[i]);
             } else {
 #pragma unroll
                 for (int i = 0; i < NV; ++i)
                     if (i < nv) acc[i] += v[i] * wr;
             }
         }
+        if (V32 && !norm_only)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) acc[i] = (double)accf[i];
         if (norm_only) store_cta_sum(nrm, partials + (size_t)blockIdx.x * KMAX);
         else store_row_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
         return;
     }
     double acc[Slots<NV>::U];
+    float accf[Slots<NV>::U];
+    __shared__ float wsf[KT];
 #pragma unroll
-    for (int u = 0; u < Slots<NV>::U; ++u) acc[u] = 0.0;
+    for (int u = 0; u < Slots<NV>::U; ++u) {
+        acc[u] = 0.0;
+        accf[u] = 0.f;
+    }
     for (int64_t t0 = r0; t0 < r1; t0 += KT) {
         const int64_t r = t0 + threadIdx.x;
         double wr = 0.0;
@@ -261,6 +290,11 @@ __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ 
         }
         if (norm_only) {
             nrm += wr * wr;
+        } else if (V32) {
+            wsf[threadIdx.x] = (float)wr;
+            __syncthreads();
+            tile_dots<NV>(V32, ld, nv, t0, r1, wsf, accf);
+            __syncthreads();
         } else {
             ws[threadIdx.x] = wr;
             __syncthreads();
@@ -269,6 +303,7 @@ __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ 
         }
     }
     if (norm_only) store_cta_sum(nrm, partials + (size_t)blockIdx.x * KMAX);
+    else if (V32) store_slot_partials<NV>(accf, nv, partials + (size_t)blockIdx.x * KMAX);
     else store_slot_partials<NV>(acc, nv, partials + (size_t)blockIdx.x * KMAX);
 }
 
@@ -276,6 +311,8 @@ __global__ void __launch_bounds__(KT, 2) update_dot_kernel(double *__restrict__ 
 // order, then a fixed shuffle tree (deterministic)
 __global__ void reduce_partials_kernel(const double *__restrict__ partials, int nblocks, int nv,
                                        double *__restrict__ out, int accumulate, const FgState *fg) {
+    pdl_trigger();
+    pdl_wait();
     if (fg) nv = min(fg->k + 1, KMAX);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     for (int i = warp; i < nv; i += nw) {
@@ -301,6 +338,8 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, int 
 __global__ void givens_kernel(double *H, int ld, int j, const double *h1, const double *h2,
                               const double *hn2, double *cs, double *sn, double *g, double *scal,
                               FgState *fg, cudaGraphConditionalHandle loop) {
+    pdl_trigger();
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (fg) j = fg->k;
     double *col = H + (size_t)j * ld;
@@ -350,6 +389,8 @@ __global__ void givens_kernel(double *H, int ld, int j, const double *h1, const 
 __global__ void scale_copy_kernel(const double *__restrict__ w, double *__restrict__ v, float *__restrict__ v32,
                                   const double *__restrict__ scal, int idx, int64_t n, const FgState *fg,
                                   int64_t ld) {
+    pdl_trigger();
+    pdl_wait();
     if (fg) {
         v += (size_t)fg->k * ld;
         if (v32) v32 += (size_t)fg->k * ld;
@@ -424,6 +465,8 @@ __global__ void take_column_kernel(const TI *__restrict__ V, int64_t ld, const F
 template <class T>
 __global__ void store_column_kernel(const T *__restrict__ z, double *__restrict__ zfix, double *__restrict__ Z,
                                     int64_t ld, const FgState *fg, int64_t n) {
+    pdl_trigger();
+    pdl_wait();
     double *zc = Z + (size_t)fg->k * ld;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = (double)z[i];
@@ -522,7 +565,7 @@ fsi_status measure_fp64_rate(int num_sms, cudaStream_t s, double *gflops) {
 fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int64_t n,
                        double *partials, int nblocks, cudaStream_t s, const FgState *fg) {
     if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
-#define CALL_MDOT(NV) mdot_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials, fg)
+#define CALL_MDOT(NV) FSI_CUDA(launch_pdl(mdot_kernel<NV>, dim3(nblocks), dim3(KT), 0, s, V, ld, nv, w, n, partials, fg))
     FSI_NV_SWITCH(nv, CALL_MDOT);
 #undef CALL_MDOT
     count_launch();
@@ -533,7 +576,7 @@ fsi_status launch_mdot(const double *V, int64_t ld, int nv, const double *w, int
 fsi_status launch_mdot32(const float *V, int64_t ld, int nv, const double *w, int64_t n, double *partials,
                          int nblocks, cudaStream_t s, const FgState *fg) {
     if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
-#define CALL_MDOT32(NV) mdot32_kernel<NV><<<nblocks, KT, 0, s>>>(V, ld, nv, w, n, partials, fg)
+#define CALL_MDOT32(NV) FSI_CUDA(launch_pdl(mdot32_kernel<NV>, dim3(nblocks), dim3(KT), 0, s, V, ld, nv, w, n, partials, fg))
     FSI_NV_SWITCH(nv, CALL_MDOT32);
 #undef CALL_MDOT32
     count_launch();
@@ -543,9 +586,9 @@ fsi_status launch_mdot32(const float *V, int64_t ld, int nv, const double *w, in
 
 fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, const double *h,
                              int64_t n, double *partials, int nblocks, int norm_only, cudaStream_t s,
-                             const FgState *fg) {
+                             const FgState *fg, const float *V32) {
     if (nv > KMAX) { set_error("too many Krylov vectors"); return FSI_ERR_ARG; }
-#define CALL_UPD(NV) update_dot_kernel<NV><<<nblocks, KT, 0, s>>>(w, V, ld, nv, h, n, partials, norm_only, fg)
+#define CALL_UPD(NV) FSI_CUDA(launch_pdl(update_dot_kernel<NV>, dim3(nblocks), dim3(KT), 0, s, w, V, ld, nv, h, n, partials, norm_only, fg, V32))
     FSI_NV_SWITCH(nv, CALL_UPD);
 #undef CALL_UPD
     count_launch();
@@ -555,7 +598,7 @@ fsi_status launch_update_dot(double *w, const double *V, int64_t ld, int nv, con
 
 fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, double *out, int accumulate,
                                   cudaStream_t s, const FgState *fg) {
-    reduce_partials_kernel<<<1, 1024, 0, s>>>(partials, nblocks, nv, out, accumulate, fg);
+    FSI_CUDA(launch_pdl(reduce_partials_kernel, dim3(1), dim3(1024), 0, s, partials, nblocks, nv, out, accumulate, fg));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -564,7 +607,7 @@ fsi_status launch_reduce_partials(const double *partials, int nblocks, int nv, d
 fsi_status launch_givens(double *H, int ld, int j, const double *h1, const double *h2, const double *hn2,
                          double *cs, double *sn, double *g, double *scal, cudaStream_t s, FgState *fg,
                          cudaGraphConditionalHandle loop) {
-    givens_kernel<<<1, 32, 0, s>>>(H, ld, j, h1, h2, hn2, cs, sn, g, scal, fg, loop);
+    FSI_CUDA(launch_pdl(givens_kernel, dim3(1), dim3(32), 0, s, H, ld, j, h1, h2, hn2, cs, sn, g, scal, fg, loop));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -572,7 +615,7 @@ fsi_status launch_givens(double *H, int ld, int j, const double *h1, const doubl
 
 fsi_status launch_scale_copy(const double *w, double *v, const double *scal, int idx, int64_t n,
                              cudaStream_t s, const FgState *fg, int64_t ld, float *v32) {
-    scale_copy_kernel<<<egrid(n), 256, 0, s>>>(w, v, v32, scal, idx, n, fg, ld);
+    FSI_CUDA(launch_pdl(scale_copy_kernel, dim3(egrid(n)), dim3(256), 0, s, w, v, v32, scal, idx, n, fg, ld));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
@@ -624,7 +667,7 @@ template fsi_status launch_take_column<double, double>(const double *, int64_t, 
 template <class T>
 fsi_status launch_store_column(const T *z, double *zfix, double *Z, int64_t ld, const FgState *fg, int64_t n,
                                cudaStream_t s) {
-    store_column_kernel<T><<<egrid(n), 256, 0, s>>>(z, zfix, Z, ld, fg, n);
+    FSI_CUDA(launch_pdl(store_column_kernel<T>, dim3(egrid(n)), dim3(256), 0, s, z, zfix, Z, ld, fg, n));
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
