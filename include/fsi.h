@@ -88,7 +88,17 @@ typedef struct {
                                  *     trailing updates on the tensor cores (tcgen05, TF32
                                  *     operands, float32 accumulation).
                                  * 2 and 3 need a mixed precision (FSI_ERR_ARG otherwise). */
+    int variant;                /* level preconditioner of the Richardson smoother (Sec. 3.2):
+                                 *   FSI_SMOOTHER_FS (0): the field-split FS-ASM P2 (the paper's
+                                 *     method): per pressure group a solid [d^s, p^s], a fluid
+                                 *     [d^f] and a fluid [u^f, p^f] block, Jacobi on K_u^s;
+                                 *   FSI_SMOOTHER_AS (1): the monolithic additive Schwarz method
+                                 *     the paper compares against: one block of all fields per
+                                 *     pressure group.  Blocks of more than ~500 dofs (3D) are
+                                 *     beyond the inversion kernels: FSI_ERR_ARG. */
 } fsi_smoother_opts;
+
+enum { FSI_SMOOTHER_FS = 0, FSI_SMOOTHER_AS = 1 };
 
 enum { FSI_FACTOR_AUTO = 0, FSI_FACTOR_FP64 = 1, FSI_FACTOR_FP32 = 2, FSI_FACTOR_TF32 = 3 };
 

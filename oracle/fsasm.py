@@ -98,15 +98,39 @@ def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
     return blocks
 
 
+def block_index_sets_monolithic(lev: Level, b: int) -> list[np.ndarray]:
+    """Blocks of the monolithic additive Schwarz preconditioner AS (Sec. 3.2):
+    the same pressure groups, but one block per group holding every variable
+    whose support meets the support of the group's pressures: the group's p^s
+    and p^f vertices and all displacement and velocity dofs, of both classes,
+    on the closure of all elements touching them (fixed dofs excluded)."""
+    touch = vertex_elements(lev)
+    blocks = []
+    for grp in vertex_groups(lev, b):
+        els = touch[grp].ravel()
+        els = np.unique(els[els >= 0])
+        q2 = np.unique(lev.elem_q2[els])
+        p = np.concatenate([lev.ps_dof[grp], lev.pf_dof[grp]])
+        idx = np.concatenate([lev.d_dof[q2].ravel(), lev.v_dof[q2].ravel(), p[p >= 0]])
+        idx = np.unique(idx)
+        idx = idx[~lev.fixed[idx]]
+        if idx.size:
+            blocks.append(idx)
+    return blocks
+
+
 class FSASM:
-    """The smoother's preconditioner P2^{-1} on one level."""
+    """The smoother's preconditioner on one level: the field-split P2^{-1}
+    (default) or, with monolithic=True, the additive Schwarz method AS whose
+    blocks hold all fields (Sec. 3.2); fixed dofs take a Jacobi step in both,
+    the lumped K_u^s rows only in the field split."""
 
     def __init__(self, A: sp.csr_matrix, lev: Level, b: int, *, dtype=np.float64,
-                 weighted: bool = True, half: bool = False):
+                 weighted: bool = True, half: bool = False, monolithic: bool = False):
         self.n = A.shape[0]
         self.dtype = np.float32 if half else dtype
         self.half = half
-        self.blocks = block_index_sets(lev, b)
+        self.blocks = block_index_sets_monolithic(lev, b) if monolithic else block_index_sets(lev, b)
         mult = np.zeros(self.n)
         for idx in self.blocks:
             mult[idx] += 1.0
@@ -134,7 +158,7 @@ class FSASM:
                 self.lu.append((m16, scale.astype(np.float32)))
             else:
                 self.lu.append(la.lu_factor(blk.astype(dtype), check_finite=True))
-        self.jacobi = np.flatnonzero((lev.group == G_US) | lev.fixed)
+        self.jacobi = np.flatnonzero(lev.fixed if monolithic else (lev.group == G_US) | lev.fixed)
         self.inv_diag = 1.0 / Ad.diagonal()[self.jacobi]
 
     def apply(self, r: np.ndarray) -> np.ndarray:

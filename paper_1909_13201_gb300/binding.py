@@ -18,6 +18,7 @@ FSI_OK, FSI_ERR_ARG, FSI_ERR_CUDA, FSI_ERR_ALLOC, FSI_ERR_ZERO_PIVOT, FSI_ERR_NO
     FSI_ERR_BREAKDOWN, FSI_ERR_NONFINITE, FSI_ERR_STATE = range(9)
 FSI_FP64, FSI_MIXED, FSI_MIXED_HALF = 0, 1, 2
 FSI_FACTOR_AUTO, FSI_FACTOR_FP64, FSI_FACTOR_FP32, FSI_FACTOR_TF32 = 0, 1, 2, 3
+FSI_SMOOTHER_FS, FSI_SMOOTHER_AS = 0, 1
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_ALLOC", 4: "ERR_ZERO_PIVOT",
                 5: "ERR_NOT_CONVERGED", 6: "ERR_BREAKDOWN", 7: "ERR_NONFINITE", 8: "ERR_STATE"}
 
@@ -48,7 +49,7 @@ class HierOpts_t(C.Structure):
 
 class SmootherOpts_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("patch", C.c_int), ("omega", C.c_double),
-                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("factor", C.c_int)]
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("factor", C.c_int), ("variant", C.c_int)]
 
 
 class SolveOpts_t(C.Structure):
@@ -175,12 +176,12 @@ class FSISolver:
             pass
 
     def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=None, nu_pre=1, nu_post=1,
-                        factor=FSI_FACTOR_AUTO):
+                        factor=FSI_FACTOR_AUTO, variant=FSI_SMOOTHER_FS):
         if patch is None:
             patch = self.problems[0].patch
         if omega is None:
             omega = getattr(self.problems[0], "omega", 1.0)
-        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor)
+        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor, variant)
         _check(load_library().fsi_setup_smoothers(self.ctx, C.byref(so)))
         self.precision = precision
 

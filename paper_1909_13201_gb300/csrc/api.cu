@@ -753,7 +753,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_TRY(D.x.alloc((size_t)D.n * tsz));
         FSI_TRY(D.r.alloc((size_t)D.n * tsz));
         if (l == 0) continue;
-        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx);
+        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx, cx.variant == FSI_SMOOTHER_AS);
         D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
         std::vector<int32_t> bp(D.h_blk_ptr.begin(), D.h_blk_ptr.end());
         std::vector<int64_t> off(D.n_blocks + 1, 0);
@@ -786,7 +786,8 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         // Jacobi rows: u^s (lumped K_u^s, Sec. 3.2) and fixed dofs
         std::vector<int32_t> jac;
         for (int64_t i = 0; i < D.n; ++i)
-            if (H.fixed[i] || (i >= H.off[3] && i < H.off[4])) jac.push_back((int32_t)i);
+            if (H.fixed[i] || (cx.variant == FSI_SMOOTHER_FS && i >= H.off[3] && i < H.off[4]))
+                jac.push_back((int32_t)i);
         D.n_jac = (int64_t)jac.size();
         FSI_TRY(upload(D.jac_idx, jac.data(), jac.size() * 4, s));
         FSI_TRY(D.jac_inv.alloc((size_t)std::max<int64_t>(D.n_jac, 1) * tsz));
@@ -1004,7 +1005,8 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
     if (opts->precision < FSI_FP64 || opts->precision > FSI_MIXED_HALF || opts->patch < 1 || opts->patch > 16 ||
         !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8 ||
-        opts->factor < FSI_FACTOR_AUTO || opts->factor > FSI_FACTOR_TF32) {
+        opts->factor < FSI_FACTOR_AUTO || opts->factor > FSI_FACTOR_TF32 ||
+        (opts->variant != FSI_SMOOTHER_FS && opts->variant != FSI_SMOOTHER_AS)) {
         set_error("smoother options out of range");
         return FSI_ERR_ARG;
     }
@@ -1020,6 +1022,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     cx->nu_pre = opts->nu_pre;
     cx->nu_post = opts->nu_post;
     cx->factor = opts->factor;
+    cx->variant = opts->variant;
     cx->smoothers_ready = false;
     for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
     FSI_CUDA(cudaStreamSynchronize(cx->stream));

@@ -208,6 +208,7 @@ struct Context {
     double omega = 1.0;
     int nu_pre = 1, nu_post = 1;
     int factor = FSI_FACTOR_AUTO;    // block inversion method (resolved per precision)
+    int variant = FSI_SMOOTHER_FS;   // field-split (FS) or monolithic (AS) Schwarz blocks
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;

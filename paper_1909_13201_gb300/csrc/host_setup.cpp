@@ -505,7 +505,8 @@ void build_restriction(const HostCSR &P, const LevelHost &fine, const LevelHost 
         }
 }
 
-void build_blocks(const LevelHost &L, int b, std::vector<int64_t> &blk_ptr, std::vector<int32_t> &blk_idx) {
+void build_blocks(const LevelHost &L, int b, std::vector<int64_t> &blk_ptr, std::vector<int32_t> &blk_idx,
+                  bool monolithic) {
     const int dim = L.dim;
     const int64_t n = L.n, m1 = n + 1;
     const int64_t ng = (m1 + b - 1) / b;
@@ -565,6 +566,23 @@ void build_blocks(const LevelHost &L, int b, std::vector<int64_t> &blk_ptr, std:
             v.swap(out);
         };
         std::vector<int32_t> &S = per[g * 3 + 0], &Fd = per[g * 3 + 1], &Fu = per[g * 3 + 2];
+        if (monolithic) {
+            // AS: one block per group, every variable whose support meets the
+            // support of the group's pressures (both materials' elements)
+            std::vector<int64_t> all_el(sol_el);
+            all_el.insert(all_el.end(), flu_el.begin(), flu_el.end());
+            std::vector<int64_t> an;
+            nodes_of(all_el, an);
+            for (int64_t y : an)
+                for (int i = 0; i < dim; ++i) {
+                    S.push_back(L.d_dof[y * dim + i]);
+                    S.push_back(L.v_dof[y * dim + i]);
+                }
+            S.insert(S.end(), ps.begin(), ps.end());
+            S.insert(S.end(), pf.begin(), pf.end());
+            finish(S);
+            continue;
+        }
         if (!sol_el.empty()) {
             for (int64_t y : sn)
                 for (int i = 0; i < dim; ++i) S.push_back(L.d_dof[y * dim + i]);

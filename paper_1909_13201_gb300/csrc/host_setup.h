@@ -55,9 +55,11 @@ void build_prolongation(const LevelHost &fine, const LevelHost &coarse, HostCSR 
 void build_restriction(const HostCSR &P, const LevelHost &fine, const LevelHost &coarse,
                        bool classical, HostCSR &R);
 
-// Schwarz block index sets of a level (Vanka groups of b^dim pressure vertices).
+// Schwarz block index sets of a level (Vanka groups of b^dim pressure
+// vertices): field split (solid [d^s, p^s], fluid [d^f], fluid [u^f, p^f]
+// per group) or, monolithic, one block of all fields per group (AS).
 void build_blocks(const LevelHost &lev, int b, std::vector<int64_t> &blk_ptr,
-                  std::vector<int32_t> &blk_idx);
+                  std::vector<int32_t> &blk_idx, bool monolithic = false);
 
 // Reference-cell tables of the 4-point Gauss rule: weights, Q2 values and
 // gradients, Q1 values; layout [q][a], [q][k][a], [q][al].

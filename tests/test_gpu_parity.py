@@ -437,3 +437,54 @@ def test_batch_larger_than_hardware_queues():
     _, sts8 = sb.solve_batched(bs, rtol=1e-8)
     for st, it1 in zip(sts8, singles):
         assert st["converged"] and abs(st["iterations"] - it1) <= 1, (st["iterations"], it1)
+
+
+# ---- monolithic additive Schwarz AS, the paper's comparison preconditioner (Sec. 3.2)
+
+@pytest.fixture(scope="module", params=list(PROBLEMS))
+def as_case(request):
+    p = PROBLEMS[request.param]()
+    H = gmg.Hierarchy(p, monolithic=True)
+    s = binding.FSISolver(p)
+    s.setup_smoothers(precision=binding.FSI_FP64, variant=binding.FSI_SMOOTHER_AS)
+    return request.param, p, H, s
+
+
+def test_as_blocks_and_smoother_fp64(as_case):
+    """AS block sets equal the oracle's on every level; the AS smoother and its
+    transpose match the oracle to 1e-9 (FP64 Gauss-Jordan vs pivoted LU)."""
+    name, p, H, s = as_case
+    rng = np.random.default_rng(31)
+    for l in range(1, len(H.A)):
+        ptr, idx = s.blocks(l)
+        S = H.smoothers[l]
+        assert len(ptr) - 1 == len(S.blocks), (name, l)
+        for j, ref in enumerate(S.blocks):
+            np.testing.assert_array_equal(idx[ptr[j]:ptr[j + 1]], ref)
+        r = rng.standard_normal(H.A[l].shape[0])
+        for tr in (False, True):
+            y = s.apply_smoother(l, _cuda(r), transpose=tr).cpu().numpy()
+            ref = S.apply_transpose(r) if tr else S.apply(r)
+            assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(ref), (name, l, tr)
+
+
+def test_as_solves_fp64_and_mixed(as_case):
+    """AS-preconditioned FGMRES: FP64 solution to 1e-9 of the direct solution,
+    iterations +-1 of the oracle's; mixed precision (FP16 inverses, tensor-core
+    factors) to 1e-8, iterations +-2 of the oracle's emulation."""
+    name, p, H, s = as_case
+    b = _rhs(p, H, 32)
+    xd = _direct(H.fine, b)
+    x, st = s.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-9 * np.linalg.norm(xd)
+    _, st8 = s.solve(_cuda(b), rtol=1e-8)
+    _, ost = ofg.solve(H, b, rtol=1e-8)
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
+    sm = binding.FSISolver(p)
+    sm.setup_smoothers(precision=binding.FSI_MIXED_HALF, variant=binding.FSI_SMOOTHER_AS)
+    x, st = sm.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+    Hm = gmg.Hierarchy(p, mixed="half", monolithic=True)
+    _, ostm = ofg.solve(Hm, b, rtol=1e-8)
+    _, stm = sm.solve(_cuda(b), rtol=1e-8)
+    assert abs(stm["iterations"] - ostm["iterations"]) <= 2, (stm["iterations"], ostm["iterations"])

@@ -5,6 +5,10 @@
   covering the whole level the smoother equals the exact solve with the
   field-split block-diagonal matrix (AS1 solid/fluid, AS2 Jacobi + fluid);
   the Jacobi step on K_u^s is exact; the transposed apply is the adjoint.
+* AS (the paper's monolithic comparison method, Sec. 3.2): block sets against
+  a brute-force statement of the Vanka rule over all fields; partition of
+  unity; one group covering the level gives the exact solve; GMG-FGMRES with
+  AS smoothing matches a sparse direct solve.
 * GMG: a 1-level hierarchy is the direct solve; the transposed V-cycle is the
   adjoint of the V-cycle; a two-grid spectral radius below 1 on this
   workload; mixed mode stays within float32 rounding of the float64 cycle.
@@ -246,3 +250,68 @@ def test_adjoint_gradients_central_differences():
         q.lambda_s = p.lambda_s
         Js.append(J(assemble(q, lev), b))
     assert gmu == pytest.approx((Js[0] - Js[1]) / (2 * h * 50.0), rel=1e-5)
+
+
+# ---- monolithic additive Schwarz AS (the paper's comparison preconditioner, Sec. 3.2)
+
+def test_monolithic_block_sets_bruteforce_geometry():
+    """AS block of a pressure group = its p^s and p^f dofs plus every d and u
+    dof (both classes) on the closure of the elements touching its vertices
+    (the union of the supports of its pressures), fixed dofs removed."""
+    p = I.make_channel_2d(8, 1, 2, 5, bulge=True, band_width=0.3)
+    lev = mesh.build_levels(p)[0]
+    h = lev.h
+    got = fsasm.block_index_sets_monolithic(lev, 2)
+    q2xy = mesh.lex(2, 2 * lev.n + 1) * (h / 2)
+    q1xy = mesh.lex(2, lev.n + 1) * h
+
+    def inside(e, xy):
+        return ((e % lev.n) * h - 1e-12 <= xy[0] <= (e % lev.n + 1) * h + 1e-12 and
+                (e // lev.n) * h - 1e-12 <= xy[1] <= (e // lev.n + 1) * h + 1e-12)
+
+    expect = []
+    for gy in range(0, lev.n + 1, 2):
+        for gx in range(0, lev.n + 1, 2):
+            verts = [z for z in range(lev.nq1) if gx <= q1xy[z, 0] / h < gx + 2 - 1e-9
+                     and gy <= q1xy[z, 1] / h < gy + 2 - 1e-9]
+            els = [e for e in range(lev.material.size) if any(inside(e, q1xy[z]) for z in verts)]
+            nodes = [y for y in range(lev.nq2) if any(inside(e, q2xy[y]) for e in els)]
+            s = [lev.d_dof[y, c] for y in nodes for c in (0, 1)] + [lev.v_dof[y, c] for y in nodes for c in (0, 1)]
+            s += [lev.ps_dof[z] for z in verts if lev.ps_dof[z] >= 0] + [lev.pf_dof[z] for z in verts if lev.pf_dof[z] >= 0]
+            s = np.array(sorted(d for d in set(s) if not lev.fixed[d]), np.int64)
+            if s.size:
+                expect.append(s)
+    assert len(got) == len(expect)
+    for a, b in zip(got, expect):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_monolithic_partition_of_unity_and_whole_level_exact_solve():
+    """AS weights sum to one on every free dof (fixed dofs: Jacobi only), and
+    with one pressure group covering the level AS is the exact solve."""
+    p = I.make_channel_2d(6, 1, 1, 3, bulge=True, band_width=0.4)
+    lev = mesh.build_levels(p)[0]
+    A = assemble(p, lev)
+    S = fsasm.FSASM(A, lev, 2, monolithic=True)
+    tot = np.zeros(S.n)
+    for idx in S.blocks:
+        tot[idx] += S.weight[idx]
+    np.testing.assert_allclose(tot[~lev.fixed], 1.0, rtol=1e-15)
+    assert np.all(tot[lev.fixed] == 0) and np.array_equal(np.sort(S.jacobi), np.flatnonzero(lev.fixed))
+    S1 = fsasm.FSASM(A, lev, lev.n + 1, monolithic=True)
+    assert len(S1.blocks) == 1
+    r = np.random.default_rng(0).standard_normal(lev.n_dofs)
+    np.testing.assert_allclose(S1.apply(r), spl.spsolve(A.tocsc(), r), rtol=1e-9, atol=1e-12)
+    r2 = np.random.default_rng(1).standard_normal(lev.n_dofs)
+    assert S.apply(r) @ r2 == pytest.approx(r @ S.apply_transpose(r2), rel=1e-11)
+
+
+def test_monolithic_gmg_fgmres_matches_direct_solve(c0):
+    p, _ = c0
+    H = gmg.Hierarchy(p, monolithic=True)
+    lev = H.levels[-1]
+    b = I.gather_natural(I.natural_vector(p, 4), lev.dof_field, lev.dof_comp, lev.dof_node)
+    x, st = fgmres.solve(H, b, rtol=1e-10)
+    xd = spl.spsolve(H.fine.tocsc(), b)
+    assert st["converged"]
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
