@@ -196,7 +196,12 @@ fsi_status smooth_apply(Context &cx, LevelDev &L, const T *r, T *x, bool tr, boo
 template <class T>
 fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr, bool x_zeroed = false) {
     cudaStream_t s = cx.stream;
-    if (l == 0) return launch_dense_gemv<T>(pb.coarse_inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
+    if (l == 0) {
+        // transposed cycle: the stored transpose, read row by row like the forward
+        // product (a column-by-column product of the row-major inverse takes 20x longer)
+        if (tr && pb.coarse_inv_t.p) return launch_dense_gemv<T>(pb.coarse_inv_t.as<double>(), pb.n0, b, x, 0, s);
+        return launch_dense_gemv<T>(pb.coarse_inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
+    }
     LevelDev &L = pb.dev[l];
     LevelDev &C = pb.dev[l - 1];
     const DevCSR &A = tr ? L.AT : L.A;
@@ -611,6 +616,10 @@ fsi_status check_opts(const fsi_solve_opts *o) {
 fsi_status build_transposes(Context &cx, Problem &pb) {
     if (pb.transposes_ready) return FSI_OK;
     cudaStream_t s = cx.stream;
+    if (!pb.coarse_inv_t.p) {
+        FSI_TRY(pb.coarse_inv_t.alloc((size_t)pb.n0 * pb.n0 * 8));
+        FSI_TRY(launch_transpose(pb.coarse_inv.as<double>(), pb.n0, pb.coarse_inv_t.as<double>(), s));
+    }
     for (size_t l = 0; l < pb.dev.size(); ++l) {
         LevelDev &L = pb.dev[l];
         HostCSR A, AT;

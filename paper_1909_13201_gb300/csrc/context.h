@@ -146,6 +146,7 @@ struct Problem {
     std::vector<HostCSR> hP, hR;     // host transfers (for accessors)
     int64_t n0 = 0;                  // coarse size
     DevBuf coarse_inv;               // n0 x n0 float64 inverse of A_0 (row-major)
+    DevBuf coarse_inv_t;             // its transpose (transposed cycle; built with the transposes)
     DevBuf coarse_b, coarse_x;       // float64 coarse vectors
     DevBuf dA_mu;                    // float64 values of dA/dmu_s on the fine pattern
     bool transposes_ready = false;
@@ -273,6 +274,8 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
                                   cudaStream_t s);
 
 fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s);
+// t = m^T for an n x n row-major float64 matrix
+fsi_status launch_transpose(const double *m, int64_t n, double *t, cudaStream_t s);
 
 template <class T>
 fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int transpose,

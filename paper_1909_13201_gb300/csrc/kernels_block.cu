@@ -420,6 +420,82 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_pipe_kernel(const
 }
 
 // transposed: A^{-1} = D_s M (D_s row scales), so A^{-T} W r = M^T (D_s W r)
+// Transposed float16 apply for blocks of at most 256 dofs, streamed by rows
+// like the forward apply: y[c] = sum_i M[i][c] (scale_i w_i r_i) for the
+// item's columns [c0, c1).  Lane q of a warp owns the 16-byte chunk q of the
+// item's columns in every row it visits; the warps take every fourth row
+// (4 rows in flight per lane) and their column partials meet in shared
+// memory before the scatter-add.  Replaces one thread per column walking all
+// rows (171 dependent 2-byte loads per thread).
+__global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_tr_kernel(const int4 *__restrict__ items,
+                                                                         const int32_t *__restrict__ blk_ptr,
+                                                                         const int32_t *__restrict__ blk_idx,
+                                                                         const int64_t *__restrict__ blk_off,
+                                                                         const float *__restrict__ blk_w,
+                                                                         const __half *__restrict__ inv,
+                                                                         const float *__restrict__ scale,
+                                                                         const int32_t *__restrict__ jac_idx,
+                                                                         const float *__restrict__ jac_inv,
+                                                                         const float *__restrict__ r,
+                                                                         float *__restrict__ x, float omega) {
+    constexpr int NW = APPLY_THREADS / 32;
+    __shared__ float rs[256];
+    __shared__ float part[NW][256];
+    pdl_trigger();
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, c0 = it.y, c1 = it.z;
+    pdl_wait();
+    if (blk < 0) {
+        for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+            const int i = jac_idx[k];
+            x[i] += omega * r[i] * jac_inv[k];
+        }
+        return;
+    }
+    const int s0 = blk_ptr[blk];
+    const int n = blk_ptr[blk + 1] - s0;
+    const int nv = ((n + 7) & ~7) / 8;            // 16-byte chunks per stored row
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = scale[s0 + i] * blk_w[s0 + i] * r[blk_idx[s0 + i]];
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int k0 = c0 / 8;                          // c0 is a multiple of 16
+    const int kk = k0 + lane;
+    const bool ok = kk < nv && lane * 8 < c1 - c0;     // chunk meets the item's columns
+    const uint4 *M = reinterpret_cast<const uint4 *>(inv + blk_off[blk]);
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int i = warp; i < n; i += 4 * NW) {
+        uint4 m[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = i + q * NW;
+            m[q] = (ok && row < n) ? __ldcs(M + (size_t)row * nv + kk) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = i + q * NW;
+            const float v = row < n ? rs[row] : 0.f;
+            const __half2 *h = reinterpret_cast<const __half2 *>(&m[q]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __half22float2(h[e]);
+                acc[2 * e] += f.x * v;
+                acc[2 * e + 1] += f.y * v;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) part[warp][lane * 8 + e] = acc[e];
+    __syncthreads();
+    for (int c = threadIdx.x; c < c1 - c0; c += blockDim.x) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += part[w][c];
+        atomicAdd(&x[blk_idx[s0 + c0 + c]], omega * sum);
+    }
+}
+
 __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const int4 *__restrict__ items,
                                                                         const int32_t *__restrict__ blk_ptr,
                                                                         const int32_t *__restrict__ blk_idx,
@@ -885,7 +961,12 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
     if (std::is_same<T, float>::value && lev.inv_store == 2) {
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
-        if (transpose)
+        if (transpose && lev.max_block <= 256)
+            FSI_CUDA(launch_pdl(block_apply_h_tr_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
+                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+                lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
+                lev.jac_inv.as<float>(), rf, xf, (float)omega));
+        else if (transpose)
             FSI_CUDA(launch_pdl(block_apply_h_t_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
                 lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
@@ -923,6 +1004,21 @@ fsi_status launch_jacobi_apply(const LevelDev &lev, const T *r, T *x, T omega, c
     int64_t g = (lev.n_jac + 255) / 256;
     if (g > 152 * 8) g = 152 * 8;
     jacobi_kernel<T><<<(unsigned)g, 256, 0, s>>>(lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), lev.n_jac, r, x, omega);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+__global__ void transpose_kernel(const double *__restrict__ m, int64_t n, double *__restrict__ t) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n * n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / n, j = k % n;
+        t[j * n + i] = m[k];
+    }
+}
+
+fsi_status launch_transpose(const double *m, int64_t n, double *t, cudaStream_t s) {
+    if (n == 0) return FSI_OK;
+    transpose_kernel<<<256, 256, 0, s>>>(m, n, t);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
