@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4
 // row.  The first group's loads are issued before the residual gather (the
 // HBM and L2 latencies overlap) and the next group's loads are in flight
 // while the current group is reduced and scattered.
-__global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_pipe_kernel(const int4 *__restrict__ items,
+__global__ void __launch_bounds__(APPLY_THREADS, 12) block_apply_h_pipe_kernel(const int4 *__restrict__ items,
                                                                            const int32_t *__restrict__ blk_ptr,
                                                                            const int32_t *__restrict__ blk_idx,
                                                                            const int64_t *__restrict__ blk_off,
