@@ -105,8 +105,9 @@ fsi_status run(const DevCSR &A, const TA *val, const TX *x, const TY *b, TY *y, 
 // G = 1 on large operators (no shuffles; enough rows to hide latency), up to
 // 16 on small ones (few rows, short chains).  STREAM: evict-first loads for
 // operators larger than L2 is useful for; small ones stay cached.
+// float32 with one lane per row: <= 40 registers, 6 CTAs (48 warps) per SM
 template <int G, bool STREAM, int UNR, class TA, class TX, class TY>
-__global__ void __launch_bounds__(256) ell_spmv_kernel(const EllBin *__restrict__ bins, int nbins, int64_t nslabs,
+__global__ void __launch_bounds__(256, (G == 1 && sizeof(TA) == 4) ? 6 : 0) ell_spmv_kernel(const EllBin *__restrict__ bins, int nbins, int64_t nslabs,
                                                        const int32_t *__restrict__ perm,
                                                        const int32_t *__restrict__ col,
                                                        const TA *__restrict__ val, const TX *__restrict__ x,
