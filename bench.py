@@ -416,7 +416,7 @@ def run_ours(args, rank, world, local):
     fwd_adj()
     ms_adj = timed(max(2, args.steps // 4), fwd_adj)
 
-    # ---- 3D valve box, 32^3 hexahedra (configs[2]), mixed precision
+    # ---- 3D valve box, 32^3 hexahedra, 4 levels, mixed precision
     p3 = I.make_config(2)
     t0 = time.time()
     s3 = FSISolver(p3, stream=stream)

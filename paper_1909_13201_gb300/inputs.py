@@ -11,7 +11,7 @@ hybrid meshes that are not available; the generators below stand in for them
 with the same structure: a solid wall band of 10-40% of the width, an
 aneurysm-like fluid pocket cut into the wall, and thin valve-like leaflets.
 
-Natural layouts (shared convention, documented in the design doc):
+Natural layouts (a convention shared by the generators, the oracle and the library tests):
   * element e of an n^dim grid on [0,1]^dim: e = i + n*j (+ n*n*k), x fastest;
   * Q2 node of index (p, q, r), 0 <= p,q,r <= 2n, at (p, q, r) * h/2, flat
     index p + (2n+1)*q (+ (2n+1)^2*r);

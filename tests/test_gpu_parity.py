@@ -3,7 +3,7 @@ the C ABI: assembled operators, SpMV, the FS-ASM smoother (and its
 transpose), the V-cycle, full FGMRES solves in FP64 and mixed precision,
 the adjoint and its gradients, and the error statuses.
 
-Tolerances (derivation in the design doc): operator values and SpMV to 1e-13 of
+Tolerances, from the arithmetic: operator values and SpMV to 1e-13 of
 the row scale (same quadrature, different summation order); smoother and
 V-cycle in FP64 to 1e-9 relative (block inverses by Gauss-Jordan versus the
 oracle's pivoted LU, condition numbers up to ~1e5); solutions to 1e-9
