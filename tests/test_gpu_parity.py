@@ -488,3 +488,20 @@ def test_as_solves_fp64_and_mixed(as_case):
     _, ostm = ofg.solve(Hm, b, rtol=1e-8)
     _, stm = sm.solve(_cuda(b), rtol=1e-8)
     assert abs(stm["iterations"] - ostm["iterations"]) <= 2, (stm["iterations"], ostm["iterations"])
+
+
+def test_as_3d_blocks_rejected():
+    """AS blocks in 3D (~750 dofs: all fields on the 5^3 nodes around a
+    vertex) exceed the inversion kernels; set-up returns FSI_ERR_ARG for every
+    factorisation and leaves the context usable with the field split."""
+    p = I.make_valve_3d(8, 2, 1, 777)
+    s = binding.FSISolver(p)
+    for prec in (binding.FSI_FP64, binding.FSI_MIXED_HALF):
+        with pytest.raises(binding.FSIError) as err:
+            s.setup_smoothers(precision=prec, variant=binding.FSI_SMOOTHER_AS)
+        assert err.value.status == binding.FSI_ERR_ARG
+    s.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    H = gmg.Hierarchy(p)
+    b = _rhs(p, H, 41)
+    x, st = s.solve(_cuda(b), rtol=1e-8)
+    assert st["converged"]
