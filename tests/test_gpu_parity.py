@@ -505,3 +505,24 @@ def test_as_3d_blocks_rejected():
     b = _rhs(p, H, 41)
     x, st = s.solve(_cuda(b), rtol=1e-8)
     assert st["converged"]
+
+
+@pytest.mark.parametrize("prec", [binding.FSI_MIXED, binding.FSI_MIXED_HALF])
+def test_mixed_adjoint_matches_direct_transposed_solve(case, prec):
+    """Mixed-precision adjoint (transposed float32 cycle: transposed FP16 or
+    float32 block applies streamed by rows, stored transpose of the coarse
+    inverse): lambda to 1e-8 of the direct solve of A^T lambda = w when solved
+    to a 1e-10 true residual, and lambda^T b = w^T x."""
+    name, p, H, s = case
+    sm = binding.FSISolver(p)
+    sm.setup_smoothers(precision=prec)
+    rng = np.random.default_rng(51)
+    b = _rhs(p, H, 52)
+    w = rng.standard_normal(b.size)
+    x, _ = sm.solve(_cuda(b), rtol=1e-10)
+    lam, _, _, st = sm.adjoint(_cuda(w), x, rtol=1e-10)
+    assert st["converged"]
+    lam = lam.cpu().numpy()
+    lam_d = _direct(H.fine.T.tocsr(), w)
+    assert np.linalg.norm(lam - lam_d) <= 1e-8 * np.linalg.norm(lam_d), (name, prec)
+    assert lam @ b == pytest.approx(w @ x.cpu().numpy(), rel=1e-8)
