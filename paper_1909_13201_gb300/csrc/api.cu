@@ -1070,8 +1070,8 @@ fsi_status issue_step_dev_head(Context &cx, Problem &pb, bool tr, cudaGraphCondi
     FgState *fg = pb.fg.as<FgState>();
     double *V = pb.V.as<double>(), *w = pb.w.as<double>(), *Z = pb.Z.as<double>();
     double *zf = pb.zbuf.as<double>();
-    FSI_TRY(launch_take_column<double, T>(V, n, fg, F.b.as<T>(), n, s, sel));
-    FSI_TRY(vcycle<T>(cx, pb, L - 1, F.b.as<T>(), F.x.as<T>(), tr));
+    FSI_TRY(launch_take_column<double, T>(V, n, fg, F.b.as<T>(), n, s, sel, F.x.as<T>()));
+    FSI_TRY(vcycle<T>(cx, pb, L - 1, F.b.as<T>(), F.x.as<T>(), tr, true));   // x zeroed above
     PdlScope pdl;                     // both follow a kernel of the cycle
     FSI_TRY(launch_store_column<T>(F.x.as<T>(), zf, Z, n, fg, n, s));
     FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), zf, (const double *)nullptr, w, SPMV_SET, s));

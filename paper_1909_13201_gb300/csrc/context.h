@@ -314,10 +314,11 @@ fsi_status launch_init_basis(const double *r, double *v0, double *g, int m, cons
                              cudaGraphConditionalHandle loop = 0, float *v0f = nullptr);
 // device-loop helpers: dst = (TO) V[:, fg->k]; zfix = Z[:, fg->k] = (double) z
 // take_column also selects the Gram-Schmidt variant of the step (SWITCH
-// node `sel`, value nv_class(fg->k + 1)) when sel is nonzero
+// node `sel`, value nv_class(fg->k + 1)) when sel is nonzero, and sets
+// zero[0..n) = 0 when zero is non-null (the cycle's fine correction)
 template <class TI, class TO>
 fsi_status launch_take_column(const TI *V, int64_t ld, const FgState *fg, TO *dst, int64_t n, cudaStream_t s,
-                              cudaGraphConditionalHandle sel = 0);
+                              cudaGraphConditionalHandle sel = 0, TO *zero = nullptr);
 // Gram-Schmidt kernels are instantiated for nv <= 1, 2, 4, 8, 16, 32, 65
 constexpr int NV_CLASSES = 7;
 __host__ __device__ inline int nv_class_bound(int c) { return c < 6 ? (1 << c) : 65; }

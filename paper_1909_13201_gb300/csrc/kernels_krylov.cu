@@ -450,7 +450,8 @@ __global__ void combine_kernel(double *__restrict__ x, const T *__restrict__ Z, 
 
 template <class TI, class TO>
 __global__ void take_column_kernel(const TI *__restrict__ V, int64_t ld, const FgState *fg, TO *__restrict__ dst,
-                                   int64_t n, cudaGraphConditionalHandle sel) {
+                                   int64_t n, cudaGraphConditionalHandle sel, TO *__restrict__ zero) {
+    pdl_trigger();
     if (sel && blockIdx.x == 0 && threadIdx.x == 0) {
         const int nv = fg->k + 1;
         int c = 0;
@@ -458,8 +459,10 @@ __global__ void take_column_kernel(const TI *__restrict__ V, int64_t ld, const F
         cudaGraphSetConditional(sel, (unsigned)c);
     }
     const TI *v = V + (size_t)fg->k * ld;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         dst[i] = (TO)v[i];
+        if (zero) zero[i] = TO(0);
+    }
 }
 
 template <class T>
@@ -653,16 +656,16 @@ template fsi_status launch_combine<double>(double *, const double *, int64_t, in
 
 template <class TI, class TO>
 fsi_status launch_take_column(const TI *V, int64_t ld, const FgState *fg, TO *dst, int64_t n, cudaStream_t s,
-                              cudaGraphConditionalHandle sel) {
-    take_column_kernel<TI, TO><<<egrid(n), 256, 0, s>>>(V, ld, fg, dst, n, sel);
+                              cudaGraphConditionalHandle sel, TO *zero) {
+    take_column_kernel<TI, TO><<<egrid(n), 256, 0, s>>>(V, ld, fg, dst, n, sel, zero);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 template fsi_status launch_take_column<double, float>(const double *, int64_t, const FgState *, float *, int64_t,
-                                                      cudaStream_t, cudaGraphConditionalHandle);
+                                                      cudaStream_t, cudaGraphConditionalHandle, float *);
 template fsi_status launch_take_column<double, double>(const double *, int64_t, const FgState *, double *, int64_t,
-                                                       cudaStream_t, cudaGraphConditionalHandle);
+                                                       cudaStream_t, cudaGraphConditionalHandle, double *);
 
 template <class T>
 fsi_status launch_store_column(const T *z, double *zfix, double *Z, int64_t ld, const FgState *fg, int64_t n,
