@@ -51,7 +51,7 @@ RTOL = 1e-8
 # FGMRES iterations the oracle's algorithm needs on each seeded workload to
 # reach RTOL (oracle.fgmres.solve on the same right-hand side); used to
 # project the oracle's per-iteration time to the metric.
-ORACLE_ITERATIONS = {1: 40, 4: 31}
+ORACLE_ITERATIONS = {0: 22, 1: 40, 4: 31}
 
 
 def parse():
@@ -71,6 +71,31 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# Replicas across ranks: every rank runs the whole workload on its own GPU;
+# the only cross-rank traffic is the timing barrier and the max of the
+# per-rank times (no collective on the data path).
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device):
+    """Slowest rank's value: the whole job takes as long as its slowest replica."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ms, world):
+    """Weak scaling: units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 # ---------------------------------------------------------------- oracle leg
@@ -226,17 +251,6 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     p = I.make_config(args.config)
     stream = torch.cuda.current_stream()
     t0 = time.time()
@@ -250,7 +264,7 @@ def run_ours(args, rank, world, local):
     x = torch.empty_like(b)
 
     def timed(k, fn):
-        barrier()
+        barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -258,8 +272,8 @@ def run_ours(args, rank, world, local):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / k)
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1) / k, world, dev)
 
     stats = {}
 
@@ -449,7 +463,7 @@ def run_ours(args, rank, world, local):
     del s3, b3, x3
     torch.cuda.empty_cache()
 
-    value = world * n / (ms * 1e-3)
+    value = job_throughput(n, ms, world)
     if rank != 0:
         return
     cpu = cpu_baseline(args.config) if world == 1 else None
@@ -464,14 +478,14 @@ def run_ours(args, rank, world, local):
                    "l2": "working set (~2.6 GB of block inverses and operators) larger than L2; no flush"},
         "iterations": st_mixed.get("iterations"), "rho": st_mixed.get("rho"),
         "rel_residual": st_mixed.get("rel_residual"),
-        "fp64": {"value": world * n / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": st64.get("iterations"),
+        "fp64": {"value": job_throughput(n, ms64, world), "ms_per_step": ms64, "iterations": st64.get("iterations"),
                  "speedup_mixed_over_fp64": ms64 / ms},
-        "mixed_f32_inverses": {"value": world * n / (ms32 * 1e-3), "ms_per_step": ms32,
+        "mixed_f32_inverses": {"value": job_throughput(n, ms32, world), "ms_per_step": ms32,
                                "iterations": st32.get("iterations")},
         "as_smoother": {"what": "monolithic additive Schwarz (one block of all fields per pressure group), "
                                 "the paper's comparison method; same cycle, mixed precision, float32 inverses "
                                 "(FP16 storage does not converge for these blocks)",
-                        "value": world * n / (ms_as * 1e-3), "ms_per_step": ms_as,
+                        "value": job_throughput(n, ms_as, world), "ms_per_step": ms_as,
                         "iterations": st_as.get("iterations"), "converged": bool(st_as.get("converged")),
                         "rel_residual": st_as.get("rel_residual"), "setup_s": setup_as_s,
                         "fs_speedup_over_as": ms_as / ms},
@@ -479,14 +493,14 @@ def run_ours(args, rank, world, local):
                     "ms_per_batch_patch3": ms_batch_fixed,
                     "autotune": {"candidates": list(tune_cand), "chosen_by_n_fine": chosen_by_size,
                                  "tune_s": tune_s},
-                    "solves_per_s": world * len(batch) / (ms_batch * 1e-3),
-                    "dof_per_s": world * batch_dofs / (ms_batch * 1e-3),
+                    "solves_per_s": job_throughput(len(batch), ms_batch, world),
+                    "dof_per_s": job_throughput(batch_dofs, ms_batch, world),
                     "iterations_min_max": [min(t["iterations"] for t in bstats),
                                            max(t["iterations"] for t in bstats)],
                     "all_converged": all(t["converged"] for t in bstats), "setup_s": setup_batch_s,
                     "workload": "64 seeded 2D channels, fine grids {32,48,64,96,128}^2, band width U[0.1,0.4]"},
         "valve3d": {"workload": p3.name, "unknowns": n3, "ms_per_solve": ms_3d,
-                    "dof_per_s": world * n3 / (ms_3d * 1e-3), "iterations": st3.get("iterations"),
+                    "dof_per_s": job_throughput(n3, ms_3d, world), "iterations": st3.get("iterations"),
                     "setup_s": {"hierarchy": setup_3d_hier_s, "smoothers": setup_3d_smooth_s,
                                 "fine_inversion_ms": inv3_ms,
                                 "fine_inversion_tflops": pf3["invert_flops"] / (inv3_ms * 1e-3) / 1e12,
@@ -495,11 +509,11 @@ def run_ours(args, rank, world, local):
                     "smoother_fine": {"mean_launch_ms": sm3, "achieved_gbs": pr3["smoother_bytes"] / sm3 / 1e6,
                                       "frac": pr3["smoother_bytes"] / sm3 / 1e6 / peak}},
         "adjoint": {"workload": pa.name, "unknowns": na, "ms_forward_plus_adjoint": ms_adj,
-                    "iterations": astats, "dof_per_s": world * na / (ms_adj * 1e-3)},
+                    "iterations": astats, "dof_per_s": job_throughput(na, ms_adj, world)},
         "factorization": fact,
         "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed_half": setup_mixed_s,
                     "smoothers_mixed_f32": setup_f32_s, "smoothers_fp64": setup_fp64_s},
-        "e2e": {"value": world * n / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+        "e2e": {"value": job_throughput(n, ms_e2e, world), "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
         "roofline": {"bound": "hbm", "kernel": "block_apply_h_kernel (fine level, f16 inverses)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
