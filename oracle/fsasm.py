@@ -43,7 +43,7 @@ import scipy.linalg as la
 import scipy.sparse as sp
 
 from .mesh import Level, flat, lex
-from .transfer import G_US
+from .transfer import G_DF, G_DS, G_PS, G_US
 
 
 def vertex_groups(lev: Level, b: int) -> list[np.ndarray]:
@@ -68,11 +68,13 @@ def vertex_elements(lev: Level) -> np.ndarray:
     return out
 
 
-def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
-    """Sorted dof index sets of all blocks: per vertex group solid, fluid-d, fluid-u."""
+def blocks_tagged(lev: Level, b: int) -> list[tuple[int, int, np.ndarray]]:
+    """(vertex group, kind, sorted dof indices) of every non-empty block, per
+    group in the order solid (kind 0, [d^s, p^s]), fluid-d (kind 1, [d^f]),
+    fluid-u (kind 2, [u^f, p^f])."""
     touch = vertex_elements(lev)
     blocks = []
-    for grp in vertex_groups(lev, b):
+    for g, grp in enumerate(vertex_groups(lev, b)):
         cand = []
         zs = grp[lev.ps_dof[grp] >= 0]
         els = touch[zs].ravel()
@@ -80,7 +82,7 @@ def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
         els = els[lev.material[els] == 1]
         if els.size:
             q2 = np.unique(lev.elem_q2[els])
-            cand.append(np.concatenate([lev.d_dof[q2].ravel(), lev.ps_dof[zs]]))
+            cand.append((0, np.concatenate([lev.d_dof[q2].ravel(), lev.ps_dof[zs]])))
         zf = grp[lev.pf_dof[grp] >= 0]
         els = touch[zf].ravel()
         els = np.unique(els[(els >= 0)])
@@ -88,14 +90,37 @@ def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
         if els.size:
             q2 = np.unique(lev.elem_q2[els])
             q2 = q2[~lev.q2_solid[q2]]
-            cand.append(lev.d_dof[q2].ravel())
-            cand.append(np.concatenate([lev.v_dof[q2].ravel(), lev.pf_dof[zf]]))
-        for idx in cand:
+            cand.append((1, lev.d_dof[q2].ravel()))
+            cand.append((2, np.concatenate([lev.v_dof[q2].ravel(), lev.pf_dof[zf]])))
+        for kind, idx in cand:
             idx = np.unique(idx)
             idx = idx[~lev.fixed[idx]]
             if idx.size:
-                blocks.append(idx)
+                blocks.append((g, kind, idx))
     return blocks
+
+
+def block_index_sets(lev: Level, b: int) -> list[np.ndarray]:
+    """Sorted dof index sets of all blocks: per vertex group solid, fluid-d, fluid-u."""
+    return [idx for _, _, idx in blocks_tagged(lev, b)]
+
+
+def colour_period(b: int) -> int:
+    """Colours per direction k of the vertex groups in a multiplicative sweep.
+    Group t spans the element closure [t b - 1, (t + 1) b] (in vertex units);
+    groups t and t + k leave a gap of (k - 1) b - 1 vertex spacings, and two
+    dofs are coupled only when they share an element (gap <= 1).  The
+    smallest k with (k - 1) b - 1 >= 2: 4 for b = 1, 3 for b = 2, else 2."""
+    return 4 if b == 1 else (3 if b == 2 else 2)
+
+
+def group_colours(lev: Level, b: int) -> np.ndarray:
+    """Colour of every vertex group: sum_a ((t_a mod k) k^a) over the group's
+    tile coordinates t_a (groups in the lex order of vertex_groups)."""
+    npd = -(-(lev.n + 1) // b)
+    k = colour_period(b)
+    t = lex(lev.dim, npd)
+    return sum((t[:, a] % k) * k ** a for a in range(lev.dim))
 
 
 def block_index_sets_monolithic(lev: Level, b: int) -> list[np.ndarray]:
@@ -126,11 +151,17 @@ class FSASM:
     the lumped K_u^s rows only in the field split."""
 
     def __init__(self, A: sp.csr_matrix, lev: Level, b: int, *, dtype=np.float64,
-                 weighted: bool = True, half: bool = False, monolithic: bool = False):
+                 weighted: bool = True, half: bool = False, monolithic: bool = False,
+                 multiplicative: bool = False):
         self.n = A.shape[0]
         self.dtype = np.float32 if half else dtype
         self.half = half
-        self.blocks = block_index_sets_monolithic(lev, b) if monolithic else block_index_sets(lev, b)
+        self.multiplicative = multiplicative and not monolithic
+        if monolithic:
+            self.blocks = block_index_sets_monolithic(lev, b)
+        else:
+            tagged = blocks_tagged(lev, b)
+            self.blocks = [idx for _, _, idx in tagged]
         mult = np.zeros(self.n)
         for idx in self.blocks:
             mult[idx] += 1.0
@@ -160,9 +191,87 @@ class FSASM:
                 self.lu.append(la.lu_factor(blk.astype(dtype), check_finite=True))
         self.jacobi = np.flatnonzero(lev.fixed if monolithic else (lev.group == G_US) | lev.fixed)
         self.inv_diag = 1.0 / Ad.diagonal()[self.jacobi]
+        if self.multiplicative:
+            self._setup_sweep(Ad, lev, b, tagged)
+
+    # ---------------------------------------------- locally multiplicative
+    # Sec. 3.2: the two field systems of P2 (block diagonal: displacement /
+    # solid pressure, velocity / fluid pressure) are solved separately, each
+    # by a locally multiplicative Schwarz sweep: block j is updated from the
+    # field residual of the most recent iterate, y <- y + R_j^T A_jj^{-1}
+    # R_j (r_F - A_FF y), blocks one after another (the paper's multiplicative
+    # update formula), starting from y = 0.  A_FF is A restricted to the
+    # field's rows and columns (P2 drops the couplings between the fields).
+    # In the velocity field the lumped K_u^s rows come first (one exact Jacobi
+    # step, Sec. 3.2), then the fluid blocks.  Fixed dofs take a Jacobi step.
+    # Block order: by pass (kind, colour) with kind 0 solid, 1 fluid-d, 2
+    # fluid-u and the colour of the block's vertex group, then by group.
+    def _setup_sweep(self, Ad, lev, b, tagged):
+        dt = self.dtype
+        col = group_colours(lev, b)
+        nc = colour_period(b) ** lev.dim
+        self.block_pass = np.array([kind * nc + col[g] for g, kind, _ in tagged], np.int64)
+        self.block_field = np.array([int(kind == 2) for _, kind, _ in tagged], np.int64)
+        self.order = np.argsort(self.block_pass, kind="stable")
+        dfield = np.isin(lev.group, (G_DS, G_DF, G_PS)) & ~lev.fixed
+        ufield = ~np.isin(lev.group, (G_DS, G_DF, G_PS)) & ~lev.fixed
+        C = Ad.tocoo()
+        self.AFF = []
+        for m in (dfield, ufield):
+            keep = m[C.row] & m[C.col]
+            self.AFF.append(sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=Ad.shape).astype(dt))
+        AFT = [M.T.tocsr() for M in self.AFF]
+        self.rows_f = [self.AFF[f][idx] for f, idx in zip(self.block_field, self.blocks)]
+        self.rows_t = [AFT[f][idx] for f, idx in zip(self.block_field, self.blocks)]
+        jac = np.zeros(self.n, bool)
+        jac[self.jacobi] = True
+        self.kdofs = np.flatnonzero((lev.group == G_US) & ~lev.fixed)
+        self.fdofs = np.flatnonzero(lev.fixed)
+        diag = Ad.diagonal()
+        self.k_inv = (1.0 / diag[self.kdofs]).astype(dt)
+        self.f_inv = (1.0 / diag[self.fdofs]).astype(dt)
+        self.k_rows = self.AFF[1][self.kdofs]
+        self.k_rows_t = AFT[1][self.kdofs]
+
+    def _solve(self, j, v, transpose=False):
+        lu = self.lu[j]
+        if self.half:
+            m16, scale = lu
+            if transpose:
+                return m16.astype(np.float32).T @ (scale * v)
+            return scale * (m16.astype(np.float32) @ v)
+        return la.lu_solve(lu, v, trans=1 if transpose else 0)
+
+    def sweep(self, r: np.ndarray, transpose: bool = False) -> np.ndarray:
+        """y = M r: one multiplicative sweep per field from y = 0; with
+        transpose, M^T r (the blocks in reverse order with A_jj^{-T} and the
+        residual of A_FF^T: the velocity field's K_u^s step comes last)."""
+        dt = self.dtype
+        r = r.astype(dt)
+        y = np.zeros(self.n, dt)
+        rows = self.rows_t if transpose else self.rows_f
+        order = self.order[::-1] if transpose else self.order
+        d_blocks = [j for j in order if self.block_field[j] == 0]
+        u_blocks = [j for j in order if self.block_field[j] == 1]
+        for j in d_blocks:
+            idx = self.blocks[j]
+            y[idx] += self._solve(j, r[idx] - rows[j] @ y, transpose).astype(dt)
+        if not transpose:
+            k = self.kdofs
+            y[k] += ((r[k] - self.k_rows @ y) * self.k_inv).astype(dt)
+        for j in u_blocks:
+            idx = self.blocks[j]
+            y[idx] += self._solve(j, r[idx] - rows[j] @ y, transpose).astype(dt)
+        if transpose:
+            k = self.kdofs
+            y[k] += ((r[k] - self.k_rows_t @ y) * self.k_inv).astype(dt)
+        y[self.fdofs] += (r[self.fdofs] * self.f_inv).astype(dt)
+        return y
 
     def apply(self, r: np.ndarray) -> np.ndarray:
-        """P2^{-1} r."""
+        """P2^{-1} r (additive), or the multiplicative sweep M r."""
+        if self.multiplicative:
+            return self.sweep(r)
         dt = self.dtype
         r = r.astype(dt)
         y = np.zeros(self.n, dt)
@@ -177,7 +286,10 @@ class FSASM:
         return y
 
     def apply_transpose(self, r: np.ndarray) -> np.ndarray:
-        """P2^{-T} r = sum_j R_j^T A_jj^{-T} W_j R_j r + D^{-1} r (adjoint smoother)."""
+        """P2^{-T} r = sum_j R_j^T A_jj^{-T} W_j R_j r + D^{-1} r (adjoint smoother),
+        or M^T r for the multiplicative sweep."""
+        if self.multiplicative:
+            return self.sweep(r, transpose=True)
         dt = self.dtype
         r = r.astype(dt)
         y = np.zeros(self.n, dt)

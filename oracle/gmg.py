@@ -2,7 +2,8 @@
 
 On every level l >= 1 the smoother is damped Richardson preconditioned by the
 field-split additive Schwarz method (monolithic=True: the paper's AS
-comparison method, blocks over all fields); level 0 is solved directly (Sec. 3.2,
+comparison method, blocks over all fields; on the mult_levels finest levels
+the locally multiplicative sweep of fsasm.FSASM.sweep); level 0 is solved directly (Sec. 3.2,
 "at the coarse level (l=0) a direct solver is employed").  Level operators
 are rediscretised on each level; transfers are P2 and R2 of Sec. 3.3.
 
@@ -31,7 +32,7 @@ from .transfer import prolongation, restriction
 class Hierarchy:
     def __init__(self, prob, *, mixed: bool = False, omega: float | None = None, nu_pre: int = 1,
                  nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
-                 weighted: bool = True, monolithic: bool = False):
+                 weighted: bool = True, monolithic: bool = False, mult_levels: int = 0):
         self.prob = prob
         self.mixed = bool(mixed)
         half = mixed == "half"
@@ -47,7 +48,8 @@ class Hierarchy:
                                        classical=classical_restriction) for l in range(1, nl)]
         b = prob.patch if patch is None else patch
         self.smoothers = [None] + [FSASM(self.A[l], self.levels[l], b, dtype=self.wdtype,
-                                         weighted=weighted, half=half, monolithic=monolithic)
+                                         weighted=weighted, half=half, monolithic=monolithic,
+                                         multiplicative=l >= nl - mult_levels)
                                    for l in range(1, nl)]
         self.coarse_lu = la.lu_factor(self.A[0].toarray())
         wd = self.wdtype
