@@ -96,6 +96,20 @@ typedef struct {
                                  *     the paper compares against: one block of all fields per
                                  *     pressure group.  Blocks of more than ~500 dofs (3D) are
                                  *     beyond the inversion kernels: FSI_ERR_ARG. */
+    int mult_levels;            /* locally multiplicative Schwarz (Sec. 3.2, multiplicative update
+                                 * formula; the paper's AS1/AS2 are multiplicative within a
+                                 * process) on the mult_levels finest levels, additive below;
+                                 * 0: additive everywhere; >= the number of smoothed levels: every
+                                 * level.  FS only (FSI_ERR_ARG with AS or a negative value).
+                                 * On such a level one smoothing step is x += omega M (b - A x)
+                                 * where M sweeps each field system of P2 separately from zero:
+                                 * block by block, each block correcting with the residual of
+                                 * its field operator A_FF at the latest iterate (velocity field:
+                                 * the K_u^s Jacobi rows first); blocks ordered by pass (solid,
+                                 * fluid-d, fluid-u kind, then the colour of the block's pressure
+                                 * group with period 4 / 3 / 2 per direction for b = 1 / 2 / >= 3),
+                                 * so blocks of one pass share no entry of A_FF and run at once.
+                                 * The transposed cycle sweeps in reverse with A_jj^{-T} and A_FF^T. */
 } fsi_smoother_opts;
 
 enum { FSI_SMOOTHER_FS = 0, FSI_SMOOTHER_AS = 1 };
@@ -211,7 +225,10 @@ fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_
 fsi_status fsi_apply_operator(fsi_ctx *ctx, int prob, int level, const double *x, double *y);
 
 
-/* y = P2^{-1} r on level l >= 1 (transpose != 0: P2^{-T} r), Sec. 3.2. */
+/* y = P2^{-1} r on level l >= 1 (transpose != 0: P2^{-T} r), Sec. 3.2.  On a
+ * level with the locally multiplicative sweep (fsi_smoother_opts.mult_levels)
+ * y = M r, the sweep of both field systems from zero (transpose: M^T r; the
+ * first transposed call builds the transposed operators). */
 fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
                               int transpose);
 
@@ -229,7 +246,10 @@ fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r
  * make that first call before any stream capture.  Every call reuses the
  * same array, so calls that may overlap on the GPU (different contexts,
  * streams or threads without ordering between them) race; calls issued on
- * one stream are ordered.  The paper has no counterpart to this entry point. */
+ * one stream are ordered.  On a multiplicative-sweep level the transposed
+ * sweep needs the transposed operators built beforehand (by fsi_adjoint or a
+ * transposed fsi_apply_smoother / fsi_apply_vcycle): FSI_ERR_STATE otherwise.
+ * The paper has no counterpart to this entry point. */
 #define FSI_NOALLOC_MAX_DOFS 2097152
 fsi_status fsi_apply_smoother_noalloc(fsi_ctx *ctx, int prob, int level, const double *r, double *y,
                                       int transpose);

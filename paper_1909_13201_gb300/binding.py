@@ -49,7 +49,8 @@ class HierOpts_t(C.Structure):
 
 class SmootherOpts_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("patch", C.c_int), ("omega", C.c_double),
-                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("factor", C.c_int), ("variant", C.c_int)]
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("factor", C.c_int), ("variant", C.c_int),
+                ("mult_levels", C.c_int)]
 
 
 class SolveOpts_t(C.Structure):
@@ -176,12 +177,14 @@ class FSISolver:
             pass
 
     def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=None, nu_pre=1, nu_post=1,
-                        factor=FSI_FACTOR_AUTO, variant=FSI_SMOOTHER_FS):
+                        factor=FSI_FACTOR_AUTO, variant=FSI_SMOOTHER_FS, mult_levels=0):
+        """mult_levels: finest levels smoothed by the locally multiplicative
+        sweep (0 = additive everywhere)."""
         if patch is None:
             patch = self.problems[0].patch
         if omega is None:
             omega = getattr(self.problems[0], "omega", 1.0)
-        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor, variant)
+        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor, variant, mult_levels)
         _check(load_library().fsi_setup_smoothers(self.ctx, C.byref(so)))
         self.precision = precision
 

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <numeric>
 #include <string>
 #include <type_traits>
 
@@ -186,9 +187,39 @@ void collect_marks(Context &cx) {
     cx.ev_marks.clear();
 }
 
+// Locally multiplicative smoothing step (Sec. 3.2, multiplicative update
+// formula, applied to each field system of P2): y = M r by the passes of the
+// level in order (transposed: in reverse, with A_jj^{-T} and A_FF^T), where
+// a pass corrects y on its blocks from r - A_FF y on its rows (the first pass
+// of a field starts from y = 0 and reads r itself); then x += omega y and y is
+// cleared for the next sweep.
+template <class T>
+fsi_status mult_smooth(Context &cx, LevelDev &L, const T *r, T *x, bool tr) {
+    cudaStream_t s = cx.stream;
+    if (tr && !L.mult_t_ready) {
+        set_error("transposed multiplicative sweep needs the transposed operators (fsi_adjoint builds them)");
+        return FSI_ERR_STATE;
+    }
+    T *y = L.y.as<T>(), *rr = L.rr.as<T>();
+    const int np = (int)L.passes.size();
+    bool started[2] = {false, false};
+    for (int q = 0; q < np; ++q) {
+        const SweepPass &P = L.passes[tr ? np - 1 - q : q];
+        const T *src = r;
+        if (started[P.field]) {
+            FSI_TRY(launch_ell_resid<T>(tr ? P.ell_t : P.ell, y, r, rr, s));
+            src = rr;
+        }
+        started[P.field] = true;
+        FSI_TRY(launch_block_apply<T>(L, src, y, (T)1, tr ? 1 : 0, s, P.it0, P.it1));
+    }
+    return launch_axpy_clear<T>(x, y, (T)cx.omega, L.n, s);
+}
+
 template <class T>
 fsi_status smooth_apply(Context &cx, LevelDev &L, const T *r, T *x, bool tr, bool fine = false) {
     ProfMark pm(cx, 0, fine);
+    if (L.mult) return mult_smooth<T>(cx, L, r, x, tr);
     return launch_block_apply<T>(L, r, x, (T)cx.omega, tr ? 1 : 0, cx.stream);
 }
 
@@ -643,6 +674,13 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
                 FSI_TRY(make_f32(L.RT, s));
             }
         }
+        if (L.mult) {
+            // A_FF^T on every pass's rows (the field masks are symmetric)
+            for (auto &P : L.passes)
+                FSI_TRY(build_ell_subset(L.AT, AT, P.rows, L.h_keep[P.field], L.keep[P.field].as<uint8_t>(), P.ell_t,
+                                         s, cx.probs.size() > 1));
+            L.mult_t_ready = true;
+        }
     }
     FSI_CUDA(cudaStreamSynchronize(s));
     pb.transposes_ready = true;
@@ -762,8 +800,33 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_TRY(D.x.alloc((size_t)D.n * tsz));
         FSI_TRY(D.r.alloc((size_t)D.n * tsz));
         if (l == 0) continue;
-        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx, cx.variant == FSI_SMOOTHER_AS);
+        // locally multiplicative sweep on the cx.mult_levels finest levels
+        const bool sweep = cx.variant == FSI_SMOOTHER_FS && cx.mult_levels > 0 &&
+                           (int64_t)l + cx.mult_levels >= (int64_t)pb.dev.size();
+        D.mult = sweep ? 1 : 0;
+        D.mult_t_ready = false;
+        D.passes.clear();
+        std::vector<int32_t> tags, bpass;
+        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx, cx.variant == FSI_SMOOTHER_AS, sweep ? &tags : nullptr);
         D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
+        if (sweep) {
+            // blocks in sweep order: by pass (kind, colour), stable inside a pass
+            sweep_passes(H, pb.patch, tags, bpass);
+            std::vector<int64_t> ord(D.n_blocks);
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t c) { return bpass[a] < bpass[c]; });
+            std::vector<int64_t> nptr(1, 0);
+            std::vector<int32_t> nidx, npass;
+            nidx.reserve(D.h_blk_idx.size());
+            for (int64_t j : ord) {
+                nidx.insert(nidx.end(), D.h_blk_idx.begin() + D.h_blk_ptr[j], D.h_blk_idx.begin() + D.h_blk_ptr[j + 1]);
+                nptr.push_back((int64_t)nidx.size());
+                npass.push_back(bpass[j]);
+            }
+            D.h_blk_ptr.swap(nptr);
+            D.h_blk_idx.swap(nidx);
+            bpass.swap(npass);
+        }
         std::vector<int32_t> bp(D.h_blk_ptr.begin(), D.h_blk_ptr.end());
         std::vector<int64_t> off(D.n_blocks + 1, 0);
         std::vector<double> mult(D.n, 0.0);
@@ -776,11 +839,12 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             for (int64_t k = D.h_blk_ptr[j]; k < D.h_blk_ptr[j + 1]; ++k) mult[D.h_blk_idx[k]] += 1.0;
         }
         D.inv_elems = off[D.n_blocks];
-        // partition-of-unity weights W_j = 1 / multiplicity
+        // partition-of-unity weights W_j = 1 / multiplicity (additive); the
+        // multiplicative update formula adds each block's correction whole
         std::vector<double> w64(D.h_blk_idx.size());
         std::vector<float> w32(D.h_blk_idx.size());
         for (size_t k = 0; k < D.h_blk_idx.size(); ++k) {
-            w64[k] = 1.0 / mult[D.h_blk_idx[k]];
+            w64[k] = sweep ? 1.0 : 1.0 / mult[D.h_blk_idx[k]];
             w32[k] = (float)w64[k];
         }
         FSI_TRY(upload(D.blk_ptr, bp.data(), bp.size() * 4, s));
@@ -812,7 +876,12 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             const int64_t want = 4 * (int64_t)cx.num_sms;
             const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
             std::vector<int32_t> it;
+            std::vector<int64_t> pass_b0, pass_i0;    // sweep: first block and first item of every pass
             for (int64_t j = 0; j < D.n_blocks; ++j) {
+                if (sweep && (j == 0 || bpass[j] != bpass[j - 1])) {
+                    pass_b0.push_back(j);
+                    pass_i0.push_back((int64_t)it.size() / 4);
+                }
                 const int nj = (int)(D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
                 int chunk = (int)((nj + split - 1) / split);
                 chunk = std::max(16, (chunk + 15) / 16 * 16);
@@ -823,6 +892,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                     it.push_back(0);
                 }
             }
+            const int64_t blk_items = (int64_t)it.size() / 4;
             // Jacobi rows ride in the same launch: items (-1, k0, k1) over the jac list
             for (int64_t k0 = 0; k0 < D.n_jac; k0 += 2048) {
                 it.push_back(-1);
@@ -832,6 +902,56 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             }
             D.n_items = (int64_t)it.size() / 4;
             FSI_TRY(upload(D.items, it.data(), it.size() * 4, s));
+            if (sweep) {
+                int nc = 1;
+                for (int a = 0; a < H.dim; ++a) nc *= colour_period(pb.patch);
+                const size_t np = pass_b0.size();
+                bool jac_placed = false;
+                auto add_jacobi = [&]() {
+                    if (jac_placed || D.n_jac == 0) return;
+                    SweepPass P;
+                    P.it0 = blk_items;
+                    P.it1 = D.n_items;
+                    P.field = 1;
+                    P.jacobi = true;
+                    P.rows = jac;
+                    D.passes.push_back(std::move(P));
+                    jac_placed = true;
+                };
+                for (size_t q = 0; q < np; ++q) {
+                    const int64_t b0 = pass_b0[q], b1 = q + 1 < np ? pass_b0[q + 1] : D.n_blocks;
+                    const int field = bpass[b0] / nc == 2 ? 1 : 0;
+                    if (field == 1) add_jacobi();      // velocity field: K_u^s rows first
+                    SweepPass P;
+                    P.it0 = pass_i0[q];
+                    P.it1 = q + 1 < np ? pass_i0[q + 1] : blk_items;
+                    P.field = field;
+                    P.rows.assign(D.h_blk_idx.begin() + D.h_blk_ptr[b0], D.h_blk_idx.begin() + D.h_blk_ptr[b1]);
+                    std::sort(P.rows.begin(), P.rows.end());
+                    D.passes.push_back(std::move(P));
+                }
+                add_jacobi();
+                // free dofs of each field system of P2: 0 = d and p^s, 1 = u and p^f
+                for (int f = 0; f < 2; ++f) {
+                    D.h_keep[f].assign(D.n, 0);
+                    for (int64_t i = 0; i < D.n; ++i)
+                        D.h_keep[f][i] = (!H.fixed[i] && ((i < H.off[3]) == (f == 0))) ? 1 : 0;
+                    FSI_TRY(upload(D.keep[f], D.h_keep[f].data(), (size_t)D.n, s));
+                }
+                for (auto &P : D.passes)
+                    FSI_TRY(build_ell_subset(D.A, H.pattern, P.rows, D.h_keep[P.field], D.keep[P.field].as<uint8_t>(),
+                                             P.ell, s, cx.probs.size() > 1));
+                FSI_TRY(D.y.alloc((size_t)D.n * tsz));
+                FSI_TRY(D.rr.alloc((size_t)D.n * tsz));
+                FSI_CUDA(cudaMemsetAsync(D.y.p, 0, (size_t)D.n * tsz, s));
+            } else {
+                for (int f = 0; f < 2; ++f) {
+                    D.h_keep[f].clear();
+                    D.keep[f].release();
+                }
+                D.y.release();
+                D.rr.release();
+            }
         }
         // staged-apply items (mixed modes): rows of one block whose stored
         // inverse fits one 64 KB shared-memory stage; enough items to give
@@ -1015,7 +1135,9 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     if (opts->precision < FSI_FP64 || opts->precision > FSI_MIXED_HALF || opts->patch < 1 || opts->patch > 16 ||
         !(opts->omega > 0) || opts->nu_pre < 1 || opts->nu_post < 1 || opts->nu_pre > 8 || opts->nu_post > 8 ||
         opts->factor < FSI_FACTOR_AUTO || opts->factor > FSI_FACTOR_TF32 ||
-        (opts->variant != FSI_SMOOTHER_FS && opts->variant != FSI_SMOOTHER_AS)) {
+        (opts->variant != FSI_SMOOTHER_FS && opts->variant != FSI_SMOOTHER_AS) ||
+        opts->mult_levels < 0 ||
+        (opts->mult_levels > 0 && opts->variant != FSI_SMOOTHER_FS)) {
         set_error("smoother options out of range");
         return FSI_ERR_ARG;
     }
@@ -1032,6 +1154,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     cx->nu_post = opts->nu_post;
     cx->factor = opts->factor;
     cx->variant = opts->variant;
+    cx->mult_levels = opts->mult_levels;
     cx->smoothers_ready = false;
     for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
     FSI_CUDA(cudaStreamSynchronize(cx->stream));
@@ -1729,6 +1852,7 @@ fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r
     if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
     DeviceGuard guard(cx->device);
     LevelDev &L = pb->dev[level];
+    if (transpose && L.mult) FSI_TRY(build_transposes(*cx, *pb));
     return cx->precision != FSI_FP64 ? apply_smoother_t<float>(*cx, L, r, y, transpose)
                                       : apply_smoother_t<double>(*cx, L, r, y, transpose);
 }

@@ -97,6 +97,18 @@ struct DevCSR {
     DevEll ell;
 };
 
+// One pass of the locally multiplicative sweep: apply work items [it0, it1)
+// of its level, field 0 (displacement, solid pressure) or 1 (velocity, fluid
+// pressure), the rows its blocks (or Jacobi rows) cover, and the binned-ELL
+// copies of A_FF (and A_FF^T) restricted to those rows.
+struct SweepPass {
+    int64_t it0 = 0, it1 = 0;
+    int field = 0;
+    bool jacobi = false;
+    std::vector<int32_t> rows;
+    DevEll ell, ell_t;
+};
+
 struct LevelDev {
     int64_t n = 0;
     DevCSR A, AT;         // operator and (adjoint) its transpose
@@ -122,6 +134,14 @@ struct LevelDev {
     DevBuf jac_idx, jac_inv;                    // int32, working precision 1/diag
     // V-cycle vectors in working precision
     DevBuf b, x, r;
+    // locally multiplicative sweep (mult != 0): blocks sorted by pass, one
+    // pass per (kind, colour) plus the Jacobi rows, in sweep order
+    int mult = 0;
+    bool mult_t_ready = false;
+    std::vector<SweepPass> passes;
+    DevBuf y, rr;                               // correction (zero between sweeps), pass residual
+    std::vector<uint8_t> h_keep[2];             // per dof: free dof of field 0 (d, p^s) / 1 (u, p^f)
+    DevBuf keep[2];
 };
 
 // Control block of a device-driven FGMRES solve (one per problem, device
@@ -210,6 +230,7 @@ struct Context {
     int nu_pre = 1, nu_post = 1;
     int factor = FSI_FACTOR_AUTO;    // block inversion method (resolved per precision)
     int variant = FSI_SMOOTHER_FS;   // field-split (FS) or monolithic (AS) Schwarz blocks
+    int mult_levels = 0;             // finest levels with the locally multiplicative sweep
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;
@@ -257,6 +278,13 @@ fsi_status launch_zero(T *v, int64_t n, cudaStream_t s);
 // the float32 copy of an existing ELL from A.val32.  concurrent: A belongs
 // to one problem of a batch (its launches share the GPU with the others').
 fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent);
+fsi_status build_ell_subset(const DevCSR &A, const HostCSR &pat, const std::vector<int32_t> &rows,
+                            const std::vector<uint8_t> &keep, const uint8_t *d_keep, DevEll &E,
+                            cudaStream_t s, bool concurrent);
+template <class T>
+fsi_status launch_ell_resid(const DevEll &E, const T *x, const T *b, T *y, cudaStream_t s);
+template <class T>
+fsi_status launch_axpy_clear(T *x, T *y, T a, int64_t n, cudaStream_t s);
 fsi_status ell_fill_f32(DevCSR &A, cudaStream_t s);
 
 // storage: 0 float64, 1 float32, 2 float16 with a float32 scale per row
@@ -264,7 +292,7 @@ fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int storage
                                cudaStream_t s, int num_sms);
 template <class T>
 fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, int transpose,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t it0 = 0, int64_t it1 = -1);
 template <class T>
 fsi_status launch_jacobi_apply(const LevelDev &lev, const T *r, T *x, T omega, cudaStream_t s);
 

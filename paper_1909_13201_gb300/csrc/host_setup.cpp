@@ -506,7 +506,7 @@ void build_restriction(const HostCSR &P, const LevelHost &fine, const LevelHost 
 }
 
 void build_blocks(const LevelHost &L, int b, std::vector<int64_t> &blk_ptr, std::vector<int32_t> &blk_idx,
-                  bool monolithic) {
+                  bool monolithic, std::vector<int32_t> *tags) {
     const int dim = L.dim;
     const int64_t n = L.n, m1 = n + 1;
     const int64_t ng = (m1 + b - 1) / b;
@@ -604,10 +604,37 @@ void build_blocks(const LevelHost &L, int b, std::vector<int64_t> &blk_ptr, std:
     }
     blk_ptr.assign(1, 0);
     blk_idx.clear();
-    for (auto &v : per) {
+    if (tags) tags->clear();
+    for (size_t q = 0; q < per.size(); ++q) {
+        const auto &v = per[q];
         if (v.empty()) continue;
         blk_idx.insert(blk_idx.end(), v.begin(), v.end());
         blk_ptr.push_back((int64_t)blk_idx.size());
+        if (tags) {
+            tags->push_back((int32_t)(q / 3));   // vertex group
+            tags->push_back((int32_t)(q % 3));   // kind: 0 solid, 1 fluid-d, 2 fluid-u
+        }
+    }
+}
+
+int colour_period(int b) { return b == 1 ? 4 : (b == 2 ? 3 : 2); }
+
+void sweep_passes(const LevelHost &L, int b, const std::vector<int32_t> &tags, std::vector<int32_t> &pass) {
+    const int dim = L.dim;
+    const int64_t ng = (L.n + 1 + b - 1) / b;
+    const int k = colour_period(b);
+    const int nc = (int)ipow(k, dim);
+    const size_t nb = tags.size() / 2;
+    pass.resize(nb);
+    for (size_t j = 0; j < nb; ++j) {
+        int64_t gc[3];
+        unflat(tags[2 * j], ng, dim, gc);
+        int colour = 0, kp = 1;
+        for (int a = 0; a < dim; ++a) {
+            colour += (int)(gc[a] % k) * kp;
+            kp *= k;
+        }
+        pass[j] = tags[2 * j + 1] * nc + colour;
     }
 }
 

@@ -58,8 +58,21 @@ void build_restriction(const HostCSR &P, const LevelHost &fine, const LevelHost 
 // Schwarz block index sets of a level (Vanka groups of b^dim pressure
 // vertices): field split (solid [d^s, p^s], fluid [d^f], fluid [u^f, p^f]
 // per group) or, monolithic, one block of all fields per group (AS).
+// tags (optional): per block its vertex group and kind (0 solid, 1 fluid-d,
+// 2 fluid-u).
 void build_blocks(const LevelHost &lev, int b, std::vector<int64_t> &blk_ptr,
-                  std::vector<int32_t> &blk_idx, bool monolithic = false);
+                  std::vector<int32_t> &blk_idx, bool monolithic = false,
+                  std::vector<int32_t> *tags = nullptr);
+
+// Locally multiplicative sweep (Sec. 3.2): the pass of every field-split
+// block, kind * k^dim + colour, where the colour of vertex group t is
+// sum_a (t_a mod k) k^a and k = colour_period(b) is the smallest period that
+// leaves two element layers between same-colour groups (4 for b = 1, 3 for
+// b = 2, else 2).  Blocks of one pass share no entry of their field's
+// operator, so a pass updates all its blocks at once and equals the paper's
+// one-block-after-another update in that order.
+int colour_period(int b);
+void sweep_passes(const LevelHost &lev, int b, const std::vector<int32_t> &tags, std::vector<int32_t> &pass);
 
 // Reference-cell tables of the 4-point Gauss rule: weights, Q2 values and
 // gradients, Q1 values; layout [q][a], [q][k][a], [q][al].

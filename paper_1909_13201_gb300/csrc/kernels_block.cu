@@ -918,13 +918,20 @@ fsi_status launch_block_invert(const DevCSR &A, const LevelDev &lev, int storage
 }
 
 template <class T>
-fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, int transpose, cudaStream_t s) {
-    if (lev.n_items == 0) return FSI_OK;
+fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, int transpose, cudaStream_t s,
+                              int64_t it0, int64_t it1) {
+    // items [it0, it1) (a pass of the multiplicative sweep), or all of them
+    const bool ranged = it1 >= 0;
+    if (!ranged) { it0 = 0; it1 = lev.n_items; }
+    if (it0 < 0 || it1 > lev.n_items || it0 > it1) { set_error("work-item range out of bounds"); return FSI_ERR_ARG; }
+    const int64_t n_it = it1 - it0;
+    if (n_it == 0) return FSI_OK;
+    const int4 *items = lev.items.as<int4>() + it0;
     if (lev.max_block > MAX_BLOCK) {
         set_error("Schwarz block larger than the apply kernel's staging buffer");
         return FSI_ERR_ARG;
     }
-    if (std::is_same<T, float>::value && !transpose && lev.n_titems > 0 && (lev.inv_store == 1 || lev.inv_store == 2)) {
+    if (std::is_same<T, float>::value && !transpose && !ranged && lev.n_titems > 0 && (lev.inv_store == 1 || lev.inv_store == 2)) {
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
         const int stages = lev.tma_stages, sbytes = lev.tma_stage_bytes;
@@ -962,23 +969,23 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
         if (transpose && lev.max_block <= 256)
-            FSI_CUDA(launch_pdl(block_apply_h_tr_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+            FSI_CUDA(launch_pdl(block_apply_h_tr_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+                items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega));
         else if (transpose)
-            FSI_CUDA(launch_pdl(block_apply_h_t_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+            FSI_CUDA(launch_pdl(block_apply_h_t_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+                items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega));
         else if (lev.max_block <= 256)
-            FSI_CUDA(launch_pdl(block_apply_h_pipe_kernel, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+            FSI_CUDA(launch_pdl(block_apply_h_pipe_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+                items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega));
         else
-            FSI_CUDA(launch_pdl(block_apply_h_kernel<4>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-                lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+            FSI_CUDA(launch_pdl(block_apply_h_kernel<4>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+                items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
                 lev.jac_inv.as<float>(), rf, xf, (float)omega));
         count_launch();
@@ -986,12 +993,12 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
         return FSI_OK;
     }
     if (transpose)
-        FSI_CUDA(launch_pdl(block_apply_t_kernel<T>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-            lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+        FSI_CUDA(launch_pdl(block_apply_t_kernel<T>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+            items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
             lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
     else
-        FSI_CUDA(launch_pdl(block_apply_kernel<T>, dim3((unsigned)lev.n_items), dim3(APPLY_THREADS), 0, s,
-            lev.items.as<int4>(), lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
+        FSI_CUDA(launch_pdl(block_apply_kernel<T>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
+            items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
             lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
     count_launch();
     FSI_CUDA(cudaGetLastError());
@@ -1062,8 +1069,10 @@ fsi_status launch_dense_gemv(const double *M, int64_t n, const T *x, T *y, int t
     return FSI_OK;
 }
 
-template fsi_status launch_block_apply<float>(const LevelDev &, const float *, float *, float, int, cudaStream_t);
-template fsi_status launch_block_apply<double>(const LevelDev &, const double *, double *, double, int, cudaStream_t);
+template fsi_status launch_block_apply<float>(const LevelDev &, const float *, float *, float, int, cudaStream_t,
+                                             int64_t, int64_t);
+template fsi_status launch_block_apply<double>(const LevelDev &, const double *, double *, double, int, cudaStream_t,
+                                             int64_t, int64_t);
 template fsi_status launch_jacobi_apply<float>(const LevelDev &, const float *, float *, float, cudaStream_t);
 template fsi_status launch_jacobi_apply<double>(const LevelDev &, const double *, double *, double, cudaStream_t);
 template fsi_status launch_dense_gemv<float>(const double *, int64_t, const float *, float *, int, cudaStream_t);

@@ -251,6 +251,40 @@ __global__ void ell_fill_kernel(int64_t n, const int32_t *__restrict__ ptr, cons
     }
 }
 
+// one thread per stored row of a row-subset copy: row rows[i] of the CSR,
+// entries whose column has keep[col] != 0, to positions base[i] + m stride[i]
+template <class T>
+__global__ void ell_fill_subset_kernel(int64_t nsub, const int32_t *__restrict__ rows,
+                                       const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                       const T *__restrict__ val, const uint8_t *__restrict__ keep,
+                                       const int64_t *__restrict__ base, const int32_t *__restrict__ rstride,
+                                       int32_t *__restrict__ ecol, T *__restrict__ eval) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsub; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = rows[i];
+        const int64_t b0 = base[i], st = rstride[i];
+        int64_t m = 0;
+        for (int k = ptr[r]; k < ptr[r + 1]; ++k) {
+            const int32_t c = col[k];
+            if (!keep[c]) continue;
+            const int64_t q = b0 + m * st;
+            if (ecol) ecol[q] = c;
+            eval[q] = val[k];
+            ++m;
+        }
+    }
+}
+
+// x += a y, then y = 0 (the multiplicative sweep's correction is consumed)
+template <class T>
+__global__ void axpy_clear_kernel(T *__restrict__ x, T *__restrict__ y, T a, int64_t n) {
+    pdl_trigger();
+    pdl_wait();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * y[i];
+        y[i] = T(0);
+    }
+}
+
 }  // namespace
 
 // Host: bins from the row lengths, then the fill kernel copies columns and
@@ -436,5 +470,133 @@ fsi_status launch_zero(T *v, int64_t n, cudaStream_t s) {
 }
 template fsi_status launch_zero<float>(float *, int64_t, cudaStream_t);
 template fsi_status launch_zero<double>(double *, int64_t, cudaStream_t);
+
+// Binned-ELL copy of a row subset of A restricted to the columns with
+// keep[c] != 0: the rows keep their indices in A (perm holds them), so a
+// product writes only those rows of its output.  Row lengths come from the
+// host copy `pat` of A's pattern; columns and values are copied on the device
+// from A's CSR.  Bins, lane count and streaming rule as in build_ell, taken
+// on the subset's size.
+fsi_status build_ell_subset(const DevCSR &A, const HostCSR &pat, const std::vector<int32_t> &rows,
+                            const std::vector<uint8_t> &keep, const uint8_t *d_keep, DevEll &E,
+                            cudaStream_t s, bool concurrent) {
+    E = DevEll();
+    const int64_t n = (int64_t)rows.size();
+    if (n == 0) return FSI_OK;
+    if ((int64_t)pat.ptr.size() != A.n_rows + 1 || (int64_t)keep.size() != A.n_cols) {
+        set_error("ELL subset: pattern or column mask does not match the operator");
+        return FSI_ERR_ARG;
+    }
+    std::vector<int32_t> len(n);
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t r = rows[i];
+        if (r < 0 || r >= A.n_rows) { set_error("ELL subset: row out of range"); return FSI_ERR_ARG; }
+        int c = 0;
+        for (int64_t k = pat.ptr[r]; k < pat.ptr[r + 1]; ++k) c += keep[pat.col[k]] ? 1 : 0;
+        len[i] = c;
+        nnz += c;
+    }
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return len[a] > len[b]; });
+    int G = 1;
+    if (!concurrent && n < 150000)
+        while (G < 16 && n * G < 300000) G *= 2;
+    if (G == 2) G = 4;
+    E.G = G;
+    E.stream = (double)nnz * 12.0 > 64e6;
+    std::vector<EllBin> bins;
+    std::vector<int64_t> base(n);
+    std::vector<int32_t> rstride(n), srows(n);
+    int64_t off = 0, slabs = 0;
+    for (int64_t i = 0; i < n;) {
+        const int l = len[order[i]];
+        int64_t j = i;
+        while (j < n && len[order[j]] == l) ++j;
+        EllBin B{};
+        B.off = off;
+        B.rows = (int32_t)(j - i);
+        B.len = l;
+        const int64_t rps = 32 / G;
+        B.stride = (int32_t)((B.rows + rps - 1) / rps * rps);
+        B.first = (int32_t)i;
+        B.slab0 = (int32_t)slabs;
+        for (int64_t t = i; t < j; ++t) {
+            base[t] = off + (t - i);
+            rstride[t] = B.stride;
+            srows[t] = rows[order[t]];
+        }
+        bins.push_back(B);
+        off += (int64_t)B.stride * l;
+        slabs += (int64_t)B.stride * G / 32;
+        i = j;
+    }
+    if (slabs > INT32_MAX) { set_error("ELL subset: too many slabs"); return FSI_ERR_ARG; }
+    E.nbins = (int)bins.size();
+    E.nslabs = slabs;
+    E.size = off;
+    FSI_TRY(E.bins.alloc(bins.size() * sizeof(EllBin)));
+    FSI_CUDA(cudaMemcpyAsync(E.bins.p, bins.data(), bins.size() * sizeof(EllBin), cudaMemcpyHostToDevice, s));
+    FSI_TRY(E.perm.alloc((size_t)n * 4));
+    FSI_CUDA(cudaMemcpyAsync(E.perm.p, srows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    DevBuf dbase, dstride;
+    FSI_TRY(dbase.alloc((size_t)n * 8));
+    FSI_TRY(dstride.alloc((size_t)n * 4));
+    FSI_CUDA(cudaMemcpyAsync(dbase.p, base.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    FSI_CUDA(cudaMemcpyAsync(dstride.p, rstride.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    FSI_TRY(E.col.alloc((size_t)E.size * 4));
+    FSI_CUDA(cudaMemsetAsync(E.col.p, 0, (size_t)E.size * 4, s));
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    int32_t *ecol = E.col.as<int32_t>();
+    if (A.val64.p) {
+        FSI_TRY(E.val64.alloc((size_t)E.size * 8));
+        FSI_CUDA(cudaMemsetAsync(E.val64.p, 0, (size_t)E.size * 8, s));
+        ell_fill_subset_kernel<double><<<(unsigned)g, 256, 0, s>>>(n, E.perm.as<int32_t>(), A.ptr.as<int32_t>(),
+                                                                   A.col.as<int32_t>(), A.val64.as<double>(), d_keep,
+                                                                   dbase.as<int64_t>(), dstride.as<int32_t>(), ecol,
+                                                                   E.val64.as<double>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+        ecol = nullptr;
+    }
+    if (A.val32.p) {
+        FSI_TRY(E.val32.alloc((size_t)E.size * 4));
+        FSI_CUDA(cudaMemsetAsync(E.val32.p, 0, (size_t)E.size * 4, s));
+        ell_fill_subset_kernel<float><<<(unsigned)g, 256, 0, s>>>(n, E.perm.as<int32_t>(), A.ptr.as<int32_t>(),
+                                                                  A.col.as<int32_t>(), A.val32.as<float>(), d_keep,
+                                                                  dbase.as<int64_t>(), dstride.as<int32_t>(), ecol,
+                                                                  E.val32.as<float>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+
+// y[i] = b[i] - (E x)[i] on the rows of the subset copy E
+template <class T>
+fsi_status launch_ell_resid(const DevEll &E, const T *x, const T *b, T *y, cudaStream_t s) {
+    if (E.nslabs == 0) return FSI_OK;
+    const T *val = std::is_same<T, float>::value ? static_cast<const T *>(E.val32.p) : static_cast<const T *>(E.val64.p);
+    if (!val) { set_error("ELL subset has no values in this precision"); return FSI_ERR_STATE; }
+    return run_ell<T, T, T>(E, val, x, b, y, SPMV_RESID, s, (T *)nullptr);
+}
+template fsi_status launch_ell_resid<float>(const DevEll &, const float *, const float *, float *, cudaStream_t);
+template fsi_status launch_ell_resid<double>(const DevEll &, const double *, const double *, double *, cudaStream_t);
+
+template <class T>
+fsi_status launch_axpy_clear(T *x, T *y, T a, int64_t n, cudaStream_t s) {
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) return FSI_OK;
+    FSI_CUDA(launch_pdl(axpy_clear_kernel<T>, dim3((unsigned)g), dim3(256), 0, s, x, y, a, n));
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+template fsi_status launch_axpy_clear<float>(float *, float *, float, int64_t, cudaStream_t);
+template fsi_status launch_axpy_clear<double>(double *, double *, double, int64_t, cudaStream_t);
 
 }  // namespace fsi
