@@ -216,6 +216,16 @@ fsi_status fsi_get_transfer(const fsi_ctx *ctx, int prob, int level, int which, 
  * (n_blocks+1), idx (blk_ptr[n_blocks]).  idx NULL: blk_ptr only. */
 fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_ptr, int32_t *idx);
 
+/* Field-split blocks of level l >= 1: pass[j] (n_blocks entries, host) is the
+ * pass of block j in the locally multiplicative sweep (Sec. 3.2), kind * k^dim
+ * + colour with kind 0 solid [d^s, p^s], 1 fluid [d^f], 2 fluid [u^f, p^f],
+ * colour = sum_a (t_a mod k) k^a over the tile coordinates t_a of the block's
+ * pressure group and k = 4 / 3 / 2 for b = 1 / 2 / >= 3 (see mult_levels).
+ * Blocks are in the order fsi_get_blocks returns (sorted by pass on levels
+ * with the multiplicative sweep).  FSI_ERR_STATE for monolithic (AS) blocks
+ * or before the blocks exist.  Works on host-only contexts. */
+fsi_status fsi_get_block_passes(const fsi_ctx *ctx, int prob, int level, int32_t *pass);
+
 /* ------------------- single-operation entry points ------------------------
  * Device-vector calls of one piece of the path, in the level's working
  * precision converted from/to float64 at the boundary; used to check each
@@ -286,7 +296,8 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
 /* Host-only inspection context: builds the levels, numbering, operator
  * sparsity patterns, transfers and (for patch >= 1) the Schwarz block index
  * sets on the host without touching a GPU, so that fsi_get_sizes,
- * fsi_get_dof_map, fsi_get_pattern, fsi_get_transfer and fsi_get_blocks can
+ * fsi_get_dof_map, fsi_get_pattern, fsi_get_transfer, fsi_get_blocks and
+ * fsi_get_block_passes can
  * be called on machines without CUDA devices.  Every other call on such a
  * context returns FSI_ERR_STATE.  Release with fsi_destroy. */
 fsi_status fsi_setup_host_only(const fsi_problem *prob, const fsi_hier_opts *opts, int patch,

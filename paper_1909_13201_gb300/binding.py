@@ -26,7 +26,7 @@ EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solv
             "fsi_adjoint", "fsi_get_sizes", "fsi_get_dof_map", "fsi_get_matrix", "fsi_get_transfer",
             "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
             "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_apply_smoother_noalloc",
-            "fsi_autotune", "fsi_destroy", "fsi_last_error"]
+            "fsi_autotune", "fsi_get_block_passes", "fsi_destroy", "fsi_last_error"]
 
 
 class FSIError(RuntimeError):
@@ -97,6 +97,7 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     lib.fsi_get_matrix.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32), C.POINTER(D)]
     lib.fsi_get_transfer.argtypes = [P, I, I, I, C.POINTER(I64), C.POINTER(I32), C.POINTER(D)]
     lib.fsi_get_blocks.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
+    lib.fsi_get_block_passes.argtypes = [P, I, I, C.POINTER(I32)]
     lib.fsi_apply_operator.argtypes = [P, I, I, P, P]
     lib.fsi_apply_smoother.argtypes = [P, I, I, P, P, I]
     lib.fsi_apply_vcycle.argtypes = [P, I, P, P, I]
@@ -322,6 +323,13 @@ class FSISolver:
         idx = np.zeros(int(ptr[-1]), np.int32)
         _check(lib.fsi_get_blocks(self.ctx, prob, level, _ptr(ptr, C.c_int64), _ptr(idx, C.c_int32)))
         return ptr, idx
+
+    def block_passes(self, level, prob=0):
+        """Sweep pass (kind * k^dim + colour) of every field-split block, in block order."""
+        nb = self.sizes(level, prob)["n_blocks"]
+        out = np.zeros(nb, np.int32)
+        _check(load_library().fsi_get_block_passes(self.ctx, prob, level, _ptr(out, C.c_int32)))
+        return out
 
     def apply_operator(self, level, x, prob=0):
         import torch

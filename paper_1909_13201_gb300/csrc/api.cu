@@ -723,7 +723,9 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
             pb.dev[l].A.nnz = pb.host[l].pattern.nnz();
             if (l >= 1 && cx.patch >= 1) {
                 LevelDev &D = pb.dev[l];
-                build_blocks(pb.host[l], cx.patch, D.h_blk_ptr, D.h_blk_idx);
+                std::vector<int32_t> tags;
+                build_blocks(pb.host[l], cx.patch, D.h_blk_ptr, D.h_blk_idx, false, &tags);
+                sweep_passes(pb.host[l], cx.patch, tags, D.h_pass);
                 D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
                 D.max_block = 0;
                 for (int64_t j = 0; j < D.n_blocks; ++j)
@@ -807,11 +809,12 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         D.mult_t_ready = false;
         D.passes.clear();
         std::vector<int32_t> tags, bpass;
-        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx, cx.variant == FSI_SMOOTHER_AS, sweep ? &tags : nullptr);
+        const bool fs = cx.variant == FSI_SMOOTHER_FS;
+        build_blocks(H, pb.patch, D.h_blk_ptr, D.h_blk_idx, !fs, fs ? &tags : nullptr);
         D.n_blocks = (int64_t)D.h_blk_ptr.size() - 1;
+        if (fs) sweep_passes(H, pb.patch, tags, bpass);
         if (sweep) {
             // blocks in sweep order: by pass (kind, colour), stable inside a pass
-            sweep_passes(H, pb.patch, tags, bpass);
             std::vector<int64_t> ord(D.n_blocks);
             std::iota(ord.begin(), ord.end(), 0);
             std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t c) { return bpass[a] < bpass[c]; });
@@ -827,6 +830,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             D.h_blk_idx.swap(nidx);
             bpass.swap(npass);
         }
+        D.h_pass = bpass;                     // empty for AS blocks
         std::vector<int32_t> bp(D.h_blk_ptr.begin(), D.h_blk_ptr.end());
         std::vector<int64_t> off(D.n_blocks + 1, 0);
         std::vector<double> mult(D.n, 0.0);
@@ -1759,6 +1763,16 @@ fsi_status fsi_get_blocks(const fsi_ctx *ctx, int prob, int level, int64_t *blk_
     if (D.h_blk_ptr.empty()) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
     std::memcpy(blk_ptr, D.h_blk_ptr.data(), D.h_blk_ptr.size() * 8);
     if (idx) std::memcpy(idx, D.h_blk_idx.data(), D.h_blk_idx.size() * 4);
+    return FSI_OK;
+}
+
+fsi_status fsi_get_block_passes(const fsi_ctx *ctx, int prob, int level, int32_t *pass) {
+    Problem *pb = get_prob(ctx, prob, level);
+    if (!pb || level < 1 || !pass) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    const LevelDev &D = pb->dev[level];
+    if (D.h_blk_ptr.empty()) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    if (D.h_pass.size() + 1 != D.h_blk_ptr.size()) { set_error("monolithic (AS) blocks have no sweep passes"); return FSI_ERR_STATE; }
+    std::memcpy(pass, D.h_pass.data(), D.h_pass.size() * 4);
     return FSI_OK;
 }
 

@@ -119,6 +119,7 @@ struct LevelDev {
     int64_t n_blocks = 0, max_block = 0, inv_elems = 0;
     std::vector<int64_t> h_blk_ptr;
     std::vector<int32_t> h_blk_idx;
+    std::vector<int32_t> h_pass;                // field split: sweep pass of every block (block order)
     DevBuf blk_ptr, blk_idx, blk_off, blk_w;   // int32, int32, int64, working-precision weights
     DevBuf inv;                                 // block inverses, row-major, padded rows
     DevBuf inv_scale;                           // float16 storage: float32 scale per block row

@@ -549,6 +549,11 @@ def test_mult_sweep_and_transpose_fp64(mult_case):
     for l in range(1, len(H.A)):
         r = rng.standard_normal(H.A[l].shape[0])
         S = H.smoothers[l]
+        # the library stores the blocks in the oracle's sweep order, with its passes
+        ptr, idx = s.blocks(l)
+        for jj, j in enumerate(S.order):
+            np.testing.assert_array_equal(idx[ptr[jj]:ptr[jj + 1]], S.blocks[j])
+        np.testing.assert_array_equal(s.block_passes(l), S.block_pass[S.order])
         for tr in (False, True):
             y = s.apply_smoother(l, _cuda(r), transpose=tr).cpu().numpy()
             ref = S.apply_transpose(r) if tr else S.apply(r)
