@@ -632,3 +632,27 @@ def test_mult_rejected_with_monolithic_blocks():
     with pytest.raises(binding.FSIError) as err:
         s.setup_smoothers(precision=binding.FSI_FP64, mult_levels=-1)
     assert err.value.status == binding.FSI_ERR_ARG
+
+
+def test_mult_3d_sweep_and_solve():
+    """3D valve box, b = 2: 27 colours x 3 kinds (72 non-empty passes) of
+    376-dof blocks; the fine-level sweep equals the oracle's to 1e-9 (FP64),
+    the solve reaches the direct solution, iterations +-1 of the oracle's."""
+    p = I.make_valve_3d(8, 2, 2, 4243)
+    H = gmg.Hierarchy(p, mult_levels=1)
+    s = binding.FSISolver(p)
+    s.setup_smoothers(precision=binding.FSI_FP64, mult_levels=1)
+    l = len(H.A) - 1
+    S = H.smoothers[l]
+    np.testing.assert_array_equal(s.block_passes(l), S.block_pass[S.order])
+    r = np.random.default_rng(71).standard_normal(H.A[l].shape[0])
+    y = s.apply_smoother(l, _cuda(r)).cpu().numpy()
+    ref = S.apply(r)
+    assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(ref)
+    b = _rhs(p, H, 72)
+    xd = _direct(H.fine, b)
+    x, st = s.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-9 * np.linalg.norm(xd)
+    _, st8 = s.solve(_cuda(b), rtol=1e-8)
+    _, ost = ofg.solve(H, b, rtol=1e-8)
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
