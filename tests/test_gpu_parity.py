@@ -635,10 +635,12 @@ def test_mult_rejected_with_monolithic_blocks():
 
 
 def test_mult_3d_sweep_and_solve():
-    """3D valve box, b = 2: 27 colours x 3 kinds (72 non-empty passes) of
-    376-dof blocks; the fine-level sweep equals the oracle's to 1e-9 (FP64),
-    the solve reaches the direct solution, iterations +-1 of the oracle's."""
-    p = I.make_valve_3d(8, 2, 2, 4243)
+    """3D valve box, b = 1 (the 3D workload's group size; b = 2 blocks of ~1000
+    dofs exceed the inversion kernels): 64 colours x 3 kinds = 192 passes of
+    blocks up to 376 dofs; the fine-level sweep equals the oracle's to 1e-9
+    (FP64), the solve reaches the direct solution, iterations +-1 of the
+    oracle's."""
+    p = I.make_valve_3d(8, 2, 1, 4243)
     H = gmg.Hierarchy(p, mult_levels=1)
     s = binding.FSISolver(p)
     s.setup_smoothers(precision=binding.FSI_FP64, mult_levels=1)
