@@ -12,6 +12,8 @@ smoothing, Arnoldi, refinement): every step of the solve path.  Set-up
              inverses, float64 Krylov), device-resident right-hand side, CUDA
              events on the solver's stream;
   mixed_f32_inverses  the same with float32 block inverses;
+  multiplicative_fine  the same with the locally multiplicative Schwarz
+             sweep per field system on the finest level (additive below);
   fp64       the all-float64 path on the same system (mixed/fp64 speed-up);
   e2e        mixed precision through the public call with host buffers
              (pinned H2D of b, solve, D2H of x inside the timed region);
