@@ -290,7 +290,11 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * ms, [24] their float64 FMAs in total, [25] first Gram-Schmidt passes timed,
  * [26] their ms, [27] their bytes in total, [28..31] reserved.  The
  * Gram-Schmidt passes are timed in host-driven solves only (solves run
- * host-driven while recording).  Problem 0. */
+ * host-driven while recording).  On a fine level with the multiplicative
+ * sweep (mult_levels) a timed "smoother launch" is the whole sweep (its pass
+ * residuals and applies), while [2] still counts only the inverse, index and
+ * vector bytes of all blocks: [2] / ([1] / [0]) then understates the
+ * bandwidth of the apply kernels.  Problem 0. */
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
 
 /* Host-only inspection context: builds the levels, numbering, operator
