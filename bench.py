@@ -217,20 +217,31 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def device_code_sha(path):
+    """sha256[:16] of a CUDA source's device code: its text before the first
+    host function definition (a line starting with "fsi_status ")."""
+    text = []
+    for line in open(path, encoding="utf-8"):
+        if line.startswith("fsi_status "):
+            break
+        text.append(line)
+    return hashlib.sha256("".join(text).encode()).hexdigest()[:16]
+
+
 def ncu_traffic():
     """Per-launch DRAM bytes of the fine smoother apply from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the kernels' device code is unchanged."""
     path = os.path.join(ROOT, "profiles", "block_apply_h_c1_mixed_half.md")
     src = os.path.join(ROOT, "paper_1909_13201_gb300", "csrc", "kernels_block.cu")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = device_code_sha(src)
     vals = {}
     for line in open(path):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             vals[k.strip()] = v.strip().split()[0]
-    if vals.get("kernels_block.cu sha256[:16]") != sha:
+    if vals.get("kernels_block.cu device code sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram bytes per launch"])
