@@ -30,6 +30,11 @@ partition-of-unity weights W_j = diag(1/multiplicity):
     P2^{-1} r = sum_j R_j^T W_j A_jj^{-1} R_j r  +  D^{-1} r |_{u^s and fixed dofs},
     x <- x + omega P2^{-1} (b - A x)        (damped Richardson, Sec. 3.2).
 
+With multiplicative=True the blocks are combined instead by the paper's
+locally multiplicative update (Sec. 3.2, multiplicative update formula), per
+field system of P2: FSASM.sweep corrects one block after another from the
+residual of the field operator at the latest iterate (see _setup_sweep).
+
 The oracle factors each block with partial-pivoting LU (scipy/LAPACK getrf).
 Storage emulations of the mixed modes: ``dtype=float32`` factors and solves
 in float32; ``half=True`` forms the float64 inverse from the LU factors,
