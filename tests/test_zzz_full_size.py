@@ -1,0 +1,123 @@
+"""Parity at the benchmark's full size: the 256x256 channel workload (7 levels,
+1.12 M unknowns) in the configuration bench.py times, against the FP64 oracle
+on outputs it can compute piece by piece and on properties that hold at any
+size.
+
+- the float64 outer product w = A x (binned-ELL kernel of the Arnoldi step) on
+  sampled rows against the oracle's assembled fine operator;
+- the fine-level FS-ASM apply with FP16 row-scaled inverses (the streaming
+  kernel the roofline reports; float64 factors here so that the stored
+  values equal the oracle's emulation) on the rows of sampled blocks, the
+  reference formed from every block that overlaps them, one block at a time;
+  the lumped K_u^s Jacobi rows on a sample;
+- the solves bench.py times (FP16 inverses from tensor-core factors, additive
+  smoother and the multiplicative sweep on the finest level): converged, with
+  the float64 true residual measured by the oracle's operator <= 1e-8 ||b||.
+
+Collected after every other test file: it builds the largest hierarchy of
+the suite.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+torch = pytest.importorskip("torch")
+
+from oracle import fsasm, mesh
+from oracle.assemble import assemble
+from oracle.transfer import G_US
+from paper_1909_13201_gb300 import binding
+from paper_1909_13201_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-8
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def sampled_half_apply(A, lev, b, r, sample, blocks=None):
+    """Rows S of the FP16-storage FS-ASM apply y = sum_j R_j^T W_j M_j R_j r
+    (M_j: float64 inverse, row-scaled, rounded to float16, applied in float32
+    times the float32 row scale; W_j = 1 / multiplicity), where S is the union
+    of the blocks `sample`: every block that meets S contributes, one by one."""
+    if blocks is None:
+        blocks = fsasm.block_index_sets(lev, b)
+    n = A.shape[0]
+    mult = np.zeros(n)
+    for idx in blocks:
+        mult[idx] += 1.0
+    w = np.where(mult > 0, 1.0 / np.maximum(mult, 1.0), 0.0).astype(np.float32)
+    S = np.unique(np.concatenate([blocks[j] for j in sample]))
+    in_s = np.zeros(n, bool)
+    in_s[S] = True
+    r32 = r.astype(np.float32)
+    y = np.zeros(n, np.float32)
+    Ac = A.tocsr()
+    for idx in blocks:
+        if not in_s[idx].any():
+            continue
+        blk = Ac[idx][:, idx].toarray()
+        inv = la.lu_solve(la.lu_factor(blk), np.eye(idx.size))
+        scale = np.abs(inv).max(1)
+        scale[scale == 0] = 1.0
+        m16 = (inv / scale[:, None]).astype(np.float16)
+        y[idx] += w[idx] * (scale.astype(np.float32) * (m16.astype(np.float32) @ r32[idx]))
+    return S, y[S].astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def full():
+    p = I.make_config(1)
+    lev = mesh.build_levels(p)[-1]
+    A = assemble(p, lev)
+    s = binding.FSISolver(p)
+    f, c, nd = s.dof_map(p.n_levels - 1)
+    np.testing.assert_array_equal(f, lev.dof_field)
+    np.testing.assert_array_equal(nd, lev.dof_node)
+    b = I.gather_natural(I.natural_vector(p, 1), lev.dof_field, lev.dof_comp, lev.dof_node)
+    return p, lev, A, s, b
+
+
+def test_full_size_outer_product_sampled_rows(full):
+    p, lev, A, s, b = full
+    rng = np.random.default_rng(81)
+    x = rng.standard_normal(A.shape[0])
+    y = s.apply_operator(p.n_levels - 1, _cuda(x)).cpu().numpy()
+    rows = rng.choice(A.shape[0], 20000, replace=False)
+    Ar = A.tocsr()[rows]
+    ref = Ar @ x
+    bound = 1e-12 * (abs(Ar) @ np.abs(x))
+    assert np.all(np.abs(y[rows] - ref) <= bound + 1e-300)
+
+
+def test_full_size_fp16_smoother_sampled_blocks(full):
+    p, lev, A, s, b = full
+    s.setup_smoothers(precision=binding.FSI_MIXED_HALF, factor=binding.FSI_FACTOR_FP64)
+    l = p.n_levels - 1
+    rng = np.random.default_rng(82)
+    r = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    y = s.apply_smoother(l, _cuda(r)).cpu().numpy()
+    blocks = fsasm.block_index_sets(lev, p.patch)
+    ptr, _ = s.blocks(l)
+    assert len(ptr) - 1 == len(blocks)
+    sample = rng.choice(len(blocks), 24, replace=False)
+    S, ref = sampled_half_apply(A, lev, p.patch, r, sample, blocks)
+    assert np.linalg.norm(y[S] - ref) <= 2e-5 * np.linalg.norm(ref)
+    # lumped K_u^s rows: one exact Jacobi step in float32
+    k = np.flatnonzero((lev.group == G_US) & ~lev.fixed)
+    k = rng.choice(k, min(2000, k.size), replace=False)
+    ref_k = r[k].astype(np.float32) * (1.0 / A.diagonal()[k]).astype(np.float32)
+    np.testing.assert_allclose(y[k], ref_k, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("mult_levels", [0, 1])
+def test_full_size_solve_true_residual(full, mult_levels):
+    p, lev, A, s, b = full
+    s.setup_smoothers(precision=binding.FSI_MIXED_HALF, mult_levels=mult_levels)
+    x, st = s.solve(_cuda(b), rtol=RTOL)
+    assert st["converged"] and st["rel_residual"] <= RTOL
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xr) <= 1.05 * RTOL * np.linalg.norm(b), (mult_levels, st)
