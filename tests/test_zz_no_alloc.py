@@ -3,8 +3,9 @@ allocate GPU memory at call time (allocator-restricted or real-time code).
 
 It must give the same y = P2^{-1} r as fsi_apply_smoother, which allocates its
 working vectors per call, and keep doing so on consecutive calls that reuse
-the library's static device array.  Collected last so that a run stopping at
-the first failure has already run every other test.
+the library's static device array.  Collected after the parity tests so that a
+run stopping at the first failure has already run them (only the full-size
+tests follow).
 """
 import numpy as np
 import pytest
