@@ -251,9 +251,10 @@ fsi_status fsi_apply_smoother(fsi_ctx *ctx, int prob, int level, const double *r
  * device array of the library holding at most FSI_NOALLOC_MAX_DOFS entries
  * per vector (2 x 2^21 float64 = 32 MiB, reserved on every GPU that loads the
  * library until the process exits).  Levels with more dofs are rejected with
- * FSI_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.  Every call reuses the
+ * FSI_ERR_ARG.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, with the context's device current); the first call
+ * on a device may load the library's device code, so make it before any
+ * stream capture.  Every call reuses the
  * same array, so calls that may overlap on the GPU (different contexts,
  * streams or threads without ordering between them) race; calls issued on
  * one stream are ordered.  On a multiplicative-sweep level the transposed

@@ -623,15 +623,6 @@ fsi_status run_batch(Context &cx, std::vector<Run> &runs) {
         for (auto &R : runs) cudaStreamSynchronize(R.pb->stream);
         collect_marks(cx);
     }
-    if (err == FSI_OK) {
-        int word = 0;
-        FSI_CUDA(cudaMemcpyAsync(&word, cx.flags.as<int>() + 2, 4, cudaMemcpyDeviceToHost, user));
-        FSI_CUDA(cudaStreamSynchronize(user));
-        if (word) {
-            set_error("a staged block copy did not complete in time (kernel error word " + std::to_string(word) + ")");
-            err = FSI_ERR_CUDA;
-        }
-    }
     return err;
 }
 
@@ -856,6 +847,44 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         FSI_TRY(upload(D.blk_off, off.data(), off.size() * 8, s));
         if (mixed) FSI_TRY(upload(D.blk_w, w32.data(), w32.size() * 4, s));
         else FSI_TRY(upload(D.blk_w, w64.data(), w64.size() * 8, s));
+        // owners of the overlapping blocks (additive levels): the slots of every
+        // covered dof in block order, for the owner-computes combination
+        D.n_own = 0;
+        if (!sweep) {
+            const int64_t nnzb = (int64_t)D.h_blk_idx.size();
+            std::vector<int32_t> ptr(D.n + 1, 0), pos(nnzb);
+            for (int32_t i : D.h_blk_idx) ptr[i + 1]++;
+            for (int64_t i = 0; i < D.n; ++i) ptr[i + 1] += ptr[i];
+            std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+            for (int64_t k = 0; k < nnzb; ++k) pos[fill[D.h_blk_idx[k]]++] = (int32_t)k;
+            std::vector<int32_t> odof, optr;
+            std::vector<double> ow64;
+            std::vector<float> ow32;
+            for (int64_t i = 0; i < D.n; ++i) {
+                if (ptr[i + 1] == ptr[i]) continue;
+                odof.push_back((int32_t)i);
+                optr.push_back(ptr[i]);
+                ow64.push_back(1.0 / mult[i]);
+                ow32.push_back((float)(1.0 / mult[i]));
+            }
+            optr.push_back((int32_t)nnzb);
+            D.n_own = (int64_t)odof.size();
+            if (D.n_own > 0) {
+                FSI_TRY(upload(D.own_dof, odof.data(), odof.size() * 4, s));
+                FSI_TRY(upload(D.own_ptr, optr.data(), optr.size() * 4, s));
+                FSI_TRY(upload(D.own_pos, pos.data(), pos.size() * 4, s));
+                if (mixed) FSI_TRY(upload(D.own_w, ow32.data(), ow32.size() * 4, s));
+                else FSI_TRY(upload(D.own_w, ow64.data(), ow64.size() * 8, s));
+                FSI_TRY(D.stage.alloc((size_t)nnzb * tsz));
+            }
+        }
+        if (D.n_own == 0) {
+            D.own_dof.release();
+            D.own_ptr.release();
+            D.own_pos.release();
+            D.own_w.release();
+            D.stage.release();
+        }
         FSI_TRY(D.inv.alloc((size_t)D.inv_elems * isz));
         D.inv_store = store;
         if (store == 2) FSI_TRY(D.inv_scale.alloc(D.h_blk_idx.size() * 4));
@@ -957,45 +986,6 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                 D.rr.release();
             }
         }
-        // staged-apply items (mixed modes): rows of one block whose stored
-        // inverse fits one 64 KB shared-memory stage; enough items to give
-        // every SM several
-        D.n_titems = 0;
-        // staged apply configuration: FSI_TMA="stages,stage_kb,ctas_per_sm" (0 disables)
-        // (measured slower than the register-streaming apply on GB300: opt-in only)
-        int tma_on = 0, t_st = 3, t_kb = 32, t_cps = 2;
-        if (const char *e = getenv("FSI_TMA")) {
-            if (e[0] != '0') {
-                tma_on = 1;
-                sscanf(e, "%d,%d,%d", &t_st, &t_kb, &t_cps);
-            }
-        }
-        if (store != 0 && tma_on) {
-            D.tma_stages = t_st;
-            D.tma_stage_bytes = t_kb * 1024;
-            const int64_t stage_bytes = D.tma_stage_bytes;
-            const int64_t want = 4 * (int64_t)cx.num_sms;
-            const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
-            std::vector<int32_t> it;
-            for (int64_t j = 0; j < D.n_blocks; ++j) {
-                const int nj = (int)(D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
-                const int64_t row_bytes = (int64_t)((nj + VW - 1) / VW * VW) * (int64_t)isz;
-                int chunk = (int)std::min<int64_t>(nj, stage_bytes / row_bytes);
-                chunk = std::min(chunk, (int)((nj + split - 1) / split));
-                chunk = std::max(4, (chunk + 3) / 4 * 4);
-                chunk = (int)std::min<int64_t>(chunk, stage_bytes / row_bytes);
-                for (int r0 = 0; r0 < nj; r0 += chunk) {
-                    it.push_back((int32_t)j);
-                    it.push_back(r0);
-                    it.push_back(std::min(nj, r0 + chunk));
-                    it.push_back(0);
-                }
-            }
-            D.n_titems = (int64_t)it.size() / 4;
-            FSI_TRY(upload(D.titems, it.data(), it.size() * 4, s));
-            D.tma_grid = (int64_t)cx.num_sms * t_cps;
-        }
-        D.err = cx.flags.as<int>() + 2;
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
         int method = cx.factor;
         if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
@@ -1006,9 +996,14 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             else
                 FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
         }
-        int flag = 0;
-        FSI_TRY(read_flag(cx, &flag));
-        if (flag) {
+        int fw[3] = {0, 0, 0};
+        FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
+        FSI_CUDA(cudaStreamSynchronize(s));
+        if (fw[2]) {   // a bounded tensor-core wait of the factorisation gave up
+            set_error("block factorisation on level " + std::to_string(l) + " timed out waiting for the tensor cores");
+            return FSI_ERR_CUDA;
+        }
+        if (fw[0]) {
             set_error("a Schwarz block on level " + std::to_string(l) + " is singular");
             return FSI_ERR_ZERO_PIVOT;
         }
@@ -1453,15 +1448,6 @@ fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
         FSI_CUDA(cudaEventRecord(cx.ev_out, R.pb->stream));
         FSI_CUDA(cudaStreamWaitEvent(user, cx.ev_out, 0));
     }
-    if (err == FSI_OK) {
-        int word = 0;
-        FSI_CUDA(cudaMemcpyAsync(&word, cx.flags.as<int>() + 2, 4, cudaMemcpyDeviceToHost, user));
-        FSI_CUDA(cudaStreamSynchronize(user));
-        if (word) {
-            set_error("a staged block copy did not complete in time (kernel error word " + std::to_string(word) + ")");
-            err = FSI_ERR_CUDA;
-        }
-    }
     return err;
 }
 
@@ -1797,22 +1783,14 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * (size_t)FSI_NOALLO
 
 namespace fsi {
 namespace {
-// device address of g_noalloc_scratch per device, looked up on first use
-// with that device current (the host-side symbol is not a device address)
-constexpr int kMaxDevices = 64;
-double *g_noalloc_addr[kMaxDevices] = {nullptr};
-
-fsi_status noalloc_scratch(int device, double **out) {
-    if (device < 0 || device >= kMaxDevices) {
-        set_error("device index out of range for the no-alloc scratch table");
-        return FSI_ERR_ARG;
-    }
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        FSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[device] = static_cast<double *>(p);
-    }
-    *out = g_noalloc_addr[device];
+// device address of g_noalloc_scratch on the current device.  Looked up on
+// every call (the host-side symbol is not a device address): the lookup
+// allocates nothing, and a per-process cache would go stale if the device's
+// primary context were reset and recreated.
+fsi_status noalloc_scratch(double **out) {
+    void *p = nullptr;
+    FSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<double *>(p);
     return FSI_OK;
 }
 
@@ -1854,7 +1832,7 @@ fsi_status fsi_apply_smoother_noalloc(fsi_ctx *ctx, int prob, int level, const d
     }
     DeviceGuard guard(cx->device);
     double *scratch = nullptr;
-    FSI_TRY(noalloc_scratch(cx->device, &scratch));
+    FSI_TRY(noalloc_scratch(&scratch));
     return cx->precision != FSI_FP64 ? apply_smoother_noalloc_t<float>(*cx, L, r, y, transpose, scratch)
                                       : apply_smoother_noalloc_t<double>(*cx, L, r, y, transpose, scratch);
 }

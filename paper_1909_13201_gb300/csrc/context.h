@@ -126,11 +126,11 @@ struct LevelDev {
     int inv_store = 0;                          // 0 float64, 1 float32, 2 float16 + row scale
     int64_t n_items = 0;
     DevBuf items;                               // int4 (block, row begin, row end, 0) apply work items
-    int64_t n_titems = 0;                       // staged (TMA) apply: block items of <= 64 KB each
-    DevBuf titems;
-    int64_t tma_grid = 0;                       // persistent CTAs
-    int tma_stages = 3, tma_stage_bytes = 64 * 1024;
-    int *err = nullptr;                         // context error word (bit 2: staged-copy wait timed out)
+    // owner-computes combination of overlapping blocks (additive levels):
+    // stage has one slot per entry of blk_idx; owner d = own_dof[d] sums its
+    // slots own_pos[own_ptr[d] .. own_ptr[d+1]) (block order) times own_w[d]
+    int64_t n_own = 0;
+    DevBuf stage, own_dof, own_ptr, own_pos, own_w;
     int64_t n_jac = 0;
     DevBuf jac_idx, jac_inv;                    // int32, working precision 1/diag
     // V-cycle vectors in working precision

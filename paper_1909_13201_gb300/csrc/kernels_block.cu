@@ -14,8 +14,13 @@
 //
 // Apply (the per-iteration hot loop): y = A_jj^{-1} r_j is a dense GEMV that
 // streams each stored inverse once from HBM with 16-byte vector loads; the
-// weighted result W_j y is scatter-added into x (atomics: blocks overlap).
-// Jacobi rows (u^s and fixed dofs) are a separate elementwise kernel.
+// blocks overlap, so each block row's result goes to its own slot of a
+// staging vector (one slot per entry of the block index lists), and a second
+// kernel combines them owner by owner: dof i adds W_i times its slots in
+// block order, the additive formula's sum over j in a fixed order, so the
+// smoother is bitwise repeatable.  Passes of the multiplicative sweep hold
+// non-overlapping blocks and add into the correction directly.  Jacobi rows
+// (u^s and fixed dofs) ride in the apply launch as their own work items.
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_kernel(const int4 *
                                                                     const int32_t *__restrict__ jac_idx,
                                                                     const T *__restrict__ jac_inv,
                                                                     const T *__restrict__ r, T *__restrict__ x,
-                                                                    T omega) {
+                                                                    T omega, T *__restrict__ stage) {
     using V = typename Vec<T>::type;
     constexpr int VW = Vec<T>::w;
     __shared__ __align__(16) T rs[MAX_BLOCK];
@@ -243,7 +248,11 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_kernel(const int4 *
         }
         const T v = warp_reduce4<T>(a, lane);
         const int q = lane >> 3;
-        if ((lane & 7) == 0 && i + q < r1) atomicAdd(&x[blk_idx[s0 + i + q]], omega * blk_w[s0 + i + q] * v);
+        if ((lane & 7) == 0 && i + q < r1) {
+            const int g = s0 + i + q;
+            if (stage) stage[g] = v;
+            else atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * v);
+        }
     }
 }
 
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_t_kernel(const int4
                                                                       const int32_t *__restrict__ jac_idx,
                                                                       const T *__restrict__ jac_inv,
                                                                       const T *__restrict__ r, T *__restrict__ x,
-                                                                      T omega) {
+                                                                      T omega, T *__restrict__ stage) {
     constexpr int VW = Vec<T>::w;
     __shared__ T rs[MAX_BLOCK];
     pdl_trigger();
@@ -282,7 +291,8 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_t_kernel(const int4
     for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
         T acc = 0;
         for (int i = 0; i < n; ++i) acc += M[(size_t)i * ld + j] * rs[i];
-        atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
+        if (stage) stage[s0 + j] = acc;
+        else atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
     }
 }
 
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4
                                                                       const int32_t *__restrict__ jac_idx,
                                                                       const float *__restrict__ jac_inv,
                                                                       const float *__restrict__ r, float *__restrict__ x,
-                                                                      float omega) {
+                                                                      float omega, float *__restrict__ stage) {
     __shared__ __align__(16) float rs[MAX_BLOCK];
     pdl_trigger();
     const int4 it = items[blockIdx.x];
@@ -347,7 +357,8 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_kernel(const int4
         const int q = lane >> 3;
         if ((lane & 7) == 0 && i + q < r1) {
             const int g = s0 + i + q;
-            atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
+            if (stage) stage[g] = scale[g] * v;
+            else atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
         }
     }
 }
@@ -367,7 +378,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, 12) block_apply_h_pipe_kernel(c
                                                                            const int32_t *__restrict__ jac_idx,
                                                                            const float *__restrict__ jac_inv,
                                                                            const float *__restrict__ r,
-                                                                           float *__restrict__ x, float omega) {
+                                                                           float *__restrict__ x, float omega,
+                                                                           float *__restrict__ stage) {
     __shared__ __align__(16) float rs[256];
     pdl_trigger();
     const int4 it = items[blockIdx.x];
@@ -412,7 +424,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, 12) block_apply_h_pipe_kernel(c
         const int q = lane >> 3;
         if ((lane & 7) == 0 && i + q < r1) {
             const int g = s0 + i + q;
-            atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
+            if (stage) stage[g] = scale[g] * v;
+            else atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * scale[g] * v);
         }
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) m[qq] = mn[qq];
@@ -437,7 +450,8 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_tr_kernel(const i
                                                                          const int32_t *__restrict__ jac_idx,
                                                                          const float *__restrict__ jac_inv,
                                                                          const float *__restrict__ r,
-                                                                         float *__restrict__ x, float omega) {
+                                                                         float *__restrict__ x, float omega,
+                                                                         float *__restrict__ stage) {
     constexpr int NW = APPLY_THREADS / 32;
     __shared__ float rs[256];
     __shared__ float part[NW][256];
@@ -492,7 +506,8 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_tr_kernel(const i
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < NW; ++w) sum += part[w][c];
-        atomicAdd(&x[blk_idx[s0 + c0 + c]], omega * sum);
+        if (stage) stage[s0 + c0 + c] = sum;
+        else atomicAdd(&x[blk_idx[s0 + c0 + c]], omega * sum);
     }
 }
 
@@ -506,7 +521,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const in
                                                                         const int32_t *__restrict__ jac_idx,
                                                                         const float *__restrict__ jac_inv,
                                                                         const float *__restrict__ r, float *__restrict__ x,
-                                                                        float omega) {
+                                                                        float omega, float *__restrict__ stage) {
     __shared__ float rs[MAX_BLOCK];
     pdl_trigger();
     const int4 it = items[blockIdx.x];
@@ -528,218 +543,32 @@ __global__ void __launch_bounds__(APPLY_THREADS) block_apply_h_t_kernel(const in
     for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
         float acc = 0.0f;
         for (int i = 0; i < n; ++i) acc += __half2float(M[(size_t)i * ld + j]) * rs[i];
-        atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
+        if (stage) stage[s0 + j] = acc;
+        else atomicAdd(&x[blk_idx[s0 + j]], omega * acc);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Persistent apply with TMA bulk staging (mixed modes, float32 vectors).
-// One CTA per SM walks the work items item = blockIdx.x + k gridDim.x.  The
-// rows of each item's inverse are contiguous in HBM (n_rows x ld entries,
-// rows padded to 16 bytes), so one cp.async.bulk copy moves them into a
-// TMA_STAGES-deep shared-memory ring, completing on an mbarrier; while item k
-// is computed from shared memory the copies of items k+1 .. k+STAGES-1 are in
-// flight, and the residual entries of item k+1 are gathered into registers.
-// Every mbarrier wait is bounded: on time-out the kernel sets bit 2 of *err,
-// waits (bounded) for its own copies still in flight and returns.
-constexpr int TMA_THREADS = 256;
-constexpr uint32_t TMA_SPIN_LIMIT = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TMA_SPIN_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-template <class S> struct StoreT;
-template <> struct StoreT<__half> { static constexpr int esize = 2, per16 = 8; };
-template <> struct StoreT<float> { static constexpr int esize = 4, per16 = 4; };
-
-// dot of one 16-byte chunk of a stored row with 16 bytes' worth of rs
-__device__ __forceinline__ float chunk_dot(const uint4 &m, const float *rs, const __half *) {
-    const float4 a = reinterpret_cast<const float4 *>(rs)[0], b = reinterpret_cast<const float4 *>(rs)[1];
-    return dot8(m, a, b);
-}
-__device__ __forceinline__ float chunk_dot(const uint4 &m, const float *rs, const float *) {
-    const float4 a = reinterpret_cast<const float4 *>(rs)[0];
-    const float4 mm = *reinterpret_cast<const float4 *>(&m);
-    return mm.x * a.x + mm.y * a.y + mm.z * a.z + mm.w * a.w;
-}
-
-struct TmaItemInfo {
-    int blk, r0, r1, s0, n, ld;
-    const char *src;
-    uint32_t bytes;
-};
-
-template <class S>
-__device__ __forceinline__ TmaItemInfo tma_item(const int4 *items, int it, const int32_t *blk_ptr,
-                                                const int64_t *blk_off, const S *inv) {
-    TmaItemInfo t;
-    const int4 v = items[it];
-    t.blk = v.x;
-    t.r0 = v.y;
-    t.r1 = v.z;
-    t.s0 = blk_ptr[t.blk];
-    t.n = blk_ptr[t.blk + 1] - t.s0;
-    t.ld = (t.n + StoreT<S>::per16 - 1) / StoreT<S>::per16 * StoreT<S>::per16;
-    t.src = reinterpret_cast<const char *>(inv + blk_off[t.blk]) + (size_t)t.r0 * t.ld * StoreT<S>::esize;
-    t.bytes = (uint32_t)((size_t)(t.r1 - t.r0) * t.ld * StoreT<S>::esize);
-    return t;
-}
-
-template <class S, int TMA_STAGES>
-__global__ void __launch_bounds__(TMA_THREADS) block_apply_tma_kernel(
-    int TMA_STAGE_BYTES, const int4 *__restrict__ items, int n_items, const int32_t *__restrict__ blk_ptr,
-    const int32_t *__restrict__ blk_idx, const int64_t *__restrict__ blk_off, const float *__restrict__ blk_w,
-    const S *__restrict__ inv, const float *__restrict__ scale, const int32_t *__restrict__ jac_idx,
-    const float *__restrict__ jac_inv, int n_jac, const float *__restrict__ r, float *__restrict__ x, float omega,
-    int *err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *stage = smem;                                            // [STAGES][STAGE_BYTES]
-    float *rsbuf = reinterpret_cast<float *>(smem + TMA_STAGES * TMA_STAGE_BYTES);   // [2][MAX_BLOCK]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(rsbuf + 2 * MAX_BLOCK);    // [STAGES]
-    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    constexpr int NW = TMA_THREADS / 32;
-    constexpr int PER16 = StoreT<S>::per16;
-    if (tid == 0) {
-        for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bar[q], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // prologue: the first STAGES items of this CTA
-    if (tid == 0) {
-        for (int q = 0; q < TMA_STAGES; ++q) {
-            const int it = blockIdx.x + q * gridDim.x;
-            if (it >= n_items) break;
-            const TmaItemInfo t = tma_item<S>(items, it, blk_ptr, blk_off, inv);
-            mbar_expect_tx(&bar[q], t.bytes);
-            tma_load(stage + (size_t)q * TMA_STAGE_BYTES, t.src, t.bytes, &bar[q]);
-        }
-    }
-    // residual entries of the first item into registers
-    constexpr int GATHER = MAX_BLOCK / TMA_THREADS;
-    float gv[GATHER];
-    int cur = blockIdx.x;
-    if (cur < n_items) {
-        const TmaItemInfo t = tma_item<S>(items, cur, blk_ptr, blk_off, inv);
-#pragma unroll
-        for (int q = 0; q < GATHER; ++q) {
-            const int i = tid + q * TMA_THREADS;
-            gv[q] = i < t.n ? r[blk_idx[t.s0 + i]] : 0.0f;
-        }
-    }
-    bool ok = true;
-    int k = 0;
-    for (; cur < n_items; cur += gridDim.x, ++k) {
-        const int sidx = k % TMA_STAGES;
-        const uint32_t parity = (uint32_t)((k / TMA_STAGES) & 1);
-        const TmaItemInfo t = tma_item<S>(items, cur, blk_ptr, blk_off, inv);
-        float *rs = rsbuf + (k & 1) * MAX_BLOCK;
-#pragma unroll
-        for (int q = 0; q < GATHER; ++q) {
-            const int i = tid + q * TMA_THREADS;
-            if (i < t.ld) rs[i] = gv[q];
-        }
-        // prefetch the next item's residual entries while this one is computed
-        const int nxt = cur + gridDim.x;
-        if (nxt < n_items) {
-            const TmaItemInfo tn = tma_item<S>(items, nxt, blk_ptr, blk_off, inv);
-#pragma unroll
-            for (int q = 0; q < GATHER; ++q) {
-                const int i = tid + q * TMA_THREADS;
-                gv[q] = i < tn.n ? r[blk_idx[tn.s0 + i]] : 0.0f;
-            }
-        }
-        // every thread waits (bounded) for stage sidx; the time-out decision is
-        // made CTA-uniform by the barrier reduction, so no thread is left
-        // waiting at a barrier another thread skipped
-        const int landed = mbar_wait(&bar[sidx], parity) ? 1 : 0;
-        if (!__syncthreads_and(landed)) {       // also orders the rs writes
-            ok = false;
-            break;
-        }
-        const uint4 *M = reinterpret_cast<const uint4 *>(stage + (size_t)sidx * TMA_STAGE_BYTES);
-        const int nv = t.ld / PER16;            // 16-byte chunks per row
-        const int rows = t.r1 - t.r0;
-        for (int i = warp * RPW; i < rows; i += NW * RPW) {
-            float a[RPW];
-#pragma unroll
-            for (int q = 0; q < RPW; ++q) a[q] = 0.0f;
-            for (int c = lane; c < nv; c += 32) {
-                const float *rc = rs + c * PER16;
-#pragma unroll
-                for (int q = 0; q < RPW; ++q)
-                    if (i + q < rows) a[q] += chunk_dot(M[(size_t)(i + q) * nv + c], rc, (const S *)nullptr);
-            }
-#pragma unroll
-            for (int q = 0; q < RPW; ++q)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
-            if (lane < RPW && i + lane < rows) {
-                float v = a[0];
-#pragma unroll
-                for (int q = 1; q < RPW; ++q)
-                    if (lane == q) v = a[q];
-                const int g = t.s0 + t.r0 + i + lane;
-                const float sc = scale ? scale[g] : 1.0f;
-                atomicAdd(&x[blk_idx[g]], omega * blk_w[g] * sc * v);
-            }
-        }
-        __syncthreads();                        // every warp is done with stage sidx
-        if (tid == 0) {
-            const int refill = cur + TMA_STAGES * gridDim.x;
-            if (refill < n_items) {
-                const TmaItemInfo tr = tma_item<S>(items, refill, blk_ptr, blk_off, inv);
-                mbar_expect_tx(&bar[sidx], tr.bytes);
-                tma_load(stage + (size_t)sidx * TMA_STAGE_BYTES, tr.src, tr.bytes, &bar[sidx]);
-            }
-        }
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(err, 2);
-        // drain: wait (bounded) for the copies this CTA issued and has not consumed
-        for (int q = 0; q < TMA_STAGES; ++q) {
-            const int kk = k + q;
-            const int it = blockIdx.x + kk * gridDim.x;
-            if (it >= n_items) break;
-            mbar_wait(&bar[kk % TMA_STAGES], (uint32_t)((kk / TMA_STAGES) & 1));
-        }
-        return;
-    }
-    // Jacobi rows (u^s and fixed dofs): grid-stride over the list
-    for (int q = blockIdx.x * TMA_THREADS + tid; q < n_jac; q += gridDim.x * TMA_THREADS) {
-        const int i = jac_idx[q];
-        x[i] += omega * r[i] * jac_inv[q];
-    }
+// Owner-computes combination of the staged block results (additive Schwarz,
+// Sec. 3.2): owner d (a dof covered by at least one block) sums
+// w_d * stage[k] over its slots k in block order and adds omega times the sum
+// to x.  Forward apply: w_d = 1 / multiplicity (the weights W_j); transposed
+// apply: the weights were applied to r before the block products, w = 1.
+template <class T>
+__global__ void __launch_bounds__(256) block_gather_kernel(const int32_t *__restrict__ own_dof,
+                                                         const int32_t *__restrict__ own_ptr,
+                                                         const int32_t *__restrict__ own_pos,
+                                                         const T *__restrict__ own_w, int64_t m,
+                                                         const T *__restrict__ stage, T *__restrict__ x,
+                                                         T omega, int weighted) {
+    pdl_trigger();
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= m) { pdl_wait(); return; }
+    const int k0 = own_ptr[d], k1 = own_ptr[d + 1], i = own_dof[d];
+    const T w = weighted ? own_w[d] : T(1);
+    pdl_wait();
+    T acc = 0;
+    for (int k = k0; k < k1; ++k) acc += w * stage[own_pos[k]];
+    x[i] += omega * acc;
 }
 
 template <class T>
@@ -931,77 +760,53 @@ fsi_status launch_block_apply(const LevelDev &lev, const T *r, T *x, T omega, in
         set_error("Schwarz block larger than the apply kernel's staging buffer");
         return FSI_ERR_ARG;
     }
-    if (std::is_same<T, float>::value && !transpose && !ranged && lev.n_titems > 0 && (lev.inv_store == 1 || lev.inv_store == 2)) {
-        const float *rf = reinterpret_cast<const float *>(r);
-        float *xf = reinterpret_cast<float *>(x);
-        const int stages = lev.tma_stages, sbytes = lev.tma_stage_bytes;
-        const size_t smem = (size_t)stages * sbytes + 2 * MAX_BLOCK * sizeof(float) + stages * sizeof(uint64_t);
-        const unsigned grid = (unsigned)std::min<int64_t>(lev.n_titems, lev.tma_grid);
-#define FSI_TMA_LAUNCH(ST, NS, INVP, SCALE)                                                                     \
-    do {                                                                                                        \
-        FSI_CUDA(cudaFuncSetAttribute(block_apply_tma_kernel<ST, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                      (int)smem));                                                              \
-        block_apply_tma_kernel<ST, NS><<<grid, TMA_THREADS, smem, s>>>(                                         \
-            sbytes, lev.titems.as<int4>(), (int)lev.n_titems, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), \
-            lev.blk_off.as<int64_t>(), lev.blk_w.as<float>(), INVP, SCALE, lev.jac_idx.as<int32_t>(),           \
-            lev.jac_inv.as<float>(), (int)lev.n_jac, rf, xf, (float)omega, lev.err);                            \
-    } while (0)
-#define FSI_TMA_STAGES_SWITCH(ST, INVP, SCALE)        \
-    switch (stages) {                                 \
-        case 2: FSI_TMA_LAUNCH(ST, 2, INVP, SCALE); break; \
-        case 3: FSI_TMA_LAUNCH(ST, 3, INVP, SCALE); break; \
-        case 4: FSI_TMA_LAUNCH(ST, 4, INVP, SCALE); break; \
-        case 6: FSI_TMA_LAUNCH(ST, 6, INVP, SCALE); break; \
-        default: FSI_TMA_LAUNCH(ST, 8, INVP, SCALE); break; \
-    }
-        if (lev.inv_store == 2) {
-            FSI_TMA_STAGES_SWITCH(__half, lev.inv.as<__half>(), lev.inv_scale.as<float>());
-        } else {
-            FSI_TMA_STAGES_SWITCH(float, lev.inv.as<float>(), (const float *)nullptr);
-        }
-#undef FSI_TMA_STAGES_SWITCH
-#undef FSI_TMA_LAUNCH
-        count_launch();
-        FSI_CUDA(cudaGetLastError());
-        return FSI_OK;
-    }
+    // overlapping blocks (a whole additive level): per-slot results, then the
+    // owner-computes combination; a pass of the multiplicative sweep holds
+    // disjoint blocks and adds into x directly
+    T *stage = (!ranged && lev.n_own > 0) ? lev.stage.as<T>() : nullptr;
     if (std::is_same<T, float>::value && lev.inv_store == 2) {
         const float *rf = reinterpret_cast<const float *>(r);
         float *xf = reinterpret_cast<float *>(x);
+        float *sf = reinterpret_cast<float *>(stage);
         if (transpose && lev.max_block <= 256)
             FSI_CUDA(launch_pdl(block_apply_h_tr_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
                 items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega));
+                lev.jac_inv.as<float>(), rf, xf, (float)omega, sf));
         else if (transpose)
             FSI_CUDA(launch_pdl(block_apply_h_t_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
                 items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega));
+                lev.jac_inv.as<float>(), rf, xf, (float)omega, sf));
         else if (lev.max_block <= 256)
             FSI_CUDA(launch_pdl(block_apply_h_pipe_kernel, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
                 items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega));
+                lev.jac_inv.as<float>(), rf, xf, (float)omega, sf));
         else
             FSI_CUDA(launch_pdl(block_apply_h_kernel<4>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
                 items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
                 lev.blk_w.as<float>(), lev.inv.as<__half>(), lev.inv_scale.as<float>(), lev.jac_idx.as<int32_t>(),
-                lev.jac_inv.as<float>(), rf, xf, (float)omega));
-        count_launch();
-        FSI_CUDA(cudaGetLastError());
-        return FSI_OK;
-    }
-    if (transpose)
+                lev.jac_inv.as<float>(), rf, xf, (float)omega, sf));
+    } else if (transpose) {
         FSI_CUDA(launch_pdl(block_apply_t_kernel<T>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
             items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
-            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
-    else
+            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega, stage));
+    } else {
         FSI_CUDA(launch_pdl(block_apply_kernel<T>, dim3((unsigned)n_it), dim3(APPLY_THREADS), 0, s,
             items, lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), lev.blk_off.as<int64_t>(),
-            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega));
+            lev.blk_w.as<T>(), lev.inv.as<T>(), lev.jac_idx.as<int32_t>(), lev.jac_inv.as<T>(), r, x, omega, stage));
+    }
     count_launch();
     FSI_CUDA(cudaGetLastError());
+    if (stage) {
+        const unsigned g = (unsigned)((lev.n_own + 255) / 256);
+        FSI_CUDA(launch_pdl(block_gather_kernel<T>, dim3(g), dim3(256), 0, s, lev.own_dof.as<int32_t>(),
+                            lev.own_ptr.as<int32_t>(), lev.own_pos.as<int32_t>(), lev.own_w.as<T>(), lev.n_own,
+                            (const T *)stage, x, omega, transpose ? 0 : 1));
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
     return FSI_OK;
 }
 

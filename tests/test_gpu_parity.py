@@ -144,7 +144,7 @@ def test_mixed_precision_solve(case, prec):
     Hm = gmg.Hierarchy(p, mixed=True if prec == binding.FSI_MIXED else "half")
     _, ost = ofg.solve(Hm, b, rtol=1e-8)
     _, st8 = sm.solve(_cuda(b), rtol=1e-8)
-    assert abs(st8["iterations"] - ost["iterations"]) <= 2, (st8["iterations"], ost["iterations"])
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
 
 
 def test_adjoint_and_gradients(case):
@@ -340,13 +340,11 @@ def test_device_loop_matches_host_loop(monkeypatch):
         for rep in range(2):
             xd, std = sd.solve(_cuda(b), rtol=rtol, restart=12)
             xh, sth = sh.solve(_cuda(b), rtol=rtol, restart=12)
-            # atomics in the smoother's scatter-add make both loops vary by
-            # rounding, so counts near the residual floor may differ by one
-            assert abs(std["iterations"] - sth["iterations"]) <= 1
-            assert std["cycles"] >= 1
-            # the smoother's overlapping scatter-add uses atomics, so two runs
-            # of either loop differ by rounding; the iterates agree to far
-            # below the requested residual
+            # the preconditioner is bitwise repeatable, so both loops take the
+            # same path; they differ only in the float64 rounding of the small
+            # least-squares update (device kernel vs host loop)
+            assert std["iterations"] == sth["iterations"]
+            assert std["cycles"] == sth["cycles"] and std["cycles"] >= 1
             xd, xh = xd.cpu().numpy(), xh.cpu().numpy()
             assert np.linalg.norm(xd - xh) <= 1e-2 * rtol * np.linalg.norm(xh)
             assert std["converged"] and sth["converged"]
@@ -354,14 +352,41 @@ def test_device_loop_matches_host_loop(monkeypatch):
     x0 = _cuda(0.5 * _direct(H.fine, b))
     xd, std = sd.solve(_cuda(b), x0=x0.clone(), rtol=1e-10)
     xh, sth = sh.solve(_cuda(b), x0=x0.clone(), rtol=1e-10)
-    assert abs(std["iterations"] - sth["iterations"]) <= 1
+    assert std["iterations"] == sth["iterations"]
     assert np.linalg.norm(xd.cpu().numpy() - xh.cpu().numpy()) <= 1e-12 * np.linalg.norm(xh.cpu().numpy())
     w = _rhs(p, H, 78)
     x, _ = sd.solve(_cuda(b), rtol=1e-10)
     ad = sd.adjoint(_cuda(w), x, rtol=1e-10)
     ah = sh.adjoint(_cuda(w), x, rtol=1e-10)
-    assert abs(ad[3]["iterations"] - ah[3]["iterations"]) <= 1
+    assert ad[3]["iterations"] == ah[3]["iterations"]
     assert np.linalg.norm(ad[0].cpu().numpy() - ah[0].cpu().numpy()) <= 1e-12 * np.linalg.norm(ah[0].cpu().numpy())
+
+
+@pytest.mark.parametrize("variant", ["fs", "as"])
+@pytest.mark.parametrize("prec", [binding.FSI_FP64, binding.FSI_MIXED, binding.FSI_MIXED_HALF])
+def test_repeatable_smoother_and_solve(prec, variant):
+    """Overlapping Schwarz blocks are combined owner by owner in block order
+    (no float atomics), so the smoother, the forward solve and the adjoint
+    solve give the same bits on every run."""
+    p = PROBLEMS["bulge48"]()
+    H = gmg.Hierarchy(p)
+    s = binding.FSISolver(p)
+    s.setup_smoothers(precision=prec, variant=binding.FSI_SMOOTHER_AS if variant == "as" else binding.FSI_SMOOTHER_FS)
+    r = _cuda(np.random.default_rng(90).standard_normal(H.fine.shape[0]))
+    l = len(H.A) - 1
+    for tr in (False, True):
+        y1 = s.apply_smoother(l, r, transpose=tr).cpu().numpy()
+        y2 = s.apply_smoother(l, r, transpose=tr).cpu().numpy()
+        np.testing.assert_array_equal(y1, y2)
+    b = _cuda(_rhs(p, H, 91))
+    x1, st1 = s.solve(b, rtol=1e-8)
+    x2, st2 = s.solve(b, rtol=1e-8)
+    assert st1["iterations"] == st2["iterations"]
+    np.testing.assert_array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    w = _cuda(np.random.default_rng(92).standard_normal(H.fine.shape[0]))
+    l1 = s.adjoint(w, x1, rtol=1e-8)[0].cpu().numpy()
+    l2 = s.adjoint(w, x1, rtol=1e-8)[0].cpu().numpy()
+    np.testing.assert_array_equal(l1, l2)
 
 
 FACTOR_CASES = {
@@ -405,7 +430,7 @@ def test_float32_blocked_inversion(name):
         assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
         _, st8 = stc.solve(_cuda(b), rtol=1e-8)
         _, st64 = s64.solve(_cuda(b), rtol=1e-8)
-        assert abs(st8["iterations"] - st64["iterations"]) <= 2, (st8["iterations"], st64["iterations"])
+        assert abs(st8["iterations"] - st64["iterations"]) <= 1, (st8["iterations"], st64["iterations"])
     with pytest.raises(binding.FSIError):
         binding.FSISolver(p).setup_smoothers(precision=binding.FSI_FP64, factor=binding.FSI_FACTOR_TF32)
 
@@ -487,7 +512,7 @@ def test_as_solves_fp64_and_mixed(as_case):
     Hm = gmg.Hierarchy(p, mixed="half", monolithic=True)
     _, ostm = ofg.solve(Hm, b, rtol=1e-8)
     _, stm = sm.solve(_cuda(b), rtol=1e-8)
-    assert abs(stm["iterations"] - ostm["iterations"]) <= 2, (stm["iterations"], ostm["iterations"])
+    assert abs(stm["iterations"] - ostm["iterations"]) <= 1, (stm["iterations"], ostm["iterations"])
 
 
 def test_as_3d_blocks_rejected():
@@ -596,7 +621,7 @@ def test_mult_vcycle_solves_and_adjoint(mult_case):
     Hh = gmg.Hierarchy(p, mixed="half", mult_levels=99)
     _, osth = ofg.solve(Hh, b, rtol=1e-8)
     _, sth = sh.solve(_cuda(b), rtol=1e-8)
-    assert abs(sth["iterations"] - osth["iterations"]) <= 2, (sth["iterations"], osth["iterations"])
+    assert abs(sth["iterations"] - osth["iterations"]) <= 1, (sth["iterations"], osth["iterations"])
 
 
 def test_mult_fine_level_only_mixed():
