@@ -110,6 +110,17 @@ typedef struct {
                                  * group with period 4 / 3 / 2 per direction for b = 1 / 2 / >= 3),
                                  * so blocks of one pass share no entry of A_FF and run at once.
                                  * The transposed cycle sweeps in reverse with A_jj^{-T} and A_FF^T. */
+    int cascade;                /* 1: the swapped cascade of the paper's future work (Sec. 5, the
+                                 * GMG and FS boxes interchanged): FGMRES on J2 preconditioned by
+                                 * the field split into the displacement system [d^s, d^f, p^s]
+                                 * (rows S, A, V) and the velocity system [u^s, u^f, p^f] (rows
+                                 * K, F, W), each diagonal block preconditioned by its own GMG
+                                 * V-cycle with the Schwarz smoothing above.  Realised as one
+                                 * V-cycle whose level operators, restrictions and coarse solve
+                                 * keep only same-system entries, so it equals
+                                 * blockdiag(GMG_d, GMG_u); the Krylov operator stays J2.  FS
+                                 * only (FSI_ERR_ARG with AS).  0: GMG outside, FS smoothing (the
+                                 * paper's method). */
 } fsi_smoother_opts;
 
 enum { FSI_SMOOTHER_FS = 0, FSI_SMOOTHER_AS = 1 };

@@ -16,6 +16,17 @@ a float32 scale per row (see fsasm.FSASM).
 The transposed cycle (adjoint extension) applies the transposed operators in
 reverse order: transposed post-smoothing first, restriction by P^T,
 transposed coarse solve, prolongation by R^T, transposed pre-smoothing.
+
+cascade=True builds the swapped cascade of the paper's future work (Sec. 5,
+the GMG and FS boxes of its solver diagram interchanged): the Krylov solver
+is preconditioned by the field split FS, whose two diagonal blocks -- the
+displacement system [d^s, d^f, p^s] (rows S, A, V) and the velocity system
+[u^s, u^f, p^f] (rows K, F, W) of J2 -- are each preconditioned by a GMG
+V-cycle with the same Schwarz (AS) smoothing.  Every operator the cycle
+uses (level matrices, restrictions, prolongations, the coarse matrix) is
+restricted to same-system entries, so one V-cycle over the whole vector is
+exactly blockdiag(GMG_d, GMG_u); the outer Krylov operator stays the full
+fine J2 (``fine``).
 """
 from __future__ import annotations
 
@@ -26,14 +37,29 @@ from .assemble import assemble
 from .fem import Reference
 from .fsasm import FSASM
 from .mesh import build_levels
-from .transfer import prolongation, restriction
+from .transfer import G_DF, G_DS, G_PS, prolongation, restriction
+
+
+def system_of(lev) -> np.ndarray:
+    """0 for the displacement system (d^s, d^f, p^s), 1 for the velocity
+    system (u^s, u^f, p^f), per dof of the level (J2 groups, Sec. 3.2)."""
+    return (~np.isin(lev.group, (G_DS, G_DF, G_PS))).astype(np.int64)
+
+
+def split_systems(M, sys_rows: np.ndarray, sys_cols: np.ndarray):
+    """M with the entries coupling the two systems removed."""
+    C = M.tocoo()
+    keep = sys_rows[C.row] == sys_cols[C.col]
+    return type(M.tocsr())((C.data[keep], (C.row[keep], C.col[keep])), shape=M.shape).tocsr()
 
 
 class Hierarchy:
     def __init__(self, prob, *, mixed: bool = False, omega: float | None = None, nu_pre: int = 1,
                  nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
-                 weighted: bool = True, monolithic: bool = False, mult_levels: int = 0):
+                 weighted: bool = True, monolithic: bool = False, mult_levels: int = 0,
+                 cascade: bool = False):
         self.prob = prob
+        self.cascade = cascade
         self.mixed = bool(mixed)
         half = mixed == "half"
         omega = getattr(prob, "omega", 1.0) if omega is None else omega
@@ -51,11 +77,20 @@ class Hierarchy:
                                          weighted=weighted, half=half, monolithic=monolithic,
                                          multiplicative=l >= nl - mult_levels)
                                    for l in range(1, nl)]
-        self.coarse_lu = la.lu_factor(self.A[0].toarray())
+        # operators of the cycle: the full ones, or (cascade) their two
+        # same-system diagonal blocks
+        Ac, Pc, Rc = self.A, self.P, self.R
+        if cascade:
+            sy = [system_of(lev) for lev in self.levels]
+            Ac = [split_systems(A, sy[l], sy[l]) for l, A in enumerate(self.A)]
+            Pc = [None] + [split_systems(self.P[l], sy[l], sy[l - 1]) for l in range(1, nl)]
+            Rc = [None] + [split_systems(self.R[l], sy[l - 1], sy[l]) for l in range(1, nl)]
+        self.A_cycle = Ac
+        self.coarse_lu = la.lu_factor(Ac[0].toarray())
         wd = self.wdtype
-        self.Aw = [A.astype(wd) for A in self.A]
-        self.Pw = [None] + [P.astype(wd) for P in self.P[1:]]
-        self.Rw = [None] + [R.astype(wd) for R in self.R[1:]]
+        self.Aw = [A.astype(wd) for A in Ac]
+        self.Pw = [None] + [P.astype(wd) for P in Pc[1:]]
+        self.Rw = [None] + [R.astype(wd) for R in Rc[1:]]
         self.AwT = [A.T.tocsr() for A in self.Aw]
 
     @property

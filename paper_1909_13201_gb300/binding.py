@@ -50,7 +50,7 @@ class HierOpts_t(C.Structure):
 class SmootherOpts_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("patch", C.c_int), ("omega", C.c_double),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("factor", C.c_int), ("variant", C.c_int),
-                ("mult_levels", C.c_int)]
+                ("mult_levels", C.c_int), ("cascade", C.c_int)]
 
 
 class SolveOpts_t(C.Structure):
@@ -178,14 +178,16 @@ class FSISolver:
             pass
 
     def setup_smoothers(self, precision=FSI_FP64, patch=None, omega=None, nu_pre=1, nu_post=1,
-                        factor=FSI_FACTOR_AUTO, variant=FSI_SMOOTHER_FS, mult_levels=0):
+                        factor=FSI_FACTOR_AUTO, variant=FSI_SMOOTHER_FS, mult_levels=0, cascade=False):
         """mult_levels: finest levels smoothed by the locally multiplicative
-        sweep (0 = additive everywhere)."""
+        sweep (0 = additive everywhere).  cascade: the swapped cascade (Krylov
+        preconditioned by FS with a GMG V-cycle inside each field system)."""
         if patch is None:
             patch = self.problems[0].patch
         if omega is None:
             omega = getattr(self.problems[0], "omega", 1.0)
-        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor, variant, mult_levels)
+        so = SmootherOpts_t(precision, patch, omega, nu_pre, nu_post, factor, variant, mult_levels,
+                            1 if cascade else 0)
         _check(load_library().fsi_setup_smoothers(self.ctx, C.byref(so)))
         self.precision = precision
 
@@ -297,6 +299,14 @@ class FSISolver:
                                              _ptr(val, C.c_double)))
         return ptr, col, val
 
+    def operator_values(self, level=None, prob=0, device="cuda"):
+        """The operator's values (CSR order of matrix()) as a float64 torch
+        tensor: the differentiable stand-in for fsi_solve_autograd."""
+        import torch
+        level = self.n_levels - 1 if level is None else level
+        _, _, val = self.matrix(level, prob)
+        return torch.from_numpy(val).to(device)
+
     def pattern(self, level, prob=0):
         sz = self.sizes(level, prob)
         ptr = np.zeros(sz["n"] + 1, np.int64)
@@ -362,12 +372,18 @@ def _make_autograd():
 
     class FSISolve(torch.autograd.Function):
         """x = J2^{-1} b with a hand-written backward: the adjoint solve
-        J2^T lambda = dL/dx (transposed V-cycle preconditioner), giving
-        dL/db = lambda.  The gradients with respect to the operator values
-        and mu_s are available from FSISolver.adjoint."""
+        J2^T lambda = dL/dx (transposed V-cycle preconditioner) gives
+        dL/db = lambda, dL/dA_ij = -lambda_i x_j on the fine operator's
+        sparsity pattern (CSR order of FSISolver.matrix) and
+        dL/dmu_s = -lambda^T (dA/dmu_s) x, all from one fsi_adjoint call.
+
+        `values` (the operator's nnz values) and `mu_s` (a 0-d tensor) are
+        the differentiable stand-ins of the operator the solver was set up
+        with: they must hold its values and shear modulus; the solve itself
+        uses the library's assembled operator."""
 
         @staticmethod
-        def forward(ctx, b, solver, rtol=1e-8):
+        def forward(ctx, b, values, mu_s, solver, rtol=1e-8):
             x, st = solver.solve(b, rtol=rtol)
             ctx.solver = solver
             ctx.rtol = rtol
@@ -377,8 +393,11 @@ def _make_autograd():
         @staticmethod
         def backward(ctx, gx):
             (x,) = ctx.saved_tensors
-            lam, _, _, _ = ctx.solver.adjoint(gx.contiguous(), x, rtol=ctx.rtol, want_dA=False, want_dmu=False)
-            return lam, None, None
+            want_dA, want_dmu = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            lam, dA, dmu, _ = ctx.solver.adjoint(gx.contiguous(), x, rtol=ctx.rtol, want_dA=want_dA,
+                                                 want_dmu=want_dmu)
+            g_mu = torch.tensor(dmu, dtype=torch.float64, device=gx.device) if want_dmu else None
+            return lam, dA if want_dA else None, g_mu, None, None
 
     return FSISolve
 
@@ -386,9 +405,22 @@ def _make_autograd():
 _FSISOLVE = None
 
 
-def fsi_solve_autograd(b, solver, rtol=1e-8):
-    """Differentiable x = J2^{-1} b (torch.autograd.Function, adjoint backward)."""
+def fsi_solve_autograd(b, solver, rtol=1e-8, values=None, mu_s=None):
+    """Differentiable x = J2^{-1} b (torch.autograd.Function, adjoint backward).
+
+    b: right-hand side (gradient dL/db = lambda).  values: optional tensor of
+    the fine operator's nnz values in CSR order (see FSISolver.operator_values);
+    its gradient is dL/dA on the pattern.  mu_s: optional 0-d float64 tensor
+    holding the solid shear modulus of the problem; its gradient is dL/dmu_s."""
+    import torch
     global _FSISOLVE
     if _FSISOLVE is None:
         _FSISOLVE = _make_autograd()
-    return _FSISOLVE.apply(b, solver, rtol)
+    nnz = solver.sizes(solver.n_levels - 1)["nnz"]
+    if values is None:
+        values = torch.zeros(nnz, dtype=torch.float64, device=b.device)
+    elif values.numel() != nnz:
+        raise ValueError(f"values must hold the fine operator's {nnz} entries")
+    if mu_s is None:
+        mu_s = torch.zeros((), dtype=torch.float64, device=b.device)
+    return _FSISOLVE.apply(b, values, mu_s, solver, rtol)

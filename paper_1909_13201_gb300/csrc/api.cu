@@ -227,17 +227,20 @@ fsi_status smooth_apply(Context &cx, LevelDev &L, const T *r, T *x, bool tr, boo
 template <class T>
 fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr, bool x_zeroed = false) {
     cudaStream_t s = cx.stream;
+    const bool cz = cx.cascade != 0;        // swapped cascade: the two system blocks only
     if (l == 0) {
         // transposed cycle: the stored transpose, read row by row like the forward
         // product (a column-by-column product of the row-major inverse takes 20x longer)
-        if (tr && pb.coarse_inv_t.p) return launch_dense_gemv<T>(pb.coarse_inv_t.as<double>(), pb.n0, b, x, 0, s);
-        return launch_dense_gemv<T>(pb.coarse_inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
+        const DevBuf &inv = cz ? pb.coarse_inv_c : pb.coarse_inv;
+        const DevBuf &inv_t = cz ? pb.coarse_inv_ct : pb.coarse_inv_t;
+        if (tr && inv_t.p) return launch_dense_gemv<T>(inv_t.as<double>(), pb.n0, b, x, 0, s);
+        return launch_dense_gemv<T>(inv.as<double>(), pb.n0, b, x, tr ? 1 : 0, s);
     }
     LevelDev &L = pb.dev[l];
     LevelDev &C = pb.dev[l - 1];
-    const DevCSR &A = tr ? L.AT : L.A;
-    const DevCSR &Rm = tr ? L.PT : L.R;     // restriction
-    const DevCSR &Pm = tr ? L.RT : L.P;     // prolongation
+    const DevCSR &A = tr ? (cz ? L.ATc : L.AT) : (cz ? L.Ac : L.A);
+    const DevCSR &Rm = tr ? L.PT : (cz ? L.Rc : L.R);     // restriction
+    const DevCSR &Pm = tr ? (cz ? L.RTc : L.RT) : L.P;    // prolongation
     const int npre = tr ? cx.nu_post : cx.nu_pre, npost = tr ? cx.nu_pre : cx.nu_post;
     const bool fine = l == (int)pb.dev.size() - 1;
     T *r = L.r.as<T>();
@@ -642,6 +645,10 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
         FSI_TRY(pb.coarse_inv_t.alloc((size_t)pb.n0 * pb.n0 * 8));
         FSI_TRY(launch_transpose(pb.coarse_inv.as<double>(), pb.n0, pb.coarse_inv_t.as<double>(), s));
     }
+    if (cx.cascade) {
+        FSI_TRY(pb.coarse_inv_ct.alloc((size_t)pb.n0 * pb.n0 * 8));
+        FSI_TRY(launch_transpose(pb.coarse_inv_c.as<double>(), pb.n0, pb.coarse_inv_ct.as<double>(), s));
+    }
     for (size_t l = 0; l < pb.dev.size(); ++l) {
         LevelDev &L = pb.dev[l];
         HostCSR A, AT;
@@ -649,6 +656,24 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
         transpose_csr(A, AT);
         FSI_TRY(upload_csr(L.AT, AT, s));
         FSI_TRY(build_ell(L.AT, s, cx.probs.size() > 1));
+        if (cx.cascade) {
+            HostCSR Ac, ATc;
+            FSI_TRY(download_csr(L.Ac, Ac, s));
+            transpose_csr(Ac, ATc);
+            FSI_TRY(upload_csr(L.ATc, ATc, s));
+            FSI_TRY(build_ell(L.ATc, s, cx.probs.size() > 1));
+            L.ATc.val32.release();
+            if (cx.precision != FSI_FP64) FSI_TRY(make_f32(L.ATc, s));
+            if (l >= 1) {
+                HostCSR Rc, RTc;
+                FSI_TRY(download_csr(L.Rc, Rc, s));
+                transpose_csr(Rc, RTc);
+                FSI_TRY(upload_csr(L.RTc, RTc, s));
+                FSI_TRY(build_ell(L.RTc, s, cx.probs.size() > 1));
+                L.RTc.val32.release();
+                if (cx.precision != FSI_FP64) FSI_TRY(make_f32(L.RTc, s));
+            }
+        }
         if (l >= 1) {
             HostCSR PT, RT;
             transpose_csr(pb.hP[l], PT);
@@ -772,8 +797,71 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
     return FSI_OK;
 }
 
+// Swapped cascade (Sec. 5, future work): the cycle runs on the two system
+// blocks of every operator -- the displacement system [d^s, d^f, p^s] (J2
+// dofs before off[3]) and the velocity system [u^s, u^f, p^f] -- so one
+// V-cycle is blockdiag(GMG_d, GMG_u).  Built once per problem: A_l and R_l
+// without their cross-system entries, and the float64 inverse of the coarse
+// block-diagonal operator.  P_l couples no systems (checked).
+HostCSR split_systems(const HostCSR &M, int64_t row_off3, int64_t col_off3) {
+    HostCSR out;
+    out.n_rows = M.n_rows;
+    out.n_cols = M.n_cols;
+    out.ptr.assign(1, 0);
+    for (int64_t i = 0; i < M.n_rows; ++i) {
+        const bool ri = i >= row_off3;
+        for (int64_t k = M.ptr[i]; k < M.ptr[i + 1]; ++k) {
+            if (((int64_t)M.col[k] >= col_off3) != ri) continue;
+            out.col.push_back(M.col[k]);
+            out.val.push_back(M.val[k]);
+        }
+        out.ptr.push_back((int64_t)out.col.size());
+    }
+    return out;
+}
+
+fsi_status build_cascade(Context &cx, Problem &pb) {
+    if (pb.cascade_ready) return FSI_OK;
+    cudaStream_t s = cx.stream;
+    const bool conc = cx.probs.size() > 1;
+    for (size_t l = 0; l < pb.dev.size(); ++l) {
+        LevelDev &L = pb.dev[l];
+        const LevelHost &H = pb.host[l];
+        HostCSR A;
+        FSI_TRY(download_csr(L.A, A, s));
+        FSI_TRY(upload_csr(L.Ac, split_systems(A, H.off[3], H.off[3]), s));
+        FSI_TRY(build_ell(L.Ac, s, conc));
+        L.Ac.val32.release();
+        if (l >= 1) {
+            const LevelHost &Hc = pb.host[l - 1];
+            const HostCSR &P = pb.hP[l];
+            for (int64_t i = 0; i < P.n_rows; ++i)
+                for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k)
+                    if ((i >= H.off[3]) != ((int64_t)P.col[k] >= Hc.off[3])) {
+                        set_error("prolongation couples the displacement and velocity systems");
+                        return FSI_ERR_STATE;
+                    }
+            FSI_TRY(upload_csr(L.Rc, split_systems(pb.hR[l], Hc.off[3], H.off[3]), s));
+            FSI_TRY(build_ell(L.Rc, s, conc));
+            L.Rc.val32.release();
+        }
+    }
+    FSI_TRY(pb.coarse_inv_c.alloc((size_t)pb.n0 * pb.n0 * 8));
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    FSI_TRY(coarse_invert(pb.dev[0].Ac, pb.n0, pb.coarse_inv_c.as<double>(), cx.flags.as<int>(), s));
+    int flag = 0;
+    FSI_TRY(read_flag(cx, &flag));
+    if (flag) {
+        set_error("coarse-level system blocks are singular");
+        return FSI_ERR_ZERO_PIVOT;
+    }
+    pb.cascade_ready = true;
+    return FSI_OK;
+}
+
 fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
     cudaStream_t s = cx.stream;
+    if (cx.cascade) FSI_TRY(build_cascade(cx, pb));
     const bool mixed = cx.precision != FSI_FP64;             // float32 cycle
     const size_t tsz = mixed ? 4 : 8;
     const int store = cx.precision == FSI_MIXED_HALF ? 2 : (mixed ? 1 : 0);
@@ -787,6 +875,10 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             if (l >= 1) {
                 FSI_TRY(make_f32(D.P, s));
                 FSI_TRY(make_f32(D.R, s));
+            }
+            if (cx.cascade) {
+                FSI_TRY(make_f32(D.Ac, s));
+                if (l >= 1) FSI_TRY(make_f32(D.Rc, s));
             }
         }
         FSI_TRY(D.b.alloc((size_t)D.n * tsz));
@@ -1136,7 +1228,9 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
         opts->factor < FSI_FACTOR_AUTO || opts->factor > FSI_FACTOR_TF32 ||
         (opts->variant != FSI_SMOOTHER_FS && opts->variant != FSI_SMOOTHER_AS) ||
         opts->mult_levels < 0 ||
-        (opts->mult_levels > 0 && opts->variant != FSI_SMOOTHER_FS)) {
+        (opts->mult_levels > 0 && opts->variant != FSI_SMOOTHER_FS) ||
+        (opts->cascade != 0 && opts->cascade != 1) ||
+        (opts->cascade == 1 && opts->variant != FSI_SMOOTHER_FS)) {
         set_error("smoother options out of range");
         return FSI_ERR_ARG;
     }
@@ -1154,6 +1248,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     cx->factor = opts->factor;
     cx->variant = opts->variant;
     cx->mult_levels = opts->mult_levels;
+    cx->cascade = opts->cascade;
     cx->smoothers_ready = false;
     for (auto &pb : cx->probs) FSI_TRY(setup_smoothers_problem(*cx, pb));
     FSI_CUDA(cudaStreamSynchronize(cx->stream));

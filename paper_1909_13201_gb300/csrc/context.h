@@ -114,6 +114,10 @@ struct LevelDev {
     DevCSR A, AT;         // operator and (adjoint) its transpose
     DevCSR P, R;          // l >= 1: P_l (n_l x n_{l-1}), R_l (n_{l-1} x n_l)
     DevCSR PT, RT;        // adjoint: P^T (restriction), R^T (prolongation)
+    // swapped cascade (Sec. 5): the same-system diagonal blocks of A and R
+    // (entries coupling the displacement and velocity systems removed) and
+    // their transposes; P couples no systems and is used as it is
+    DevCSR Ac, ATc, Rc, RTc;
     DevBuf fixed;         // uint8 per dof
     // Schwarz blocks (l >= 1)
     int64_t n_blocks = 0, max_block = 0, inv_elems = 0;
@@ -168,6 +172,8 @@ struct Problem {
     int64_t n0 = 0;                  // coarse size
     DevBuf coarse_inv;               // n0 x n0 float64 inverse of A_0 (row-major)
     DevBuf coarse_inv_t;             // its transpose (transposed cycle; built with the transposes)
+    DevBuf coarse_inv_c, coarse_inv_ct;   // swapped cascade: inverse of A_0's system blocks, transpose
+    bool cascade_ready = false;      // Ac / Rc / coarse_inv_c built
     DevBuf coarse_b, coarse_x;       // float64 coarse vectors
     DevBuf dA_mu;                    // float64 values of dA/dmu_s on the fine pattern
     bool transposes_ready = false;
@@ -232,6 +238,7 @@ struct Context {
     int factor = FSI_FACTOR_AUTO;    // block inversion method (resolved per precision)
     int variant = FSI_SMOOTHER_FS;   // field-split (FS) or monolithic (AS) Schwarz blocks
     int mult_levels = 0;             // finest levels with the locally multiplicative sweep
+    int cascade = 0;                 // 1: swapped cascade, the cycle on the two system blocks (Sec. 5)
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;

@@ -22,6 +22,7 @@ torch = pytest.importorskip("torch")
 from oracle import adjoint as oadj
 from oracle import fgmres as ofg
 from oracle import gmg
+from oracle.assemble import assemble
 from paper_1909_13201_gb300 import binding
 from paper_1909_13201_gb300 import inputs as I
 
@@ -197,6 +198,48 @@ def test_autograd_backward_is_adjoint():
     x = binding.fsi_solve_autograd(b, s, rtol=1e-10)
     (x * w).sum().backward()
     lam = _direct(H.fine.T.tocsr(), w.cpu().numpy())
+    assert np.linalg.norm(b.grad.cpu().numpy() - lam) <= 1e-9 * np.linalg.norm(lam)
+
+
+def test_autograd_operator_and_mu_s_gradients_central_differences():
+    """autograd through fsi_solve_autograd with the operator values and mu_s
+    as inputs: dJ/dA on the pattern and dJ/dmu_s against central differences
+    of J = w^T A^{-1} b computed with the oracle (sparse direct solves of the
+    oracle's assembled operator; mu_s perturbed in the assembly with
+    lambda_s held fixed)."""
+    p = I.make_config(0)
+    s = binding.FSISolver(p)
+    s.setup_smoothers(precision=binding.FSI_FP64)
+    H = gmg.Hierarchy(p)
+    A = H.fine.tocsr()
+    rng = np.random.default_rng(15)
+    bn = _rhs(p, H, 16)
+    wn = rng.standard_normal(bn.size)
+    b = _cuda(bn).requires_grad_(True)
+    vals = s.operator_values().requires_grad_(True)
+    mu = torch.tensor(p.mu_s, dtype=torch.float64, device="cuda", requires_grad=True)
+    ptr, col, v0 = s.matrix(len(H.A) - 1)
+    x = binding.fsi_solve_autograd(b, s, rtol=1e-11, values=vals, mu_s=mu)
+    (x * _cuda(wn)).sum().backward()
+    gA = vals.grad.cpu().numpy()
+    gmu = float(mu.grad)
+    solve = lambda M, rhs: _direct(M.tocsr(), rhs)
+    J = lambda M: wn @ solve(M, bn)
+    h = 1e-6
+    # a random direction scaled entry-wise by |A_ij| (entries span many decades)
+    dv = rng.standard_normal(v0.size) * np.abs(v0)
+    D = sp.csr_matrix((dv, col, ptr), shape=A.shape)        # on the library's pattern and order
+    fd = (J(A + h * D) - J(A - h * D)) / (2 * h)
+    assert gA @ dv == pytest.approx(fd, rel=1e-5)
+    Js = []
+    for sgn in (1, -1):
+        q = I.make_config(0)
+        q.mu_s = p.mu_s * (1 + sgn * h)
+        q.lambda_s = p.lambda_s
+        Js.append(J(assemble(q, H.levels[-1])))
+    assert gmu == pytest.approx((Js[0] - Js[1]) / (2 * h * p.mu_s), rel=1e-5)
+    # dJ/db is lambda, as before
+    lam = _direct(A.T.tocsr(), wn)
     assert np.linalg.norm(b.grad.cpu().numpy() - lam) <= 1e-9 * np.linalg.norm(lam)
 
 
@@ -683,3 +726,49 @@ def test_mult_3d_sweep_and_solve():
     _, st8 = s.solve(_cuda(b), rtol=1e-8)
     _, ost = ofg.solve(H, b, rtol=1e-8)
     assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
+
+
+# ---- swapped cascade (the paper's future work, Sec. 5): Krylov preconditioned
+# by FS with a GMG V-cycle inside each field system
+@pytest.mark.parametrize("mult_levels", [0, 1])
+def test_cascade_vcycle_and_solves(case, mult_levels):
+    name, p, H, s = case
+    Hc = gmg.Hierarchy(p, cascade=True, mult_levels=mult_levels)
+    sc = binding.FSISolver(p)
+    sc.setup_smoothers(precision=binding.FSI_FP64, cascade=True, mult_levels=mult_levels)
+    rng = np.random.default_rng(95)
+    v = rng.standard_normal(Hc.fine.shape[0])
+    b = _rhs(p, Hc, 96)
+    xd = _direct(Hc.fine, b)
+    x, st = sc.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"]
+    assert np.linalg.norm(x.cpu().numpy() - xd) <= 1e-9 * np.linalg.norm(xd)
+    _, st8 = sc.solve(_cuda(b), rtol=1e-8)
+    _, ost = ofg.solve(Hc, b, rtol=1e-8)
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
+    # the transposed cycle (built with the transposes by the adjoint)
+    w = rng.standard_normal(b.size)
+    lam, _, _, sta = sc.adjoint(_cuda(w), x, rtol=1e-10)
+    lam_d = _direct(Hc.fine.T.tocsr(), w)
+    assert sta["converged"]
+    assert np.linalg.norm(lam.cpu().numpy() - lam_d) <= 1e-9 * np.linalg.norm(lam_d)
+    for tr in (False, True):
+        z = sc.apply_vcycle(_cuda(v), transpose=tr).cpu().numpy()
+        ref = Hc.vcycle_transpose(v) if tr else Hc.vcycle(v)
+        assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref), (name, tr)
+    # mixed precision with float16 inverses: iterations against the oracle's emulation
+    sh = binding.FSISolver(p)
+    sh.setup_smoothers(precision=binding.FSI_MIXED_HALF, factor=binding.FSI_FACTOR_FP64, cascade=True,
+                       mult_levels=mult_levels)
+    x, st = sh.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+    Hh = gmg.Hierarchy(p, cascade=True, mixed="half", mult_levels=mult_levels)
+    _, osth = ofg.solve(Hh, b, rtol=1e-8)
+    _, sth = sh.solve(_cuda(b), rtol=1e-8)
+    assert abs(sth["iterations"] - osth["iterations"]) <= 1, (sth["iterations"], osth["iterations"])
+
+
+def test_cascade_rejected_with_monolithic_blocks():
+    s = binding.FSISolver(I.make_config(0))
+    with pytest.raises(binding.FSIError):
+        s.setup_smoothers(precision=binding.FSI_FP64, variant=binding.FSI_SMOOTHER_AS, cascade=True)
