@@ -11,13 +11,21 @@ size.
   reference formed from every block that overlaps them, one block at a time;
   the lumped K_u^s Jacobi rows on a sample;
 - the solves bench.py times (FP16 inverses from tensor-core factors, additive
-  smoother and the multiplicative sweep on the finest level): converged, the
-  float64 true residual re-evaluated on the host with the library's operator,
-  and that operator equal to the oracle's on the solution.
+  smoother and the multiplicative sweep on the finest level): converged, and
+  the true residual of the oracle's operator, evaluated on the host in
+  extended precision, within 1.05 rtol;
+- iteration counts within +-1 of the oracle's on the same storage emulation
+  and the solution against the oracle's float64 solution at sampled
+  unknowns, both from tests/golden/full_size_256.json, which
+  tests/golden/make_full_size_reference.py writes from oracle/ alone; two
+  solves in a row give the same iterate bit for bit.
 
 Collected after every other test file: it builds the largest hierarchy of
 the suite.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg as la
@@ -115,21 +123,78 @@ def test_full_size_fp16_smoother_sampled_blocks(full):
     np.testing.assert_allclose(y[k], ref_k, rtol=1e-6, atol=0)
 
 
+def _residual_ld(A, x, b):
+    """||b - A x|| evaluated in extended precision (numpy longdouble: 64-bit
+    significand on x86, 113-bit on Arm): on these row-scaled systems
+    || |A| |x| || ~ 3e6 ||b||, so a float64 evaluation alone is uncertain by
+    ~1e-9 ||b||; the extended sum removes the host's share of that."""
+    Al = A.astype(np.longdouble)
+    r = b.astype(np.longdouble) - Al @ x.astype(np.longdouble)
+    return float(np.sqrt(np.sum(r * r)))
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "full_size_256.json")) as f:
+        g = json.load(f)
+    return g
+
+
 @pytest.mark.parametrize("mult_levels", [0, 1])
-def test_full_size_solve_true_residual(full, mult_levels):
-    """The solve's claim, re-evaluated on the host: ||b - A_lib x|| <= rtol ||b||
-    with the library's own operator (slack 1.5x: on these row-scaled systems
-    || |A| |x| || ~ 3e6 ||b||, so float64 summation order alone moves the
-    residual by ~1e-9 ||b||), and the library's operator equals the oracle's
-    on the solution, ||(A_lib - A) x|| <= 1e-12 || |A| |x| ||, so x solves the
-    oracle's system to that agreement."""
+def test_full_size_solve_true_residual(full, golden, mult_levels):
+    """The solves bench.py times (FP16 inverses from tensor-core factors):
+    x solves the oracle's assembled system, ||b - A x|| <= 1.05 rtol ||b||
+    (the solve stops on its own float64 true residual <= rtol; 5 % covers the
+    float64 summation order of that on-device evaluation), and the iteration
+    count stays within one of the oracle's on the same storage emulation."""
     p, lev, A, s, b = full
     s.setup_smoothers(precision=binding.FSI_MIXED_HALF, mult_levels=mult_levels)
     x, st = s.solve(_cuda(b), rtol=RTOL)
     assert st["converged"] and st["rel_residual"] <= RTOL
     xr = x.cpu().numpy()
-    ptr, col, val = s.matrix(p.n_levels - 1)
-    A_lib = sp.csr_matrix((val, col, ptr), shape=A.shape)
-    r_lib = b - A_lib @ xr
-    assert np.linalg.norm(r_lib) <= 1.5 * RTOL * np.linalg.norm(b), (mult_levels, st)
-    assert np.linalg.norm(A_lib @ xr - A @ xr) <= 1e-12 * np.linalg.norm(abs(A) @ np.abs(xr))
+    assert _residual_ld(A, xr, b) <= 1.05 * RTOL * np.linalg.norm(b), (mult_levels, st)
+    key = "iterations_half_mult_fine" if mult_levels else "iterations_half_additive"
+    assert abs(st["iterations"] - golden[key]) <= 1, (st["iterations"], golden[key])
+
+
+@pytest.mark.parametrize("mult_levels", [0, 1])
+def test_full_size_iterations_match_oracle(full, golden, mult_levels):
+    """FGMRES iteration count at full size within +-1 of the oracle's, with
+    the storage the oracle emulates (float64 block inverses rounded to
+    row-scaled float16, float32 cycle, float64 Krylov); the count was written
+    by tests/golden/make_full_size_reference.py from oracle/ alone."""
+    p, lev, A, s, b = full
+    s.setup_smoothers(precision=binding.FSI_MIXED_HALF, factor=binding.FSI_FACTOR_FP64,
+                      mult_levels=mult_levels)
+    key = "iterations_half_mult_fine" if mult_levels else "iterations_half_additive"
+    x, st = s.solve(_cuda(b), rtol=RTOL)
+    assert st["converged"]
+    assert abs(st["iterations"] - golden[key]) <= 1, (st["iterations"], golden[key])
+    x2, st2 = s.solve(_cuda(b), rtol=RTOL)
+    # the smoother combines overlapping blocks in a fixed order: repeatable
+    assert st2["iterations"] == st["iterations"]
+    np.testing.assert_array_equal(x.cpu().numpy(), x2.cpu().numpy())
+
+
+def test_full_size_solution_matches_oracle(full, golden):
+    """The bench's mixed solve to 1e-8 against the oracle's float64 solution
+    to 1e-8 at 1024 sampled unknowns of every J2 field group (their
+    magnitudes span many decades, so each group is compared on its own
+    scale).  Two solutions meeting the same residual bound differ by up to
+    cond(A) x 2e-8, and cond(A) of this row-scaled system is too large for a
+    useful a-priori bound, so each group's tolerance comes from the oracle
+    alone: 10x the spread between its own float64 and float16-storage
+    solutions (both to 1e-8), at least 1e-7, stored beside the sample by the
+    script that wrote it."""
+    p, lev, A, s, b = full
+    s.setup_smoothers(precision=binding.FSI_MIXED_HALF)
+    x, st = s.solve(_cuda(b), rtol=golden["fp64_rtol"])
+    assert st["converged"]
+    xs = x.cpu().numpy()
+    for g in golden["groups"]:
+        tol = max(10 * g["half_vs_fp64_rel_diff"], 1e-7)
+        dofs = np.flatnonzero(lev.group == g["group"])
+        idx = np.asarray(g["sample_idx"])
+        ref = np.asarray(g["x_sample"])
+        assert abs(np.linalg.norm(xs[dofs]) - g["norm"]) <= tol * g["norm"], g["group"]
+        assert np.linalg.norm(xs[idx] - ref) <= tol * np.linalg.norm(ref), (g["group"], tol)
