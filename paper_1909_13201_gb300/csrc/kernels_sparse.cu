@@ -210,21 +210,24 @@ fsi_status run_ell_g(const DevEll &E, const TA *val, const TX *x, const TY *b, T
     return FSI_OK;
 }
 
+// The kernel's lanes per row must equal the layout's: a bin's slabs hold
+// 32 / G rows, so any other G maps slabs to rows past the bin.
+template <bool STREAM, class TA, class TX, class TY>
+fsi_status run_ell_s(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s,
+                     TY *z) {
+    switch (E.G) {
+        case 1: return run_ell_g<1, STREAM>(E, val, x, b, y, mode, s, z);
+        case 4: return run_ell_g<4, STREAM>(E, val, x, b, y, mode, s, z);
+        case 8: return run_ell_g<8, STREAM>(E, val, x, b, y, mode, s, z);
+        case 16: return run_ell_g<16, STREAM>(E, val, x, b, y, mode, s, z);
+        default: set_error("ELL copy with an unsupported lane count"); return FSI_ERR_STATE;
+    }
+}
+
 template <class TA, class TX, class TY>
 fsi_status run_ell(const DevEll &E, const TA *val, const TX *x, const TY *b, TY *y, int mode, cudaStream_t s,
                    TY *z) {
-    if (E.stream) {
-        switch (E.G) {
-            case 1: return run_ell_g<1, true>(E, val, x, b, y, mode, s, z);
-            default: return run_ell_g<4, true>(E, val, x, b, y, mode, s, z);
-        }
-    }
-    switch (E.G) {
-        case 1: return run_ell_g<1, false>(E, val, x, b, y, mode, s, z);
-        case 4: return run_ell_g<4, false>(E, val, x, b, y, mode, s, z);
-        case 8: return run_ell_g<8, false>(E, val, x, b, y, mode, s, z);
-        default: return run_ell_g<16, false>(E, val, x, b, y, mode, s, z);
-    }
+    return E.stream ? run_ell_s<true>(E, val, x, b, y, mode, s, z) : run_ell_s<false>(E, val, x, b, y, mode, s, z);
 }
 
 template <class T>
