@@ -1002,13 +1002,19 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             const int64_t split = D.n_blocks >= want ? 1 : (want + D.n_blocks - 1) / D.n_blocks;
             std::vector<int32_t> it;
             std::vector<int64_t> pass_b0, pass_i0;    // sweep: first block and first item of every pass
+            int64_t split_p = split;
             for (int64_t j = 0; j < D.n_blocks; ++j) {
                 if (sweep && (j == 0 || bpass[j] != bpass[j - 1])) {
                     pass_b0.push_back(j);
                     pass_i0.push_back((int64_t)it.size() / 4);
+                    // a pass is its own launch: split its blocks by rows until
+                    // the pass alone gives every SM several items
+                    int64_t nb = 0;
+                    while (j + nb < D.n_blocks && bpass[j + nb] == bpass[j]) ++nb;
+                    split_p = nb >= want ? 1 : (want + nb - 1) / nb;
                 }
                 const int nj = (int)(D.h_blk_ptr[j + 1] - D.h_blk_ptr[j]);
-                int chunk = (int)((nj + split - 1) / split);
+                int chunk = (int)((nj + split_p - 1) / split_p);
                 chunk = std::max(16, (chunk + 15) / 16 * 16);
                 for (int r0 = 0; r0 < nj; r0 += chunk) {
                     it.push_back((int32_t)j);
@@ -1019,10 +1025,11 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
             }
             const int64_t blk_items = (int64_t)it.size() / 4;
             // Jacobi rows ride in the same launch: items (-1, k0, k1) over the jac list
-            for (int64_t k0 = 0; k0 < D.n_jac; k0 += 2048) {
+            // (256 rows each: a sweep runs them as a pass of their own)
+            for (int64_t k0 = 0; k0 < D.n_jac; k0 += 256) {
                 it.push_back(-1);
                 it.push_back((int32_t)k0);
-                it.push_back((int32_t)std::min<int64_t>(D.n_jac, k0 + 2048));
+                it.push_back((int32_t)std::min<int64_t>(D.n_jac, k0 + 256));
                 it.push_back(0);
             }
             D.n_items = (int64_t)it.size() / 4;
