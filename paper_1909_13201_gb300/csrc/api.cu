@@ -192,7 +192,10 @@ void collect_marks(Context &cx) {
 // level in order (transposed: in reverse, with A_jj^{-T} and A_FF^T), where
 // a pass corrects y on its blocks from r - A_FF y on its rows (the first pass
 // of a field starts from y = 0 and reads r itself); then x += omega y and y is
-// cleared for the next sweep.
+// cleared for the next sweep.  P2 is block diagonal in the two field systems
+// and each sweep reads and writes only its own system's rows of y and rr, so
+// the velocity system's passes run on an auxiliary stream beside the
+// displacement system's (forked from and joined back to the caller's stream).
 template <class T>
 fsi_status mult_smooth(Context &cx, LevelDev &L, const T *r, T *x, bool tr) {
     cudaStream_t s = cx.stream;
@@ -202,16 +205,26 @@ fsi_status mult_smooth(Context &cx, LevelDev &L, const T *r, T *x, bool tr) {
     }
     T *y = L.y.as<T>(), *rr = L.rr.as<T>();
     const int np = (int)L.passes.size();
+    const bool two = L.fj.aux != nullptr;
+    if (two) {
+        FSI_CUDA(cudaEventRecord(L.fj.fork, s));
+        FSI_CUDA(cudaStreamWaitEvent(L.fj.aux, L.fj.fork, 0));
+    }
     bool started[2] = {false, false};
     for (int q = 0; q < np; ++q) {
         const SweepPass &P = L.passes[tr ? np - 1 - q : q];
+        cudaStream_t sp = (two && P.field == 1) ? L.fj.aux : s;
         const T *src = r;
         if (started[P.field]) {
-            FSI_TRY(launch_ell_resid<T>(tr ? P.ell_t : P.ell, y, r, rr, s));
+            FSI_TRY(launch_ell_resid<T>(tr ? P.ell_t : P.ell, y, r, rr, sp));
             src = rr;
         }
         started[P.field] = true;
-        FSI_TRY(launch_block_apply<T>(L, src, y, (T)1, tr ? 1 : 0, s, P.it0, P.it1));
+        FSI_TRY(launch_block_apply<T>(L, src, y, (T)1, tr ? 1 : 0, sp, P.it0, P.it1));
+    }
+    if (two) {
+        FSI_CUDA(cudaEventRecord(L.fj.join, L.fj.aux));
+        FSI_CUDA(cudaStreamWaitEvent(s, L.fj.join, 0));
     }
     return launch_axpy_clear<T>(x, y, (T)cx.omega, L.n, s);
 }
@@ -1076,6 +1089,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                 FSI_TRY(D.y.alloc((size_t)D.n * tsz));
                 FSI_TRY(D.rr.alloc((size_t)D.n * tsz));
                 FSI_CUDA(cudaMemsetAsync(D.y.p, 0, (size_t)D.n * tsz, s));
+                FSI_CUDA(D.fj.create());
             } else {
                 for (int f = 0; f < 2; ++f) {
                     D.h_keep[f].clear();
@@ -1083,6 +1097,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                 }
                 D.y.release();
                 D.rr.release();
+                D.fj.release();
             }
         }
         FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));

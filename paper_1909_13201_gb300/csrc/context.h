@@ -27,6 +27,40 @@ void set_error(const std::string &msg);
         if (s_ != FSI_OK) return s_;       \
     } while (0)
 
+// An auxiliary stream with a fork and a join event (owned): the two field
+// systems of a multiplicative sweep run side by side on it and the caller's
+// stream.  Inside a stream capture the fork/join become graph edges.
+struct ForkJoin {
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ForkJoin() = default;
+    ForkJoin(const ForkJoin &) = delete;
+    ForkJoin &operator=(const ForkJoin &) = delete;
+    ForkJoin(ForkJoin &&o) noexcept { *this = std::move(o); }
+    ForkJoin &operator=(ForkJoin &&o) noexcept {
+        if (this != &o) {
+            release();
+            aux = o.aux; fork = o.fork; join = o.join;
+            o.aux = nullptr; o.fork = nullptr; o.join = nullptr;
+        }
+        return *this;
+    }
+    ~ForkJoin() { release(); }
+    void release() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (aux) cudaStreamDestroy(aux);
+        aux = nullptr; fork = nullptr; join = nullptr;
+    }
+    cudaError_t create() {
+        if (aux) return cudaSuccess;
+        cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        return e;
+    }
+};
+
 // Owned device allocation.
 struct DevBuf {
     void *p = nullptr;
@@ -145,6 +179,7 @@ struct LevelDev {
     bool mult_t_ready = false;
     std::vector<SweepPass> passes;
     DevBuf y, rr;                               // correction (zero between sweeps), pass residual
+    ForkJoin fj;                                // the velocity system's passes run on fj.aux
     std::vector<uint8_t> h_keep[2];             // per dof: free dof of field 0 (d, p^s) / 1 (u, p^f)
     DevBuf keep[2];
 };
