@@ -9,17 +9,20 @@ smoothing, Arnoldi, refinement): every step of the solve path.  Set-up
 (hierarchy, assembly, block factorisation) is timed separately.
 
   value      mixed precision (float32 cycle with float16 row-scaled block
-             inverses, float64 Krylov), device-resident right-hand side, CUDA
+             inverses, float64 Krylov) with the locally multiplicative Schwarz
+             sweep per field system on the finest level (Sec. 3.2; additive
+             on the coarser levels), device-resident right-hand side, CUDA
              events on the solver's stream;
-  mixed_f32_inverses  the same with float32 block inverses;
-  multiplicative_fine  the same with the locally multiplicative Schwarz
-             sweep per field system on the finest level (additive below);
+  additive   the same with the additive field-split smoother everywhere;
+  mixed_f32_inverses  the headline configuration with float32 inverses;
   fp64       the all-float64 path on the same system (mixed/fp64 speed-up);
-  e2e        mixed precision through the public call with host buffers
+  as_smoother  the paper's monolithic AS comparison smoother;
+  cascade    the swapped cascade of the paper's future work (Sec. 5);
+  e2e        the headline through the public call with host buffers
              (pinned H2D of b, solve, D2H of x inside the timed region);
-  roofline   the fine-level FS-ASM smoother apply, the dominant kernel:
-             algorithmic bytes / its mean launch time from CUDA events,
-             against the measured HBM copy bandwidth;
+  roofline   the fine-level sweep (its apply and pass-residual launches on
+             two streams): algorithmic bytes / its mean time from CUDA
+             events, against the measured HBM copy bandwidth;
   cpu_baseline  the FP64 oracle on this host, bounded sample (see "sample").
 
 --impl reference runs the oracle itself as the reference arm.  With
@@ -50,10 +53,14 @@ if ROOT not in sys.path:
 METRIC = "fine DOF/s to 1e-8 rel residual (mixed vs FP64 GPU); smoother % HBM peak"
 UNIT = "DOF/s"
 RTOL = 1e-8
-# FGMRES iterations the oracle's algorithm needs on each seeded workload to
-# reach RTOL (oracle.fgmres.solve on the same right-hand side); used to
+# the timed smoother: the locally multiplicative sweep on this many finest
+# levels (additive below); 0 = additive everywhere
+HEAD_MULT = 1
+# FGMRES iterations the oracle's float64 algorithm with that smoother needs on
+# each seeded workload to reach RTOL (oracle.fgmres.solve with
+# gmg.Hierarchy(p, mult_levels=1) on the same right-hand side); used to
 # project the oracle's per-iteration time to the metric.
-ORACLE_ITERATIONS = {0: 22, 1: 40, 4: 31}
+ORACLE_ITERATIONS = {0: 12, 1: 24, 4: 18}
 
 
 def parse():
@@ -122,7 +129,7 @@ def oracle_sample(cfg: int, iters: int, steps: int = 1, warmup: int = 0):
     from paper_1909_13201_gb300 import inputs as I
     p = I.make_config(cfg)
     t0 = time.time()
-    H = gmg.Hierarchy(p)
+    H = gmg.Hierarchy(p, mult_levels=HEAD_MULT)
     setup_s = time.time() - t0
     b = oracle_rhs(p)
     per_it, cpu_it = [], []
@@ -261,23 +268,25 @@ def device_code_sha(path):
     return hashlib.sha256("".join(text).encode()).hexdigest()[:16]
 
 
-def ncu_traffic():
-    """Per-launch DRAM bytes of the fine smoother apply from the committed ncu
-    summary, valid only while the kernels' device code is unchanged."""
-    path = os.path.join(ROOT, "profiles", "block_apply_h_c1_mixed_half.md")
-    src = os.path.join(ROOT, "paper_1909_13201_gb300", "csrc", "kernels_block.cu")
+def ncu_traffic(summary="sweep_fine_c1_mult_half.md", key="dram bytes per sweep",
+                sources=("kernels_block.cu", "kernels_sparse.cu")):
+    """DRAM bytes per unit of the roofline's kernel(s) from a committed ncu
+    summary, valid only while the device code of every source it covers is
+    unchanged (the summary records each source's sha)."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
-    sha = device_code_sha(src)
     vals = {}
     for line in open(path):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             vals[k.strip()] = v.strip().split()[0]
-    if vals.get("kernels_block.cu device code sha256[:16]") != sha:
-        return None
+    for src in sources:
+        sha = device_code_sha(os.path.join(ROOT, "paper_1909_13201_gb300", "csrc", src))
+        if vals.get(f"{src} device code sha256[:16]") != sha:
+            return None
     try:
-        return float(vals["dram bytes per launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -335,9 +344,10 @@ def run_ours(args, rank, world, local):
         t = timed(k, fn)
         return t, its_summary(its_log)
 
-    # ---- mixed precision with float16 block-inverse storage (headline)
+    # ---- headline: mixed precision, float16 block inverses, the locally
+    # multiplicative sweep (Sec. 3.2) on the finest level, additive below
     t0 = time.time()
-    s.setup_smoothers(precision=FSI_MIXED_HALF)
+    s.setup_smoothers(precision=FSI_MIXED_HALF, mult_levels=HEAD_MULT)
     torch.cuda.synchronize()
     setup_mixed_s = time.time() - t0
     for _ in range(args.warmup):
@@ -351,7 +361,7 @@ def run_ours(args, rank, world, local):
     ms, its_mixed = timed_its(args.steps, solve_dev)
     clk = clocks.stop()
     st_mixed = dict(stats)
-    # roofline of the fine smoother and launch count, from profiled solves
+    # roofline of the fine-level sweep and launch count, from profiled solves
     s.profile(1)
     for _ in range(2):
         solve_dev()
@@ -403,7 +413,7 @@ def run_ours(args, rank, world, local):
     fact["tf32_peak_tflops"] = tf32_peak
     # ---- mixed precision with float32 block inverses
     t0 = time.time()
-    s.setup_smoothers(precision=FSI_MIXED)
+    s.setup_smoothers(precision=FSI_MIXED, mult_levels=HEAD_MULT)
     torch.cuda.synchronize()
     setup_f32_s = time.time() - t0
     solve_dev()
@@ -411,7 +421,7 @@ def run_ours(args, rank, world, local):
     st32 = dict(stats)
     # ---- all-float64 path on the same system
     t0 = time.time()
-    s.setup_smoothers(precision=FSI_FP64)
+    s.setup_smoothers(precision=FSI_FP64, mult_levels=HEAD_MULT)
     torch.cuda.synchronize()
     setup_fp64_s = time.time() - t0
     solve_dev()
@@ -433,16 +443,29 @@ def run_ours(args, rank, world, local):
     ms_as, its_as = timed_its(max(2, args.steps // 4), solve_as)
     st_as = dict(stats)
 
-    # ---- the locally multiplicative sweep (Sec. 3.2) on the finest level,
-    # additive below; FP16 inverses from tensor-core factors as the headline
+    # ---- the additive field-split smoother on every level (same storage)
     t0 = time.time()
-    s.setup_smoothers(precision=FSI_MIXED_HALF, mult_levels=1)
+    s.setup_smoothers(precision=FSI_MIXED_HALF, mult_levels=0)
     torch.cuda.synchronize()
-    setup_mult_s = time.time() - t0
+    setup_add_s = time.time() - t0
     for _ in range(max(args.warmup, 1)):
         solve_dev()
-    ms_mult, its_mult = timed_its(args.steps, solve_dev)
-    st_mult = dict(stats)
+    ms_add, its_add = timed_its(args.steps, solve_dev)
+    st_add = dict(stats)
+    s.profile(1)
+    for _ in range(2):
+        solve_dev()
+    prof_add = s.profile(0)
+    sm_add_ms = prof_add["smoother_ms"] / max(prof_add["smoother_launches"], 1)
+    sm_add_gbs = prof_add["smoother_bytes"] / (sm_add_ms * 1e-3) / 1e9
+    # ---- the swapped cascade (Sec. 5 future work): FGMRES preconditioned by
+    # the field split, a GMG V-cycle inside each field system
+    t0 = time.time()
+    s.setup_smoothers(precision=FSI_MIXED_HALF, mult_levels=HEAD_MULT, cascade=True)
+    torch.cuda.synchronize()
+    setup_casc_s = time.time() - t0
+    solve_dev()
+    ms_casc, its_casc = timed_its(max(2, args.steps // 4), solve_dev)
 
     # ---- batched: 64 independent uneven 2D systems solved together
     batch = I.make_config(3)
@@ -551,13 +574,18 @@ def run_ours(args, rank, world, local):
                         "iterations": its_as, "converged": bool(st_as.get("converged")),
                         "rel_residual": st_as.get("rel_residual"), "setup_s": setup_as_s,
                         "fs_speedup_over_as": ms_as / ms},
-        "multiplicative_fine": {"what": "FS with the locally multiplicative Schwarz sweep per field system "
-                                        "(Sec. 3.2, the paper's AS1/AS2 within a process) on the finest level, "
-                                        "additive on the coarser levels; mixed precision, FP16 inverses",
-                                "value": job_throughput(n, ms_mult, world), "ms_per_step": ms_mult,
-                                "iterations": its_mult, "converged": bool(st_mult.get("converged")),
-                                "rel_residual": st_mult.get("rel_residual"), "setup_s": setup_mult_s,
-                                "speedup_over_additive": ms / ms_mult},
+        "additive": {"what": "the additive field-split smoother on every level (partition-of-unity weights, "
+                             "owner-computes combination); mixed precision, FP16 inverses",
+                     "value": job_throughput(n, ms_add, world), "ms_per_step": ms_add, "iterations": its_add,
+                     "converged": bool(st_add.get("converged")), "setup_s": setup_add_s,
+                     "mult_speedup_over_additive": ms_add / ms,
+                     "smoother_fine": {"mean_launch_ms": sm_add_ms, "achieved_gbs": sm_add_gbs,
+                                       "frac": sm_add_gbs / peak,
+                                       "algorithmic_bytes_per_launch": prof_add["smoother_bytes"]}},
+        "cascade": {"what": "swapped cascade (Sec. 5 future work): FGMRES preconditioned by the field split, "
+                            "each field system by its own GMG V-cycle with the same smoothing",
+                    "value": job_throughput(n, ms_casc, world), "ms_per_step": ms_casc, "iterations": its_casc,
+                    "setup_s": setup_casc_s, "slowdown_vs_headline": ms_casc / ms},
         "batched": {"systems": len(batch), "unknowns_total": batch_dofs, "ms_per_batch": ms_batch,
                     "ms_per_batch_patch3": ms_batch_fixed,
                     "autotune": {"candidates": list(tune_cand), "chosen_by_n_fine": chosen_by_size,
@@ -583,8 +611,8 @@ def run_ours(args, rank, world, local):
         "setup_s": {"hierarchy": setup_hier_s, "smoothers_mixed_half": setup_mixed_s,
                     "smoothers_mixed_f32": setup_f32_s, "smoothers_fp64": setup_fp64_s},
         "e2e_iterations": its_e2e,
-        "kernels": {"smoother_fine": {"achieved_gbs": achieved, "frac": achieved / peak, "mean_launch_ms": sm_ms,
-                                      "algorithmic_bytes_per_launch": prof["smoother_bytes"]},
+        "kernels": {"sweep_fine": {"achieved_gbs": achieved, "frac": achieved / peak, "mean_sweep_ms": sm_ms,
+                                   "algorithmic_bytes_per_sweep": prof["smoother_bytes"]},
                     "spmv_fine": {"achieved": spmv_gbs, "frac": spmv_gbs / peak, "mean_launch_ms": spmv_ms},
                     "restriction_fine": {"achieved": rst_gbs, "frac": rst_gbs / peak, "mean_launch_ms": rst_ms},
                     "prolongation_fine": {"achieved": pro_gbs, "frac": pro_gbs / peak, "mean_launch_ms": pro_ms},
@@ -615,11 +643,13 @@ def run_ours(args, rank, world, local):
                    "rtol": RTOL, "parallelism": f"replicas x{world}", "l2": "inputs > L2, no flush"},
         "iterations": its_mixed,
         "fp64": {"ms_per_step": round(ms64, 3), "its": its64["median"], "speedup_mixed": round(ms64 / ms, 3)},
-        "mult_fine": {"ms_per_step": round(ms_mult, 3), "its": its_mult["median"]},
+        "additive": {"ms_per_step": round(ms_add, 3), "its": its_add["median"]},
+        "cascade": {"ms_per_step": round(ms_casc, 3), "its": its_casc["median"]},
         "as": {"ms_per_step": round(ms_as, 3), "its": its_as["median"]},
         "e2e": {"value": job_throughput(n, ms_e2e, world), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
-        "roofline": {"bound": "hbm", "kernel": "block_apply_h_pipe_kernel", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "fine-level sweep (12 apply + 11 residual passes, 2 streams)",
+                     "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": traffic},
         "gpu_launches": int(round(launches_per_step * args.steps)),

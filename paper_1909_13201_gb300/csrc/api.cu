@@ -1703,6 +1703,18 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
         blk += nj * nj * is + nj * (4.0 + ts + ts + 2.0 * ts + rowx);   // inverse, idx, weight, gather r, x RMW
     }
     blk += (double)F.n_jac * (4.0 + ts + ts + 2.0 * ts);
+    if (F.mult) {
+        // a multiplicative sweep adds the pass residuals r - A_FF y on the rows
+        // of every pass but the first of each field (A_FF entries with their
+        // column indices; perm, b, y and rr per row) and the closing
+        // x += omega y with y cleared
+        bool started[2] = {false, false};
+        for (const auto &P : F.passes) {
+            if (started[P.field]) blk += (double)P.ell.nnz * (ts + 4.0) + (double)P.rows.size() * (4.0 + 3.0 * ts);
+            started[P.field] = true;
+        }
+        blk += (double)F.n * 4.0 * ts;
+    }
     const double spmv = (double)F.A.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)F.n * 3.0 * ts;
     out[0] = (double)cx->prof_n[0];
     out[1] = cx->prof_ms[0];

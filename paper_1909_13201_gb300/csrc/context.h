@@ -115,6 +115,7 @@ struct DevEll {
     int G = 1;                      // lanes per row (slab = 32 / G rows)
     bool stream = true;             // evict-first loads (operators far larger than L2 share)
     int64_t nslabs = 0, size = 0;   // slabs (warps), stored entries (with padding)
+    int64_t nnz = 0;                // entries of the operator (without padding)
     DevBuf bins;                    // EllBin[nbins]
     DevBuf perm;                    // int32[n_rows]: CSR row of each sorted position
     DevBuf col;                     // int32[size]

@@ -539,6 +539,7 @@ fsi_status build_ell_subset(const DevCSR &A, const HostCSR &pat, const std::vect
     E.nbins = (int)bins.size();
     E.nslabs = slabs;
     E.size = off;
+    E.nnz = nnz;
     FSI_TRY(E.bins.alloc(bins.size() * sizeof(EllBin)));
     FSI_CUDA(cudaMemcpyAsync(E.bins.p, bins.data(), bins.size() * sizeof(EllBin), cudaMemcpyHostToDevice, s));
     FSI_TRY(E.perm.alloc((size_t)n * 4));

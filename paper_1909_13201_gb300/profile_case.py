@@ -1,6 +1,6 @@
 """Run a few solves of one workload, for profiler captures (ncu).
 
-    python -m paper_1909_13201_gb300.profile_case --config 4 --precision half --solves 2
+    python -m paper_1909_13201_gb300.profile_case --config 4 --precision half --solves 2 --mult-levels 1
 
 Builds nothing and times nothing: it sets up the hierarchy and smoothers of
 the chosen workload and runs `--solves` FGMRES solves to 1e-8 from zero, so a
@@ -19,6 +19,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed", "half"], default="half")
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--mult-levels", type=int, default=0,
+                    help="finest levels smoothed by the multiplicative sweep (0: additive)")
     a = ap.parse_args()
     import torch
 
@@ -27,7 +29,7 @@ def main():
     prec = {"fp64": FSI_FP64, "mixed": FSI_MIXED, "half": FSI_MIXED_HALF}[a.precision]
     p = I.make_config(a.config)
     s = FSISolver(p)
-    s.setup_smoothers(precision=prec)
+    s.setup_smoothers(precision=prec, mult_levels=a.mult_levels)
     lv = p.n_levels - 1
     f, c, nd = s.dof_map(lv)
     b = torch.from_numpy(I.gather_natural(I.natural_vector(p, 1), f.astype(np.int64), c.astype(np.int64),
