@@ -361,6 +361,9 @@ def run_ours(args, rank, world, local):
     ms, its_mixed = timed_its(args.steps, solve_dev)
     clk = clocks.stop()
     st_mixed = dict(stats)
+    # whole solve against the HBM roofline: algorithmic bytes of every V-cycle,
+    # outer product and Gram-Schmidt pass of the timed solve (fsi_get_cost)
+    solve_bytes = s.solve_bytes(its_mixed["median"])
     # roofline of the fine-level sweep and launch count, from profiled solves
     s.profile(1)
     for _ in range(2):
@@ -495,8 +498,13 @@ def run_ours(args, rank, world, local):
     chosen, _ = sb.autotune(tune_cand, rtol=RTOL)
     torch.cuda.synchronize()
     tune_s = time.time() - t0
+    # lanes per row of the sparse copies, timed on the whole batch (native autotuner)
+    t0 = time.time()
+    lanes_chosen, lanes_times = sb.autotune_layout((0, 1, 4), rtol=RTOL)
+    tune_layout_s = time.time() - t0
     solve_batch()
     ms_batch = timed(max(2, args.steps // 4), solve_batch)
+    batch_bytes = sum(sb.solve_bytes(t["iterations"], prob=k) for k, t in enumerate(bstats))
     chosen_by_size = {str(q.n_fine): c for q, c in zip(batch, chosen)}
     batch_dofs = sum(int(v.numel()) for v in bb)
     # ---- adjoint: forward solve plus the transposed solve with gradients (128^2)
@@ -563,7 +571,10 @@ def run_ours(args, rank, world, local):
     detail = {
         "detail": "legs of the bench run (the result line follows)",
         "mixed_half": {"ms_per_step": ms, "iterations": its_mixed, "rho": st_mixed.get("rho"),
-                       "rel_residual": st_mixed.get("rel_residual")},
+                       "rel_residual": st_mixed.get("rel_residual"),
+                       "solve_hbm": {"algorithmic_bytes": solve_bytes,
+                                     "achieved_gbs": solve_bytes / (ms * 1e-3) / 1e9,
+                                     "frac": solve_bytes / (ms * 1e-3) / 1e9 / peak}},
         "fp64": {"value": job_throughput(n, ms64, world), "ms_per_step": ms64, "iterations": its64,
                  "speedup_mixed_over_fp64": ms64 / ms},
         "mixed_f32_inverses": {"value": job_throughput(n, ms32, world), "ms_per_step": ms32, "iterations": its32},
@@ -589,12 +600,20 @@ def run_ours(args, rank, world, local):
         "batched": {"systems": len(batch), "unknowns_total": batch_dofs, "ms_per_batch": ms_batch,
                     "ms_per_batch_patch3": ms_batch_fixed,
                     "autotune": {"candidates": list(tune_cand), "chosen_by_n_fine": chosen_by_size,
-                                 "tune_s": tune_s},
+                                 "tune_s": tune_s,
+                                 "ell_lanes": {"candidates": [0, 1, 4], "chosen": lanes_chosen,
+                                               "batch_ms": lanes_times, "tune_s": tune_layout_s,
+                                               "note": "0 = size rule (1 lane per row inside a batch)"}},
                     "solves_per_s": job_throughput(len(batch), ms_batch, world),
                     "dof_per_s": job_throughput(batch_dofs, ms_batch, world),
                     "iterations_min_max": [min(t["iterations"] for t in bstats),
                                            max(t["iterations"] for t in bstats)],
                     "all_converged": all(t["converged"] for t in bstats), "setup_s": setup_batch_s,
+                    "hbm": {"algorithmic_bytes": batch_bytes,
+                            "achieved_gbs": batch_bytes / (ms_batch * 1e-3) / 1e9,
+                            "frac": batch_bytes / (ms_batch * 1e-3) / 1e9 / peak,
+                            "how": "sum over systems of its Arnoldi steps x (V-cycle + float64 outer product "
+                                   "+ Gram-Schmidt bytes), fsi_get_cost; one graph launch for all systems"},
                     "workload": "64 seeded 2D channels, fine grids {32,48,64,96,128}^2, band width U[0.1,0.4]"},
         "valve3d": {"workload": p3.name, "unknowns": n3, "ms_per_solve": ms_3d,
                     "dof_per_s": job_throughput(n3, ms_3d, world), "iterations": its_3d,
@@ -652,6 +671,8 @@ def run_ours(args, rank, world, local):
                      "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": traffic},
+        "solve_hbm_frac": round(solve_bytes / (ms * 1e-3) / 1e9 / peak, 3),
+        "batched": {"ms": round(ms_batch, 2), "hbm_frac": round(batch_bytes / (ms_batch * 1e-3) / 1e9 / peak, 3)},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind")} |

@@ -304,10 +304,36 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * Gram-Schmidt passes are timed in host-driven solves only (solves run
  * host-driven while recording).  On a fine level with the multiplicative
  * sweep (mult_levels) a timed "smoother launch" is the whole sweep (its pass
- * residuals and applies), while [2] still counts only the inverse, index and
- * vector bytes of all blocks: [2] / ([1] / [0]) then understates the
- * bandwidth of the apply kernels.  Problem 0. */
+ * residuals, applies and closing update) and [2] counts the sweep's bytes:
+ * the blocks' inverse, index and vector bytes, the A_FF entries and row
+ * vectors of every pass residual and the closing x += omega y.  Problem 0. */
 fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out);
+
+/* fsi_autotune_layout -- picks the lanes per row of every binned-ELL copy
+ * (level operators, transfers and their transposes): for each candidate in
+ * lanes[0..n_lanes) (0: the size rule -- one lane per row for large
+ * operators and inside a batch, up to 16 for small ones alone; or 1, 4, 8,
+ * 16 for every copy) it rebuilds the copies and times a solve of every
+ * problem of the context at once (b = A 1, options opts, the second of two
+ * runs, host clock); keeps the fastest.  chosen: host int, the lanes value
+ * kept; times_ms: host array of n_lanes (nullable; 1e300 for a candidate
+ * whose solves did not converge).  An extension: the paper's data layout is
+ * PETSc's CSR.  Captured graphs are rebuilt on the next solve. */
+fsi_status fsi_autotune_layout(fsi_ctx *ctx, const int *lanes, int n_lanes, const fsi_solve_opts *opts, int *chosen,
+                               double *times_ms);
+
+/* fsi_get_cost -- algorithmic bytes of one solve's parts for problem `prob`
+ * (an extension for roofline accounting; the paper reports times only):
+ * cost[0] one V-cycle from zero on the fine level (per level: two smoothing
+ * steps as counted by fsi_profile [2], two residual products, restriction
+ * and prolongation; the coarse inverse GEMV; the mixed modes' casts),
+ * cost[1] one float64 outer product w = A z, cost[2] the Gram-Schmidt bytes
+ * per basis vector of one Arnoldi step (the three fused passes read each
+ * vector in float32 and twice in float64: 20 B per entry; FP64 mode 24 B),
+ * cost[3] fine-level unknowns.  One Arnoldi step j costs cost[0] + cost[1] +
+ * (j + 1) cost[2].  cost: host array of 4.  FSI_ERR_STATE before
+ * fsi_setup_smoothers. */
+fsi_status fsi_get_cost(fsi_ctx *ctx, int prob, double *cost);
 
 /* Host-only inspection context: builds the levels, numbering, operator
  * sparsity patterns, transfers and (for patch >= 1) the Schwarz block index

@@ -26,6 +26,7 @@ EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solv
             "fsi_adjoint", "fsi_get_sizes", "fsi_get_dof_map", "fsi_get_matrix", "fsi_get_transfer",
             "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
             "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_apply_smoother_noalloc",
+            "fsi_get_cost", "fsi_autotune_layout",
             "fsi_autotune", "fsi_get_block_passes", "fsi_destroy", "fsi_last_error"]
 
 
@@ -105,6 +106,8 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     lib.fsi_get_pattern.argtypes = [P, I, I, C.POINTER(I64), C.POINTER(I32)]
     lib.fsi_profile.argtypes = [P, I, C.POINTER(D)]
     lib.fsi_apply_smoother_noalloc.argtypes = [P, I, I, P, P, I]
+    lib.fsi_get_cost.argtypes = [P, I, C.POINTER(D)]
+    lib.fsi_autotune_layout.argtypes = [P, C.POINTER(I), I, C.POINTER(SolveOpts_t), C.POINTER(I), C.POINTER(D)]
     lib.fsi_autotune.argtypes = [P, C.POINTER(I), I, C.POINTER(SolveOpts_t), C.POINTER(I), C.POINTER(D)]
     lib.fsi_destroy.argtypes = [P]
     lib.fsi_destroy.restype = None
@@ -257,6 +260,18 @@ class FSISolver:
                                            _ptr(times, C.c_double)))
         return list(chosen), times.reshape(n, len(candidates))
 
+    def autotune_layout(self, lanes=(0, 1, 4), rtol=1e-8, restart=30, max_iters=300):
+        """Lanes per row of the sparse copies (fsi_autotune_layout): times a
+        solve of every problem at once per candidate and keeps the fastest.
+        Returns (chosen, times_ms)."""
+        cand = (C.c_int * len(lanes))(*lanes)
+        chosen = C.c_int(0)
+        times = np.zeros(len(lanes), np.float64)
+        opts = self._opts(rtol, restart, max_iters, False)
+        _check(load_library().fsi_autotune_layout(self.ctx, cand, len(lanes), C.byref(opts), C.byref(chosen),
+                                                  _ptr(times, C.c_double)))
+        return chosen.value, times.tolist()
+
     def profile(self, mode):
         """mode 1 start (reset), 0 stop, 2 read, 3 read and measure the
         float64 FMA rate.  Returns the counters of fsi_profile as a dict."""
@@ -298,6 +313,21 @@ class FSISolver:
         _check(load_library().fsi_get_matrix(self.ctx, prob, level, _ptr(ptr, C.c_int64), _ptr(col, C.c_int32),
                                              _ptr(val, C.c_double)))
         return ptr, col, val
+
+    def cost(self, prob=0):
+        """Algorithmic bytes of one V-cycle, one float64 outer product, the
+        Gram-Schmidt bytes per basis vector, and the fine unknowns
+        (fsi_get_cost)."""
+        out = (C.c_double * 4)()
+        _check(load_library().fsi_get_cost(self.ctx, prob, out))
+        return {"cycle_bytes": out[0], "outer_bytes": out[1], "gs_bytes_per_vector": out[2], "n": int(out[3])}
+
+    def solve_bytes(self, iterations, restart=30, prob=0):
+        """Algorithmic bytes of a solve of `iterations` Arnoldi steps:
+        sum over steps j (mod restart) of cycle + outer + (j + 1) GS."""
+        c = self.cost(prob)
+        gs = sum((j % restart) + 1 for j in range(int(iterations)))
+        return int(iterations) * (c["cycle_bytes"] + c["outer_bytes"]) + gs * c["gs_bytes_per_vector"]
 
     def operator_values(self, level=None, prob=0, device="cuda"):
         """The operator's values (CSR order of matrix()) as a float64 torch

@@ -293,7 +293,15 @@ fsi_status vcycle(Context &cx, Problem &pb, int l, const T *b, T *x, bool tr, bo
 }
 
 // ------------------------------------------------------------ workspace
+// duration of the last batch-graph launch (every system of the batch reports it)
+float batch_ms_last = 0.f;
+
+// bumped whenever a problem's graphs are dropped (workspace or smoothers
+// changed): a batch graph captured under an older epoch is stale
+std::atomic<int64_t> g_graph_epoch{0};
+
 void drop_graphs(Problem &pb) {
+    ++g_graph_epoch;
     for (auto &v : pb.graphs) {
         for (auto &ge : v)
             if (ge) cudaGraphExecDestroy(ge);
@@ -668,13 +676,13 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
         FSI_TRY(download_csr(L.A, A, s));
         transpose_csr(A, AT);
         FSI_TRY(upload_csr(L.AT, AT, s));
-        FSI_TRY(build_ell(L.AT, s, cx.probs.size() > 1));
+        FSI_TRY(build_ell(L.AT, s, cx.probs.size() > 1, cx.ell_lanes));
         if (cx.cascade) {
             HostCSR Ac, ATc;
             FSI_TRY(download_csr(L.Ac, Ac, s));
             transpose_csr(Ac, ATc);
             FSI_TRY(upload_csr(L.ATc, ATc, s));
-            FSI_TRY(build_ell(L.ATc, s, cx.probs.size() > 1));
+            FSI_TRY(build_ell(L.ATc, s, cx.probs.size() > 1, cx.ell_lanes));
             L.ATc.val32.release();
             if (cx.precision != FSI_FP64) FSI_TRY(make_f32(L.ATc, s));
             if (l >= 1) {
@@ -682,7 +690,7 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
                 FSI_TRY(download_csr(L.Rc, Rc, s));
                 transpose_csr(Rc, RTc);
                 FSI_TRY(upload_csr(L.RTc, RTc, s));
-                FSI_TRY(build_ell(L.RTc, s, cx.probs.size() > 1));
+                FSI_TRY(build_ell(L.RTc, s, cx.probs.size() > 1, cx.ell_lanes));
                 L.RTc.val32.release();
                 if (cx.precision != FSI_FP64) FSI_TRY(make_f32(L.RTc, s));
             }
@@ -693,8 +701,8 @@ fsi_status build_transposes(Context &cx, Problem &pb) {
             transpose_csr(pb.hR[l], RT);
             FSI_TRY(upload_csr(L.PT, PT, s));
             FSI_TRY(upload_csr(L.RT, RT, s));
-            FSI_TRY(build_ell(L.PT, s, cx.probs.size() > 1));
-            FSI_TRY(build_ell(L.RT, s, cx.probs.size() > 1));
+            FSI_TRY(build_ell(L.PT, s, cx.probs.size() > 1, cx.ell_lanes));
+            FSI_TRY(build_ell(L.RT, s, cx.probs.size() > 1, cx.ell_lanes));
         }
         if (cx.precision != FSI_FP64) {
             FSI_TRY(make_f32(L.AT, s));
@@ -779,15 +787,15 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
         FSI_TRY(upload_csr(D.A, H.pattern, s));
         FSI_TRY(D.A.val64.alloc((size_t)D.A.nnz * 8));
         FSI_TRY(launch_assemble(H, d, ref, D.A, false, D.A.val64.as<double>(), s));
-        FSI_TRY(build_ell(D.A, s, cx.probs.size() > 1));
+        FSI_TRY(build_ell(D.A, s, cx.probs.size() > 1, cx.ell_lanes));
         FSI_TRY(upload(D.fixed, H.fixed.data(), H.fixed.size(), s));
         if (l >= 1) {
             build_prolongation(H, pb.host[l - 1], pb.hP[l]);
             build_restriction(pb.hP[l], H, pb.host[l - 1], cx.restriction == 1, pb.hR[l]);
             FSI_TRY(upload_csr(D.P, pb.hP[l], s));
             FSI_TRY(upload_csr(D.R, pb.hR[l], s));
-            FSI_TRY(build_ell(D.P, s, cx.probs.size() > 1));
-            FSI_TRY(build_ell(D.R, s, cx.probs.size() > 1));
+            FSI_TRY(build_ell(D.P, s, cx.probs.size() > 1, cx.ell_lanes));
+            FSI_TRY(build_ell(D.R, s, cx.probs.size() > 1, cx.ell_lanes));
         }
     }
     // dA/dmu_s on the fine pattern (adjoint gradient)
@@ -843,7 +851,7 @@ fsi_status build_cascade(Context &cx, Problem &pb) {
         HostCSR A;
         FSI_TRY(download_csr(L.A, A, s));
         FSI_TRY(upload_csr(L.Ac, split_systems(A, H.off[3], H.off[3]), s));
-        FSI_TRY(build_ell(L.Ac, s, conc));
+        FSI_TRY(build_ell(L.Ac, s, conc, cx.ell_lanes));
         L.Ac.val32.release();
         if (l >= 1) {
             const LevelHost &Hc = pb.host[l - 1];
@@ -855,7 +863,7 @@ fsi_status build_cascade(Context &cx, Problem &pb) {
                         return FSI_ERR_STATE;
                     }
             FSI_TRY(upload_csr(L.Rc, split_systems(pb.hR[l], Hc.off[3], H.off[3]), s));
-            FSI_TRY(build_ell(L.Rc, s, conc));
+            FSI_TRY(build_ell(L.Rc, s, conc, cx.ell_lanes));
             L.Rc.val32.release();
         }
     }
@@ -1360,8 +1368,11 @@ fsi_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGra
     return FSI_OK;
 }
 
+// One problem's whole solve captured into `top` as a chain with no
+// dependencies (a root of the graph); cnt_out: kernels in the prologue, per
+// restart cycle outside the steps, per Arnoldi step.
 template <class T>
-fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
+fsi_status capture_chain(Context &cx, Problem &pb, bool tr, int m, cudaGraph_t top, int64_t cnt_out[3]) {
     LevelDev &F = pb.dev.back();
     const int64_t n = F.n;
     const DevCSR &A = tr ? F.AT : F.A;
@@ -1370,8 +1381,6 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
     double *b = pb.bbuf.as<double>(), *x = pb.xbuf.as<double>();
     cudaStream_t s0 = pb.stream, s1 = cx.cap[0], s2 = cx.cap[1], s3 = cx.cap[2];
     cudaStream_t saved = cx.stream;
-    cudaGraph_t top = nullptr;
-    cudaGraphExec_t exec = nullptr;
     int64_t cnt[3] = {0, 0, 0};
     fsi_status st = FSI_OK;
     int capturing = 0;        // streams in capture, innermost last
@@ -1383,7 +1392,6 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
             cudaStreamEndCapture(active[i], &junk);
         }
         cudaGetLastError();
-        if (top) cudaGraphDestroy(top);
         cx.stream = saved;
         return e;
     };
@@ -1401,7 +1409,6 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
         }                                              \
     } while (0)
     const int64_t c0 = launches_so_far();
-    FSI_CAPCUDA(cudaGraphCreate(&top, 0));
     cudaGraphConditionalHandle h_out = 0, h_in = 0;
     FSI_CAPCUDA(cudaGraphConditionalHandleCreate(&h_out, top, 0, cudaGraphCondAssignDefault));
     // prologue
@@ -1475,14 +1482,30 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
         capturing = 0;
     }
     cx.stream = saved;
-    FSI_CAPCUDA(cudaGraphInstantiate(&exec, top, 0));
-    cudaGraphDestroy(top);
 #undef FSI_CAP
 #undef FSI_CAPCUDA
     cnt[0] = c1 - c0;                       // prologue
     cnt[1] = (c2 - c1) + (c4 - c3);         // per cycle, outside the steps
     cnt[2] = (c3 - c2) - (int64_t)(ncls - 1) * tail_kernels;   // per Arnoldi step (one case runs)
     count_launch(-(int)(c4 - c0));          // captured, not run
+    for (int i = 0; i < 3; ++i) cnt_out[i] = cnt[i];
+    (void)cnt;
+    return FSI_OK;
+}
+
+template <class T>
+fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
+    cudaGraph_t top = nullptr;
+    FSI_CUDA(cudaGraphCreate(&top, 0));
+    int64_t cnt[3] = {0, 0, 0};
+    fsi_status st = capture_chain<T>(cx, pb, tr, m, top, cnt);
+    cudaGraphExec_t exec = nullptr;
+    if (st == FSI_OK && cudaGraphInstantiate(&exec, top, 0) != cudaSuccess) {
+        set_error("cudaGraphInstantiate of the solve graph failed");
+        st = FSI_ERR_CUDA;
+    }
+    cudaGraphDestroy(top);
+    FSI_TRY(st);
     const int d = tr ? 1 : 0;
     if (pb.solve_graph[d]) cudaGraphExecDestroy(pb.solve_graph[d]);
     pb.solve_graph[d] = exec;
@@ -1491,40 +1514,105 @@ fsi_status capture_solve(Context &cx, Problem &pb, bool tr, int m) {
     return FSI_OK;
 }
 
+// Every problem of a batch in one graph: one root chain per problem (its
+// prologue and restart/Arnoldi WHILE loops, conditions on its own control
+// block), so one launch solves all systems and each stops on its own test.
+template <class T>
+fsi_status capture_batch(Context &cx, bool tr, int m) {
+    cudaGraph_t top = nullptr;
+    FSI_CUDA(cudaGraphCreate(&top, 0));
+    const int d = tr ? 1 : 0;
+    fsi_status st = FSI_OK;
+    for (auto &pb : cx.probs) {
+        int64_t cnt[3] = {0, 0, 0};
+        st = capture_chain<T>(cx, pb, tr, m, top, cnt);
+        if (st != FSI_OK) break;
+        for (int i = 0; i < 3; ++i) pb.graph_counts[d][i] = cnt[i];
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (st == FSI_OK && cudaGraphInstantiate(&exec, top, 0) != cudaSuccess) {
+        set_error("cudaGraphInstantiate of the batch graph failed");
+        st = FSI_ERR_CUDA;
+    }
+    cudaGraphDestroy(top);
+    FSI_TRY(st);
+    if (cx.batch_graph[d]) cudaGraphExecDestroy(cx.batch_graph[d]);
+    cx.batch_graph[d] = exec;
+    cx.batch_graph_m[d] = m;
+    cx.batch_epoch[d] = g_graph_epoch.load();
+    return FSI_OK;
+}
+
 template <class T>
 fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
     cudaStream_t user = cx.stream;
     FSI_CUDA(cudaMemsetAsync(cx.flags.as<int>() + 2, 0, 4, user));   // kernel error word
     FSI_CUDA(cudaEventRecord(cx.ev_in, user));
+    // a batch over every problem of the context in one graph
+    const bool batch = runs.size() > 1 && runs.size() == cx.probs.size();
+    const int bd = runs[0].tr ? 1 : 0, bm = runs[0].o.restart;
+    if (batch) {
+        for (auto &R : runs) {
+            Problem &pb = *R.pb;
+            FSI_TRY(ensure_workspace(cx, pb, bm));
+            if (!pb.bbuf.p) {
+                const int64_t n = pb.dev.back().n;
+                FSI_TRY(pb.bbuf.alloc((size_t)n * 8));
+                FSI_TRY(pb.xbuf.alloc((size_t)n * 8));
+                FSI_TRY(pb.zbuf.alloc((size_t)n * 8));
+            }
+        }
+        if (!cx.batch_graph[bd] || cx.batch_graph_m[bd] != bm || cx.batch_epoch[bd] != g_graph_epoch.load())
+            FSI_TRY(capture_batch<T>(cx, runs[0].tr, bm));
+    }
     for (auto &R : runs) {
         Problem &pb = *R.pb;
         const int m = R.o.restart;
         const int d = R.tr ? 1 : 0;
         const int64_t n = pb.dev.back().n;
-        FSI_TRY(ensure_workspace(cx, pb, m));
-        if (!pb.bbuf.p) {
-            FSI_TRY(pb.bbuf.alloc((size_t)n * 8));
-            FSI_TRY(pb.xbuf.alloc((size_t)n * 8));
-            FSI_TRY(pb.zbuf.alloc((size_t)n * 8));
+        if (!batch) {
+            FSI_TRY(ensure_workspace(cx, pb, m));
+            if (!pb.bbuf.p) {
+                FSI_TRY(pb.bbuf.alloc((size_t)n * 8));
+                FSI_TRY(pb.xbuf.alloc((size_t)n * 8));
+                FSI_TRY(pb.zbuf.alloc((size_t)n * 8));
+            }
+            FSI_CUDA(cudaStreamWaitEvent(pb.stream, cx.ev_in, 0));
+            if (!pb.solve_graph[d] || pb.solve_graph_m[d] != m) FSI_TRY(capture_solve<T>(cx, pb, R.tr, m));
         }
-        FSI_CUDA(cudaStreamWaitEvent(pb.stream, cx.ev_in, 0));
-        if (!pb.solve_graph[d] || pb.solve_graph_m[d] != m) FSI_TRY(capture_solve<T>(cx, pb, R.tr, m));
         R.st = fsi_solve_stats();
         FgState &in = pb.h_fg[0];
         in = FgState();
         in.rtol = R.o.rtol;
         in.max_iters = R.o.max_iters;
         in.m = m;
-        cudaStream_t s = pb.stream;
-        FSI_CUDA(cudaEventRecord(pb.ev_a, s));
+        cudaStream_t s = batch ? user : pb.stream;
+        if (!batch) FSI_CUDA(cudaEventRecord(pb.ev_a, s));
         FSI_CUDA(cudaMemcpyAsync(pb.fg.p, &in, sizeof(FgState), cudaMemcpyHostToDevice, s));
         FSI_CUDA(cudaMemcpyAsync(pb.bbuf.p, R.b, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
         if (R.o.use_x0) FSI_CUDA(cudaMemcpyAsync(pb.xbuf.p, R.x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
         else FSI_CUDA(cudaMemsetAsync(pb.xbuf.p, 0, (size_t)n * 8, s));
+        if (batch) continue;
         FSI_CUDA(cudaGraphLaunch(pb.solve_graph[d], s));
         FSI_CUDA(cudaMemcpyAsync(R.x, pb.xbuf.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
         FSI_CUDA(cudaMemcpyAsync(&pb.h_fg[1], pb.fg.p, sizeof(FgState), cudaMemcpyDeviceToHost, s));
         FSI_CUDA(cudaEventRecord(pb.ev_b, s));
+    }
+    if (batch) {
+        // one launch for every system; each chain stops on its own test
+        Problem &p0 = *runs[0].pb;
+        FSI_CUDA(cudaEventRecord(p0.ev_a, user));
+        FSI_CUDA(cudaGraphLaunch(cx.batch_graph[bd], user));
+        FSI_CUDA(cudaEventRecord(p0.ev_b, user));
+        for (auto &R : runs) {
+            Problem &pb = *R.pb;
+            FSI_CUDA(cudaMemcpyAsync(R.x, pb.xbuf.p, (size_t)pb.dev.back().n * 8, cudaMemcpyDeviceToDevice, user));
+            FSI_CUDA(cudaMemcpyAsync(&pb.h_fg[1], pb.fg.p, sizeof(FgState), cudaMemcpyDeviceToHost, user));
+        }
+        FSI_CUDA(cudaStreamSynchronize(user));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p0.ev_a, p0.ev_b);
+        batch_ms_last = ms;
     }
     fsi_status err = FSI_OK;
     for (auto &R : runs) {
@@ -1559,7 +1647,8 @@ fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
         }
         finish(R, status);
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pb.ev_a, pb.ev_b) == cudaSuccess) R.st.solve_ms = ms;
+        if (batch) R.st.solve_ms = batch_ms_last;
+        else if (cudaEventElapsedTime(&ms, pb.ev_a, pb.ev_b) == cudaSuccess) R.st.solve_ms = ms;
     }
     for (auto &R : runs) {
         FSI_CUDA(cudaEventRecord(cx.ev_out, R.pb->stream));
@@ -1571,12 +1660,68 @@ fsi_status run_device_loop(Context &cx, std::vector<Run> &runs) {
 }  // namespace
 }  // namespace fsi
 
+namespace fsi {
+namespace {
+// Algorithmic bytes (the data the method must move) of one smoothing step on
+// level L: every block's inverse (n^2 entries) with its index, weight,
+// gathered residual and updated correction entries (+ a float32 row scale
+// with FP16 storage), the Jacobi rows; a multiplicative sweep adds the pass
+// residuals r - A_FF y on the rows of every pass but the first of each field
+// (A_FF entries with their column indices; permutation index, b, y and rr
+// per row) and the closing x += omega y with y cleared.
+double smoother_bytes(const Context &cx, const LevelDev &L) {
+    const double ts = cx.precision != FSI_FP64 ? 4.0 : 8.0;
+    const double is = cx.precision == FSI_MIXED_HALF ? 2.0 : ts;
+    const double rowx = cx.precision == FSI_MIXED_HALF ? 4.0 : 0.0;
+    double b = 0.0;
+    for (int64_t j = 0; j + 1 < (int64_t)L.h_blk_ptr.size(); ++j) {
+        const double nj = (double)(L.h_blk_ptr[j + 1] - L.h_blk_ptr[j]);
+        b += nj * nj * is + nj * (4.0 + ts + ts + 2.0 * ts + rowx);
+    }
+    b += (double)L.n_jac * (4.0 + ts + ts + 2.0 * ts);
+    if (L.mult) {
+        bool started[2] = {false, false};
+        for (const auto &P : L.passes) {
+            if (started[P.field]) b += (double)P.ell.nnz * (ts + 4.0) + (double)P.rows.size() * (4.0 + 3.0 * ts);
+            started[P.field] = true;
+        }
+        b += (double)L.n * 4.0 * ts;
+    }
+    return b;
+}
+
+// one sparse product y = b - A x (or A x): values and column indices, row
+// pointers, x, b and y
+double spmv_bytes(const DevCSR &A, double ts) {
+    return (double)A.nnz * (ts + 4.0) + (double)(A.n_rows + 1) * 4.0 + (double)A.n_rows * 3.0 * ts;
+}
+
+// one V-cycle from a zero guess on the fine level (Sec. 3.2): per level l >= 1
+// two smoothing steps, two residuals (before restriction, before the
+// post-smoothing step), restriction and prolongation; the coarse inverse
+// GEMV; the fine-level casts of v and z in the mixed modes
+double cycle_bytes(const Context &cx, const Problem &pb) {
+    const double ts = cx.precision != FSI_FP64 ? 4.0 : 8.0;
+    double b = (double)pb.n0 * (double)pb.n0 * 8.0 + (double)pb.n0 * 2.0 * ts;
+    for (size_t l = 1; l < pb.dev.size(); ++l) {
+        const LevelDev &L = pb.dev[l];
+        const DevCSR &A = cx.cascade ? L.Ac : L.A;
+        const DevCSR &R = cx.cascade ? L.Rc : L.R;
+        b += 2.0 * smoother_bytes(cx, L) + 2.0 * spmv_bytes(A, ts) + spmv_bytes(R, ts) + spmv_bytes(L.P, ts);
+    }
+    if (cx.precision != FSI_FP64) b += (double)pb.dev.back().n * 2.0 * 12.0;
+    return b;
+}
+}  // namespace
+}  // namespace fsi
+
 extern "C" {
 
 // Hardware work queues of the context (CUDA_DEVICE_MAX_CONNECTIONS, default
 // 8).  Streams beyond that share queues, and a whole-solve graph then blocks
-// every solve queued behind it, so batches larger than this advance in
-// host-driven rounds of one Arnoldi step instead.
+// every solve queued behind it, so partial batches larger than this advance
+// in host-driven rounds of one Arnoldi step instead.  A batch over every
+// problem of the context is one graph launch (capture_batch).
 static int hw_queues() {
     const char *e = getenv("CUDA_DEVICE_MAX_CONNECTIONS");
     const int v = e ? atoi(e) : 0;
@@ -1584,7 +1729,9 @@ static int hw_queues() {
 }
 
 static fsi_status solve_runs(Context &cx, std::vector<Run> &runs) {
-    const bool dev_loop = cx.use_graphs && cx.device_loop && !cx.profile && (int)runs.size() <= hw_queues();
+    const bool whole = runs.size() > 1 && runs.size() == cx.probs.size();
+    const bool dev_loop = cx.use_graphs && cx.device_loop && !cx.profile &&
+                          ((int)runs.size() <= hw_queues() || whole);
     fsi_status s = dev_loop ? ((cx.precision != FSI_FP64) ? run_device_loop<float>(cx, runs)
                                                           : run_device_loop<double>(cx, runs))
                             : ((cx.precision != FSI_FP64) ? run_batch<float>(cx, runs) : run_batch<double>(cx, runs));
@@ -1695,27 +1842,8 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     const Problem &pb = cx->probs[0];
     const LevelDev &F = pb.dev.back();
     const double ts = cx->precision != FSI_FP64 ? 4.0 : 8.0;
-    const double is = cx->precision == FSI_MIXED_HALF ? 2.0 : ts;
-    const double rowx = cx->precision == FSI_MIXED_HALF ? 4.0 : 0.0;   // row scale
-    double blk = 0.0;
-    for (int64_t j = 0; j + 1 < (int64_t)F.h_blk_ptr.size(); ++j) {
-        const double nj = (double)(F.h_blk_ptr[j + 1] - F.h_blk_ptr[j]);
-        blk += nj * nj * is + nj * (4.0 + ts + ts + 2.0 * ts + rowx);   // inverse, idx, weight, gather r, x RMW
-    }
-    blk += (double)F.n_jac * (4.0 + ts + ts + 2.0 * ts);
-    if (F.mult) {
-        // a multiplicative sweep adds the pass residuals r - A_FF y on the rows
-        // of every pass but the first of each field (A_FF entries with their
-        // column indices; perm, b, y and rr per row) and the closing
-        // x += omega y with y cleared
-        bool started[2] = {false, false};
-        for (const auto &P : F.passes) {
-            if (started[P.field]) blk += (double)P.ell.nnz * (ts + 4.0) + (double)P.rows.size() * (4.0 + 3.0 * ts);
-            started[P.field] = true;
-        }
-        blk += (double)F.n * 4.0 * ts;
-    }
-    const double spmv = (double)F.A.nnz * (ts + 4.0) + (double)(F.n + 1) * 4.0 + (double)F.n * 3.0 * ts;
+    const double blk = smoother_bytes(*cx, F);
+    const double spmv = spmv_bytes(F.A, ts);
     out[0] = (double)cx->prof_n[0];
     out[1] = cx->prof_ms[0];
     out[2] = blk;
@@ -1752,6 +1880,120 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     out[26] = cx->prof_ms[7];
     out[27] = cx->prof_work[7];
     for (int k = 28; k < 32; ++k) out[k] = 0.0;
+    return FSI_OK;
+}
+
+}  // extern "C"
+
+namespace fsi {
+namespace {
+// Rebuild every binned-ELL copy of the context (level operators, transfers,
+// their transposes and the cascade's operators, when present) with
+// cx.ell_lanes lanes per row; captured graphs hold the old copies' pointers
+// and are dropped.
+fsi_status rebuild_ells(Context &cx) {
+    cudaStream_t s = cx.stream;
+    const bool conc = cx.probs.size() > 1;
+    auto one = [&](DevCSR &A) -> fsi_status {
+        if (A.nnz == 0 || !A.val64.p) return FSI_OK;
+        FSI_TRY(build_ell(A, s, conc, cx.ell_lanes));
+        A.ell.val32.release();
+        if (A.val32.p) FSI_TRY(ell_fill_f32(A, s));
+        return FSI_OK;
+    };
+    for (auto &pb : cx.probs) {
+        drop_graphs(pb);
+        for (auto &L : pb.dev) {
+            for (DevCSR *A : {&L.A, &L.AT, &L.P, &L.R, &L.PT, &L.RT, &L.Ac, &L.ATc, &L.Rc, &L.RTc}) FSI_TRY(one(*A));
+        }
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+}  // namespace
+}  // namespace fsi
+
+extern "C" {
+
+fsi_status fsi_autotune_layout(fsi_ctx *ctx, const int *lanes, int n_lanes, const fsi_solve_opts *opts, int *chosen,
+                               double *times_ms) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !lanes || n_lanes < 1 || n_lanes > 8 || !chosen) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (!cx->smoothers_ready) { set_error("fsi_setup_smoothers has not completed"); return FSI_ERR_STATE; }
+    FSI_TRY(check_opts(opts));
+    for (int c = 0; c < n_lanes; ++c)
+        if (!(lanes[c] == 0 || lanes[c] == 1 || lanes[c] == 4 || lanes[c] == 8 || lanes[c] == 16)) {
+            set_error("lanes per row must be 0 (size rule), 1, 4, 8 or 16");
+            return FSI_ERR_ARG;
+        }
+    DeviceGuard guard(cx->device);
+    cudaStream_t s = cx->stream;
+    const int np = (int)cx->probs.size();
+    // right-hand sides b = A * 1 per problem (set-up time memory)
+    std::vector<DevBuf> bv(np), xv(np);
+    for (int i = 0; i < np; ++i) {
+        Problem &pb = cx->probs[i];
+        const int64_t n = pb.dev.back().n;
+        DevBuf ones;
+        FSI_TRY(ones.alloc((size_t)n * 8));
+        FSI_TRY(bv[i].alloc((size_t)n * 8));
+        FSI_TRY(xv[i].alloc((size_t)n * 8));
+        std::vector<double> h1(n, 1.0);
+        FSI_CUDA(cudaMemcpyAsync(ones.p, h1.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        const DevCSR &A = pb.dev.back().A;
+        FSI_TRY(launch_spmv<double, double, double>(A, A.val64.as<double>(), ones.as<double>(), (const double *)nullptr,
+                                                    bv[i].as<double>(), SPMV_SET, s));
+        FSI_CUDA(cudaStreamSynchronize(s));
+    }
+    double best_t = 1e300;
+    int best = lanes[0];
+    for (int c = 0; c < n_lanes; ++c) {
+        cx->ell_lanes = lanes[c];
+        FSI_TRY(rebuild_ells(*cx));
+        double t_ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {           // the first run captures the graphs
+            std::vector<Run> runs(np);
+            for (int i = 0; i < np; ++i) {
+                runs[i].pb = &cx->probs[i];
+                runs[i].b = bv[i].as<double>();
+                runs[i].x = xv[i].as<double>();
+                runs[i].o = *opts;
+                runs[i].o.use_x0 = 0;
+            }
+            const auto t0 = std::chrono::steady_clock::now();
+            fsi_status e = solve_runs(*cx, runs);
+            FSI_CUDA(cudaStreamSynchronize(s));
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (e == FSI_ERR_CUDA || e == FSI_ERR_ALLOC) return e;
+            t_ms = e == FSI_OK ? ms : 1e300;
+        }
+        if (times_ms) times_ms[c] = t_ms;
+        if (t_ms < best_t) {
+            best_t = t_ms;
+            best = lanes[c];
+        }
+    }
+    cx->ell_lanes = best;
+    FSI_TRY(rebuild_ells(*cx));
+    *chosen = best;
+    g_last_error.clear();
+    return FSI_OK;
+}
+
+fsi_status fsi_get_cost(fsi_ctx *ctx, int prob, double *cost) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !cost || prob < 0 || prob >= (int)cx->probs.size()) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (!cx->smoothers_ready) { set_error("smoothers not set up"); return FSI_ERR_STATE; }
+    const Problem &pb = cx->probs[prob];
+    const LevelDev &F = pb.dev.back();
+    cost[0] = cycle_bytes(*cx, pb);
+    cost[1] = (double)F.A.nnz * 12.0 + (double)(F.n + 1) * 4.0 + (double)F.n * 2.0 * 8.0;   // float64 A z
+    cost[2] = (double)F.n * (cx->precision != FSI_FP64 ? 20.0 : 24.0);   // Gram-Schmidt, per basis vector
+    cost[3] = (double)F.n;
     return FSI_OK;
 }
 
@@ -2004,6 +2246,10 @@ void fsi_destroy(fsi_ctx *ctx) {
         collect_marks(*cx);
         for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
         cx->ev_pool.clear();
+        for (int d = 0; d < 2; ++d) {
+            if (cx->batch_graph[d]) cudaGraphExecDestroy(cx->batch_graph[d]);
+            cx->batch_graph[d] = nullptr;
+        }
         for (auto &pb : cx->probs) {
             drop_graphs(pb);
             if (pb.stream) {

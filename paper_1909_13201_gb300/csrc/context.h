@@ -275,6 +275,7 @@ struct Context {
     int variant = FSI_SMOOTHER_FS;   // field-split (FS) or monolithic (AS) Schwarz blocks
     int mult_levels = 0;             // finest levels with the locally multiplicative sweep
     int cascade = 0;                 // 1: swapped cascade, the cycle on the two system blocks (Sec. 5)
+    int ell_lanes = 0;               // lanes per row of every ELL copy (0: size rule; fsi_autotune_layout)
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;
@@ -298,6 +299,11 @@ struct Context {
     bool use_graphs = true;
     bool device_loop = true;         // whole solve as one graph with WHILE nodes
     cudaStream_t cap[3] = {nullptr, nullptr, nullptr};   // streams for capturing loop bodies
+    // batched solves: every problem's solve chain in one graph (per direction),
+    // valid while no problem's graphs were dropped since (graph epoch)
+    cudaGraphExec_t batch_graph[2] = {nullptr, nullptr};
+    int batch_graph_m[2] = {0, 0};
+    int64_t batch_epoch[2] = {-1, -1};
 };
 
 // ---------------------------------------------------------------- kernels
@@ -321,7 +327,8 @@ fsi_status launch_zero(T *v, int64_t n, cudaStream_t s);
 // binned-ELL copy of A (structure and val64; val32 too if present), and
 // the float32 copy of an existing ELL from A.val32.  concurrent: A belongs
 // to one problem of a batch (its launches share the GPU with the others').
-fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent);
+// force_G: lanes per row (1, 4, 8 or 16) chosen by the layout autotuner; 0 = the size rule
+fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent, int force_G = 0);
 fsi_status build_ell_subset(const DevCSR &A, const HostCSR &pat, const std::vector<int32_t> &rows,
                             const std::vector<uint8_t> &keep, const uint8_t *d_keep, DevEll &E,
                             cudaStream_t s, bool concurrent);

@@ -292,7 +292,7 @@ __global__ void axpy_clear_kernel(T *__restrict__ x, T *__restrict__ y, T a, int
 
 // Host: bins from the row lengths, then the fill kernel copies columns and
 // values.  The per-row ELL bases are kept only for the fill (freed here).
-fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent) {
+fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent, int force_G) {
     DevEll &E = A.ell;
     const int64_t n = A.n_rows;
     if (n == 0 || A.nnz == 0 || !A.val64.p) return FSI_OK;
@@ -318,6 +318,7 @@ fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent) {
     if (!concurrent && n < 150000)
         while (G < 16 && n * G < 300000) G *= 2;
     if (G == 2) G = 4;
+    if (force_G == 1 || force_G == 4 || force_G == 8 || force_G == 16) G = force_G;   // layout autotuner
     E.G = G;
     E.stream = (double)A.nnz * 12.0 > 64e6;
     std::vector<EllBin> bins;

@@ -292,6 +292,36 @@ def test_batched_uneven_systems_match_single_solves():
         assert st["iterations"] == it1
 
 
+def test_batch_graph_and_layout_autotune():
+    """A batch over every problem runs as one graph launch (one solve chain
+    per problem, each stopping on its own test): twice in a row it gives the
+    same bits; the layout autotuner keeps one of its candidates, and the
+    batched solves after it still match the direct solutions."""
+    probs = [I.make_channel_2d(16, 3, 1, 111, band_width=0.2),
+             I.make_channel_2d(32, 4, 3, 112, band_width=0.35, mu_s=20.0),
+             I.make_channel_2d(24, 3, 3, 113, band_width=0.15)]
+    sb = binding.FSISolver(probs)
+    sb.setup_smoothers(precision=binding.FSI_MIXED_HALF, patch=3)
+    bs, refs = [], []
+    for i, p in enumerate(probs):
+        H = gmg.Hierarchy(p)
+        b = _rhs(p, H, 30 + i)
+        bs.append(_cuda(b))
+        refs.append(_direct(H.fine, b))
+    xs1, sts1 = sb.solve_batched(bs, rtol=1e-10)
+    xs2, sts2 = sb.solve_batched(bs, rtol=1e-10)
+    for a, b_, s1, s2 in zip(xs1, xs2, sts1, sts2):
+        assert s1["iterations"] == s2["iterations"]
+        np.testing.assert_array_equal(a.cpu().numpy(), b_.cpu().numpy())
+    chosen, times = sb.autotune_layout((0, 1, 4), rtol=1e-8)
+    assert chosen in (0, 1, 4) and len(times) == 3 and min(times) < 1e300
+    xs, sts = sb.solve_batched(bs, rtol=1e-10)
+    for x, ref, st, st1 in zip(xs, refs, sts, sts1):
+        assert st["converged"]
+        assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+        assert abs(st["iterations"] - st1["iterations"]) <= 1
+
+
 def test_3d_valve_box_parity():
     """3D: Q2 hexahedra (27 nodes), 376-dof Vanka blocks (8-CTA cluster
     Gauss-Jordan in float64), FP16 storage apply for blocks above 256 dofs."""
