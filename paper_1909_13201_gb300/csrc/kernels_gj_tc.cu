@@ -42,6 +42,7 @@ constexpr int TC_THREADS = 256;
 constexpr int PANEL = 32;
 constexpr int CM_SBO = 1024, CM_LBO = 128;
 constexpr size_t MISC_BYTES = 64 + PANEL * 33 * 4 + 64;   // mbarrier, TMEM slot, flags, Dm
+constexpr int HT = 1024;          // slots of the gather's dof -> position table (> 2 x the largest block)
 
 struct GJTCParams {
     const int32_t *blk_ptr, *blk_idx;
@@ -82,7 +83,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int C, bool TC>
-__global__ void __launch_bounds__(TC_THREADS, 1) block_gj_tc_kernel(GJTCParams P) {
+__global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (C > 1) ? (int)cluster.block_rank() : 0;
@@ -115,56 +116,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) block_gj_tc_kernel(GJTCParams P
         sflag[1] = 0;
         if (TC) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     }
-    // gather the local rows (float64 CSR -> float32).  The CTA's nonzeros
-    // are walked as one flat range (row of entry e by binary search over the
-    // row offsets), so every thread keeps independent global loads in flight;
-    // column positions by binary search in the block's sorted index list.
-    int *roff = reinterpret_cast<int *>(sidx + ((n + 3) & ~3));   // [R + 1] flat offsets
-    int *rbeg = roff + R + 1;                                      // [R] CSR start of each row
+    // gather the local rows (float64 CSR -> float32): a warp per row, lanes
+    // over its entries (independent global loads), each column's position in
+    // the block from an open-addressing table global dof -> local position
+    // built in the (not yet used) F buffer
+    int *hkey = reinterpret_cast<int *>(Fs);
+    int *hval = hkey + HT;
     for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
+    for (int t = tid; t < HT; t += blockDim.x) hkey[t] = -1;
     for (int t = tid; t < n; t += blockDim.x) sidx[t] = idx[t];
     __syncthreads();
-    for (int li = tid; li < nr; li += blockDim.x) {
+    for (int t = tid; t < n; t += blockDim.x) {
+        const int key = sidx[t];
+        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> 22;            // 10 bits: HT = 1024
+        while (true) {                                               // n < HT: an empty slot exists
+            const int prev = atomicCAS(&hkey[h], -1, key);
+            if (prev == -1) { hval[h] = t; break; }
+            h = (h + 1) & (HT - 1);
+        }
+    }
+    __syncthreads();
+    for (int li = warp; li < nr; li += TC_THREADS / 32) {
         const int g = sidx[r0 + li];
-        const int a = P.row_ptr[g];
-        rbeg[li] = a;
-        roff[li + 1] = P.row_ptr[g + 1] - a;                       // length, scanned below
-    }
-    __syncthreads();
-    if (warp == 0) {                                               // exclusive scan of the lengths
-        int carry = 0;
-        if (lane == 0) roff[0] = 0;
-        for (int b0 = 0; b0 < nr; b0 += 32) {
-            const int li = b0 + lane;
-            int v = li < nr ? roff[li + 1] : 0;
+        const int a = P.row_ptr[g], b = P.row_ptr[g + 1];
+        float *mrow = Ms + (size_t)li * ldm;
+        for (int k = a + lane; k < b; k += 64) {
+            const bool two = k + 32 < b;
+            const int c0 = P.col[k];
+            const float v0 = (float)P.val[k];
+            const int c1 = two ? P.col[k + 32] : -1;
+            const float v1 = two ? (float)P.val[k + 32] : 0.f;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int w = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += w;
+            for (int u = 0; u < 2; ++u) {
+                const int c = u ? c1 : c0;
+                if (c < 0) continue;
+                uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
+                int pos = -1;
+                while (true) {
+                    const int kk = hkey[h];
+                    if (kk == c) { pos = hval[h]; break; }
+                    if (kk == -1) break;
+                    h = (h + 1) & (HT - 1);
+                }
+                if (pos >= 0) mrow[pos] = u ? v1 : v0;
             }
-            if (li < nr) roff[li + 1] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
         }
-    }
-    __syncthreads();
-    const int total = roff[nr];
-#pragma unroll 4
-    for (int e = tid; e < total; e += blockDim.x) {
-        int lo = 0, hi = nr;                                       // largest li with roff[li] <= e
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (roff[mid] <= e) lo = mid; else hi = mid;
-        }
-        const int k = rbeg[lo] + (e - roff[lo]);
-        const int c = P.col[k];
-        const float v = (float)P.val[k];
-        int a = 0, b = n, pos = -1;
-        while (a < b) {
-            const int mid = (a + b) >> 1, w = sidx[mid];
-            if (w == c) { pos = mid; break; }
-            if (w < c) a = mid + 1; else b = mid;
-        }
-        if (pos >= 0) Ms[(size_t)lo * ldm + pos] = v;
     }
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -414,32 +410,46 @@ fsi_status launch_tc(const GJTCParams &P, int64_t n_blocks, size_t smem, cudaStr
 
 }  // namespace
 
-// Shared-memory and tensor-memory plan for blocks of up to n dofs: the
-// smallest cluster whose CTAs hold R = 32-aligned rows within the budgets.
-bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out) {
-    const size_t budget = 225 * 1024;
+// Shared-memory and tensor-memory plan for blocks of up to n dofs.  First
+// choice: the smallest cluster whose CTAs fit two to an SM (<= 112 KB of
+// shared memory, <= 256 tensor-memory columns each, so two co-resident CTAs
+// -- of one cluster or two -- never wait on each other's columns): while one
+// CTA is in a serial panel step the other keeps the SM busy.  Otherwise the
+// smallest cluster that fits at all, one CTA per SM (a cluster's CTAs then
+// never share an SM: a second CTA waiting in tcgen05.alloc behind the
+// first's columns would never proceed).  Rows are stored with an odd stride,
+// so a warp reading one column of 32 consecutive rows hits 32 banks.
+static size_t gj_tc_bytes(int n, int C, int R, int *cols_out) {
     const int npad = (n + 15) & ~15;
-    for (int C = 1; C <= 8; C *= 2) {
-        int R = (n + C - 1) / C;
-        if (C > 1) R = (R + PANEL - 1) / PANEL * PANEL;
-        const int tiles = (R + 127) / 128;
-        if (tiles * npad > 512) continue;
-        int ldm = n;
-        ldm += (33 - (ldm % 32)) % 32;                  // row stride = 1 (mod 32): conflict-free column reads
-        const size_t m_bytes = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
-        const size_t f_bytes = (size_t)tiles * 16384;
-        const size_t b_bytes = ((size_t)npad * 128 + 1023) & ~(size_t)1023;
-        // misc: barrier, flags, Dm; then the block's indices and the row offsets
-        size_t total = m_bytes + f_bytes + b_bytes + MISC_BYTES + (size_t)(((n + 3) & ~3) + 2 * R + 4) * 4;
-        // a cluster's CTAs must not share an SM: each holds its tensor-memory
-        // columns until the last cluster barrier, so a second CTA of the same
-        // cluster waiting in tcgen05.alloc on that SM would never proceed
-        if (C > 1) total = std::max(total, (size_t)120 * 1024);
-        if (total <= budget) {
-            *C_out = C;
-            *R_out = R;
-            *smem_out = total;
-            return true;
+    const int tiles = (R + 127) / 128;
+    int cols = 32;
+    while (cols < tiles * npad) cols *= 2;
+    *cols_out = tiles * npad > 512 ? 1 << 30 : cols;
+    const int ldm = n | 1;
+    const size_t m_bytes = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
+    const size_t f_bytes = (size_t)tiles * 16384;
+    const size_t b_bytes = ((size_t)npad * 128 + 1023) & ~(size_t)1023;
+    // misc: barrier, flags, Dm; then the block's indices and the row offsets
+    return m_bytes + f_bytes + b_bytes + MISC_BYTES + (size_t)(((n + 3) & ~3) + 2 * R + 4) * 4;
+}
+
+bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out) {
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t budget = pass == 0 ? 112 * 1024 : 225 * 1024;
+        for (int C = 1; C <= 8; C *= 2) {
+            int R = (n + C - 1) / C;
+            if (C > 1) R = (R + PANEL - 1) / PANEL * PANEL;
+            int cols = 0;
+            size_t total = gj_tc_bytes(n, C, R, &cols);
+            if (cols > 512) continue;
+            if (pass == 0 && cols > 256) continue;
+            if (pass == 1 && C > 1) total = std::max(total, (size_t)120 * 1024);
+            if (total <= budget) {
+                *C_out = C;
+                *R_out = R;
+                *smem_out = total;
+                return true;
+            }
         }
     }
     return false;
@@ -468,8 +478,7 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
     P.storage = storage;
     P.n_max = n;
     P.rows_per_cta = R;
-    int ldm = n;
-    ldm += (33 - (ldm % 32)) % 32;
+    const int ldm = n | 1;
     P.ldm = ldm;
     P.npad = (n + 15) & ~15;
     P.tiles = (R + 127) / 128;
