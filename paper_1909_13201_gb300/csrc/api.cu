@@ -14,6 +14,8 @@
 #include <string>
 #include <type_traits>
 
+#include <cublas_v2.h>
+
 #include "context.h"
 
 namespace fsi {
@@ -1113,7 +1115,19 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
         if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
         {
             ProfMark pm(cx, 3, l + 1 == pb.dev.size());
-            if (method == FSI_FACTOR_FP64)
+            // monolithic (AS) blocks beyond one cluster: the split inversion over
+            // the two field systems, float32 inverses
+            int cq = 0, rq = 0;
+            size_t smq = 0;
+            const bool split = cx.variant == FSI_SMOOTHER_AS && !gj_tc_plan((int)D.max_block, &cq, &rq, &smq);
+            if (split) {
+                if (store != 1) {
+                    set_error("AS blocks of " + std::to_string(D.max_block) +
+                              " dofs are inverted by the split method, which needs FSI_MIXED (float32 inverses)");
+                    return FSI_ERR_ARG;
+                }
+                FSI_TRY(launch_block_invert_schur(cx, D.A, D, H.off[3], method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
+            } else if (method == FSI_FACTOR_FP64)
                 FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
             else
                 FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
@@ -2250,6 +2264,8 @@ void fsi_destroy(fsi_ctx *ctx) {
             if (cx->batch_graph[d]) cudaGraphExecDestroy(cx->batch_graph[d]);
             cx->batch_graph[d] = nullptr;
         }
+        if (cx->cublas) cublasDestroy(static_cast<cublasHandle_t>(cx->cublas));
+        cx->cublas = nullptr;
         for (auto &pb : cx->probs) {
             drop_graphs(pb);
             if (pb.stream) {

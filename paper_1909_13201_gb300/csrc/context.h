@@ -276,6 +276,7 @@ struct Context {
     int mult_levels = 0;             // finest levels with the locally multiplicative sweep
     int cascade = 0;                 // 1: swapped cascade, the cycle on the two system blocks (Sec. 5)
     int ell_lanes = 0;               // lanes per row of every ELL copy (0: size rule; fsi_autotune_layout)
+    void *cublas = nullptr;          // cuBLAS handle (batched GEMMs of the split inversion of large AS blocks)
     bool smoothers_ready = false;
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;
@@ -349,6 +350,11 @@ fsi_status launch_jacobi_apply(const LevelDev &lev, const T *r, T *x, T omega, c
 
 // blocked float32 Gauss-Jordan (tensor: tcgen05 TF32 rank-32 updates;
 // otherwise float32 FMAs); storage 1 float32, 2 float16 + row scale
+// Monolithic blocks beyond one cluster (3D AS): inverse from the 2 x 2 split
+// over the two field systems (off3 = first velocity-system dof), float32
+fsi_status launch_block_invert_schur(Context &cx, const DevCSR &A, const LevelDev &lev, int64_t off3, bool tensor,
+                                     int *flags, cudaStream_t s);
+bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out);
 fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int storage, bool tensor, int *flags,
                                   cudaStream_t s);
 

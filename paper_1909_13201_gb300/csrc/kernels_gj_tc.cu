@@ -29,6 +29,9 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <vector>
+
+#include <cublas_v2.h>
 
 #include "context.h"
 
@@ -60,6 +63,7 @@ struct GJTCParams {
     int tmem_cols;             // allocated tensor-memory columns
     size_t off_f, off_b, off_misc;   // shared-memory offsets (bytes)
     int *flags;                // [0] zero pivot, [2] |= 4: MMA wait timed out
+    const float *dense;        // dense mode: block b is dense[b n n ..], row-major n x n (every block n = n_max)
 };
 
 __host__ __device__ inline int cm_off(int r, int k) {
@@ -90,7 +94,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     const int blk = blockIdx.x / C;
     const int s0 = P.blk_ptr[blk];
     const int n = P.blk_ptr[blk + 1] - s0;
-    const int32_t *idx = P.blk_idx + s0;
     const int R = P.rows_per_cta, ldm = P.ldm;
     const int r0 = rank * R;
     const int nr = max(0, min(R, n - r0));             // rows held by this CTA
@@ -120,45 +123,56 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     // over its entries (independent global loads), each column's position in
     // the block from an open-addressing table global dof -> local position
     // built in the (not yet used) F buffer
-    int *hkey = reinterpret_cast<int *>(Fs);
-    int *hval = hkey + HT;
-    for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
-    for (int t = tid; t < HT; t += blockDim.x) hkey[t] = -1;
-    for (int t = tid; t < n; t += blockDim.x) sidx[t] = idx[t];
-    __syncthreads();
-    for (int t = tid; t < n; t += blockDim.x) {
-        const int key = sidx[t];
-        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> 22;            // 10 bits: HT = 1024
-        while (true) {                                               // n < HT: an empty slot exists
-            const int prev = atomicCAS(&hkey[h], -1, key);
-            if (prev == -1) { hval[h] = t; break; }
-            h = (h + 1) & (HT - 1);
+    if (P.dense) {
+        // dense mode: the block's rows from a row-major n x n array
+        const float *src = P.dense + (size_t)blk * n * n;
+        for (int t = tid; t < nr * n; t += blockDim.x) {
+            const int li = t / n, c = t - li * n;
+            Ms[(size_t)li * ldm + c] = src[(size_t)(r0 + li) * n + c];
         }
-    }
-    __syncthreads();
-    for (int li = warp; li < nr; li += TC_THREADS / 32) {
-        const int g = sidx[r0 + li];
-        const int a = P.row_ptr[g], b = P.row_ptr[g + 1];
-        float *mrow = Ms + (size_t)li * ldm;
-        for (int k = a + lane; k < b; k += 64) {
-            const bool two = k + 32 < b;
-            const int c0 = P.col[k];
-            const float v0 = (float)P.val[k];
-            const int c1 = two ? P.col[k + 32] : -1;
-            const float v1 = two ? (float)P.val[k + 32] : 0.f;
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int c = u ? c1 : c0;
-                if (c < 0) continue;
-                uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
-                int pos = -1;
-                while (true) {
-                    const int kk = hkey[h];
-                    if (kk == c) { pos = hval[h]; break; }
-                    if (kk == -1) break;
-                    h = (h + 1) & (HT - 1);
+        for (int t = tid; t < nr; t += blockDim.x)
+            for (int c = n; c < ldm; ++c) Ms[(size_t)t * ldm + c] = 0.f;
+    } else {
+        int *hkey = reinterpret_cast<int *>(Fs);
+        int *hval = hkey + HT;
+        for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
+        for (int t = tid; t < HT; t += blockDim.x) hkey[t] = -1;
+        for (int t = tid; t < n; t += blockDim.x) sidx[t] = P.blk_idx[s0 + t];
+        __syncthreads();
+        for (int t = tid; t < n; t += blockDim.x) {
+            const int key = sidx[t];
+            uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> 22;            // 10 bits: HT = 1024
+            while (true) {                                               // n < HT: an empty slot exists
+                const int prev = atomicCAS(&hkey[h], -1, key);
+                if (prev == -1) { hval[h] = t; break; }
+                h = (h + 1) & (HT - 1);
+            }
+        }
+        __syncthreads();
+        for (int li = warp; li < nr; li += TC_THREADS / 32) {
+            const int g = sidx[r0 + li];
+            const int a = P.row_ptr[g], b = P.row_ptr[g + 1];
+            float *mrow = Ms + (size_t)li * ldm;
+            for (int k = a + lane; k < b; k += 64) {
+                const bool two = k + 32 < b;
+                const int c0 = P.col[k];
+                const float v0 = (float)P.val[k];
+                const int c1 = two ? P.col[k + 32] : -1;
+                const float v1 = two ? (float)P.val[k + 32] : 0.f;
+    #pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = u ? c1 : c0;
+                    if (c < 0) continue;
+                    uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
+                    int pos = -1;
+                    while (true) {
+                        const int kk = hkey[h];
+                        if (kk == c) { pos = hval[h]; break; }
+                        if (kk == -1) break;
+                        h = (h + 1) & (HT - 1);
+                    }
+                    if (pos >= 0) mrow[pos] = u ? v1 : v0;
                 }
-                if (pos >= 0) mrow[pos] = u ? v1 : v0;
             }
         }
     }
@@ -489,6 +503,7 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
     P.off_b = P.off_f + (size_t)P.tiles * 16384;
     P.off_misc = P.off_b + (((size_t)P.npad * 128 + 1023) & ~(size_t)1023);
     P.flags = flags;
+    P.dense = nullptr;
 #define FSI_TC_CASE(CC)                                                                       \
     case CC:                                                                                  \
         return tensor ? launch_tc<CC, true>(P, lev.n_blocks, smem, s)                         \
@@ -503,6 +518,275 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
             return FSI_ERR_ARG;
     }
 #undef FSI_TC_CASE
+}
+
+// ---------------------------------------------------------------------------
+// Monolithic Schwarz blocks larger than one cluster holds (the AS comparison
+// preconditioner in 3D: all fields of the closure of 8 hexahedra, ~750
+// dofs).  The block's unknowns split, in their J2 order, into the
+// displacement system (d^s, d^f, p^s: a prefix of the sorted index list) and
+// the velocity system (u^s, u^f, p^f); with M = [A B; C D] on that split,
+//   X = A^{-1},  S = D - C X B,  Y = S^{-1},
+//   M^{-1} = [X + X B Y C X, -X B Y; -Y C X, Y],
+// evaluated as U = C X, T = X B, S = D - U B, Y = S^{-1}, TR = -T Y,
+// BL = -Y U, TL = X - T BL.  A and S (each about half the block) are
+// inverted by the cluster Gauss-Jordan kernel in dense mode, the products
+// are float32 batched GEMMs (cuBLAS).  Every block is padded to the
+// largest split sizes N1, N2 with identity rows and columns (the padded M is
+// blockdiag(M, I), whose inverse is blockdiag(M^{-1}, I)), so a chunk of
+// blocks is one strided batch.
+
+// A, B, C, D of blocks [j0, j0 + gridDim.x) from the CSR, padded; zeroed first
+__global__ void __launch_bounds__(256) schur_gather_kernel(const int32_t *__restrict__ row_ptr,
+                                                            const int32_t *__restrict__ col,
+                                                            const double *__restrict__ val,
+                                                            const int32_t *__restrict__ blk_ptr,
+                                                            const int32_t *__restrict__ blk_idx, int64_t j0,
+                                                            int off3, int N1, int N2, float *__restrict__ Ad,
+                                                            float *__restrict__ Bd, float *__restrict__ Cd,
+                                                            float *__restrict__ Dd) {
+    constexpr int HT2 = 2048;
+    __shared__ int hkey[HT2], hval[HT2];
+    const int64_t j = j0 + blockIdx.x;
+    const int s0 = blk_ptr[j], n = blk_ptr[j + 1] - s0;
+    float *A = Ad + (size_t)blockIdx.x * N1 * N1, *B = Bd + (size_t)blockIdx.x * N1 * N2;
+    float *C = Cd + (size_t)blockIdx.x * N2 * N1, *D = Dd + (size_t)blockIdx.x * N2 * N2;
+    for (int t = threadIdx.x; t < HT2; t += blockDim.x) hkey[t] = -1;
+    __shared__ int n1s;
+    if (threadIdx.x == 0) n1s = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int key = blk_idx[s0 + t];
+        if (key < off3) atomicAdd(&n1s, 1);
+        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> 21;            // 11 bits
+        while (true) {
+            const int prev = atomicCAS(&hkey[h], -1, key);
+            if (prev == -1) { hval[h] = t; break; }
+            h = (h + 1) & (HT2 - 1);
+        }
+    }
+    __syncthreads();
+    const int n1 = n1s, n2 = n - n1;
+    // zero, then the padding diagonals
+    for (int t = threadIdx.x; t < N1 * N1; t += blockDim.x) A[t] = 0.f;
+    for (int t = threadIdx.x; t < N1 * N2; t += blockDim.x) B[t] = 0.f;
+    for (int t = threadIdx.x; t < N2 * N1; t += blockDim.x) C[t] = 0.f;
+    for (int t = threadIdx.x; t < N2 * N2; t += blockDim.x) D[t] = 0.f;
+    __syncthreads();
+    for (int t = n1 + threadIdx.x; t < N1; t += blockDim.x) A[(size_t)t * N1 + t] = 1.f;
+    for (int t = n2 + threadIdx.x; t < N2; t += blockDim.x) D[(size_t)t * N2 + t] = 1.f;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int li = warp; li < n; li += blockDim.x / 32) {
+        const int g = blk_idx[s0 + li];
+        for (int k = row_ptr[g] + lane; k < row_ptr[g + 1]; k += 32) {
+            const int c = col[k];
+            uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 21;
+            int pos = -1;
+            while (true) {
+                const int kk = hkey[h];
+                if (kk == c) { pos = hval[h]; break; }
+                if (kk == -1) break;
+                h = (h + 1) & (HT2 - 1);
+            }
+            if (pos < 0) continue;
+            const float v = (float)val[k];
+            if (li < n1) {
+                if (pos < n1) A[(size_t)li * N1 + pos] = v;
+                else B[(size_t)li * N2 + (pos - n1)] = v;
+            } else {
+                if (pos < n1) C[(size_t)(li - n1) * N1 + pos] = v;
+                else D[(size_t)(li - n1) * N2 + (pos - n1)] = v;
+            }
+        }
+    }
+}
+
+// the block's inverse from its four padded parts into the level's storage
+// (row-major, rows padded to 4 floats, at blk_off[j])
+__global__ void __launch_bounds__(256) schur_scatter_kernel(const int32_t *__restrict__ blk_ptr,
+                                                             const int32_t *__restrict__ blk_idx,
+                                                             const int64_t *__restrict__ blk_off, int64_t j0,
+                                                             int off3, int N1, int N2, const float *__restrict__ TL,
+                                                             const float *__restrict__ TR, const float *__restrict__ BL,
+                                                             const float *__restrict__ Y, float *__restrict__ inv) {
+    const int64_t j = j0 + blockIdx.x;
+    const int s0 = blk_ptr[j], n = blk_ptr[j + 1] - s0;
+    __shared__ int n1s;
+    if (threadIdx.x == 0) n1s = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        if (blk_idx[s0 + t] < off3) atomicAdd(&n1s, 1);
+    __syncthreads();
+    const int n1 = n1s;
+    const int ldo = (n + 3) & ~3;
+    float *out = inv + blk_off[j];
+    const size_t b = blockIdx.x;
+    for (int t = threadIdx.x; t < n * ldo; t += blockDim.x) {
+        const int r = t / ldo, c = t - r * ldo;
+        float v = 0.f;
+        if (c < n) {
+            if (r < n1) v = c < n1 ? TL[b * N1 * N1 + (size_t)r * N1 + c] : TR[b * N1 * N2 + (size_t)r * N2 + (c - n1)];
+            else v = c < n1 ? BL[b * N2 * N1 + (size_t)(r - n1) * N1 + c]
+                            : Y[b * N2 * N2 + (size_t)(r - n1) * N2 + (c - n1)];
+        }
+        out[(size_t)r * ldo + c] = v;
+    }
+}
+
+namespace {
+// row-major C (m x n) = alpha A (m x k) B (k x n) + beta C, strided batch
+// (cuBLAS is column-major: C^T = B^T A^T)
+cublasStatus_t sgemm_rm(cublasHandle_t h, int m, int n, int k, float alpha, const float *A, long long sA,
+                        const float *B, long long sB, float beta, float *C, long long sC, int batch) {
+    return cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, m, k, &alpha, B, n, sB, A, k, sA, &beta, C, n,
+                                     sC, batch);
+}
+
+// nb dense row-major N x N matrices at `in` inverted into `out` (float32)
+fsi_status invert_dense(const float *in, float *out, int64_t nb, int N, bool tensor, int *flags,
+                        const int32_t *dptr, const int64_t *doff, cudaStream_t s) {
+    int C = 1, R = 0;
+    size_t smem = 0;
+    if (!gj_tc_plan(N, &C, &R, &smem)) {
+        set_error("Schur part too large for the cluster inversion (" + std::to_string(N) + ")");
+        return FSI_ERR_ARG;
+    }
+    GJTCParams P;
+    P.blk_ptr = dptr;
+    P.blk_idx = nullptr;
+    P.blk_off = doff;
+    P.row_ptr = nullptr;
+    P.col = nullptr;
+    P.val = nullptr;
+    P.inv = out;
+    P.scale = nullptr;
+    P.storage = 1;
+    P.n_max = N;
+    P.rows_per_cta = R;
+    const int ldm = N | 1;
+    P.ldm = ldm;
+    P.npad = (N + 15) & ~15;
+    P.tiles = (R + 127) / 128;
+    int cols = 32;
+    while (cols < P.tiles * P.npad) cols *= 2;
+    P.tmem_cols = cols;
+    P.off_f = ((size_t)R * ldm * 4 + 1023) & ~(size_t)1023;
+    P.off_b = P.off_f + (size_t)P.tiles * 16384;
+    P.off_misc = P.off_b + (((size_t)P.npad * 128 + 1023) & ~(size_t)1023);
+    P.flags = flags;
+    P.dense = in;
+#define FSI_TC_CASE(CC)                                                                   \
+    case CC:                                                                              \
+        return tensor ? launch_tc<CC, true>(P, nb, smem, s) : launch_tc<CC, false>(P, nb, smem, s);
+    switch (C) {
+        FSI_TC_CASE(1)
+        FSI_TC_CASE(2)
+        FSI_TC_CASE(4)
+        FSI_TC_CASE(8)
+        default:
+            set_error("bad cluster size");
+            return FSI_ERR_ARG;
+    }
+#undef FSI_TC_CASE
+}
+}  // namespace
+
+#define FSI_CUBLAS(call)                                                                      \
+    do {                                                                                      \
+        cublasStatus_t e_ = (call);                                                           \
+        if (e_ != CUBLAS_STATUS_SUCCESS) {                                                    \
+            set_error(std::string(#call) + " failed (cuBLAS status " + std::to_string((int)e_) + ")"); \
+            return FSI_ERR_CUDA;                                                              \
+        }                                                                                     \
+    } while (0)
+
+fsi_status launch_block_invert_schur(Context &cx, const DevCSR &A, const LevelDev &lev, int64_t off3, bool tensor,
+                                     int *flags, cudaStream_t s) {
+    if (lev.n_blocks == 0) return FSI_OK;
+    if (lev.inv_store != 1) { set_error("the split block inversion stores float32 inverses"); return FSI_ERR_ARG; }
+    int n1max = 1, n2max = 1;
+    for (int64_t j = 0; j < lev.n_blocks; ++j) {
+        int n1 = 0;
+        for (int64_t k = lev.h_blk_ptr[j]; k < lev.h_blk_ptr[j + 1]; ++k) n1 += lev.h_blk_idx[k] < off3 ? 1 : 0;
+        n1max = std::max(n1max, n1);
+        n2max = std::max(n2max, (int)(lev.h_blk_ptr[j + 1] - lev.h_blk_ptr[j]) - n1);
+    }
+    const int N1 = (n1max + 3) & ~3, N2 = (n2max + 3) & ~3;
+    int Ct, Rt;
+    size_t sm;
+    if (!gj_tc_plan(N1, &Ct, &Rt, &sm) || !gj_tc_plan(N2, &Ct, &Rt, &sm)) {
+        set_error("Schwarz block halves too large for the cluster inversion (" + std::to_string(n1max) + ", " +
+                  std::to_string(n2max) + " dofs)");
+        return FSI_ERR_ARG;
+    }
+    if (!cx.cublas) {
+        cublasHandle_t h = nullptr;
+        FSI_CUBLAS(cublasCreate(&h));
+        cx.cublas = h;
+    }
+    cublasHandle_t h = static_cast<cublasHandle_t>(cx.cublas);
+    FSI_CUBLAS(cublasSetStream(h, s));
+    FSI_CUBLAS(cublasSetMathMode(h, tensor ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH));
+    const size_t q11 = (size_t)N1 * N1, q12 = (size_t)N1 * N2, q22 = (size_t)N2 * N2;
+    const size_t per_block = (3 * q11 + 6 * q12 + 2 * q22) * 4;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(lev.n_blocks, ((int64_t)4 << 30) / (int64_t)per_block));
+    DevBuf Ad, Bd, Cd, Dd, X, T, U, Y, TR, BL, TL, p1, o1, p2, o2;
+    FSI_TRY(Ad.alloc(chunk * q11 * 4));
+    FSI_TRY(X.alloc(chunk * q11 * 4));
+    FSI_TRY(TL.alloc(chunk * q11 * 4));
+    FSI_TRY(Bd.alloc(chunk * q12 * 4));
+    FSI_TRY(T.alloc(chunk * q12 * 4));
+    FSI_TRY(TR.alloc(chunk * q12 * 4));
+    FSI_TRY(Cd.alloc(chunk * q12 * 4));
+    FSI_TRY(U.alloc(chunk * q12 * 4));
+    FSI_TRY(BL.alloc(chunk * q12 * 4));
+    FSI_TRY(Dd.alloc(chunk * q22 * 4));
+    FSI_TRY(Y.alloc(chunk * q22 * 4));
+    {
+        std::vector<int32_t> a(chunk + 1), c(chunk + 1);
+        std::vector<int64_t> b(chunk), d(chunk);
+        for (int64_t i = 0; i <= chunk; ++i) {
+            a[i] = (int32_t)(i * N1);
+            c[i] = (int32_t)(i * N2);
+        }
+        for (int64_t i = 0; i < chunk; ++i) {
+            b[i] = i * (int64_t)q11;
+            d[i] = i * (int64_t)q22;
+        }
+        FSI_TRY(p1.alloc(a.size() * 4));
+        FSI_TRY(p2.alloc(c.size() * 4));
+        FSI_TRY(o1.alloc(b.size() * 8));
+        FSI_TRY(o2.alloc(d.size() * 8));
+        FSI_CUDA(cudaMemcpyAsync(p1.p, a.data(), a.size() * 4, cudaMemcpyHostToDevice, s));
+        FSI_CUDA(cudaMemcpyAsync(p2.p, c.data(), c.size() * 4, cudaMemcpyHostToDevice, s));
+        FSI_CUDA(cudaMemcpyAsync(o1.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, s));
+        FSI_CUDA(cudaMemcpyAsync(o2.p, d.data(), d.size() * 8, cudaMemcpyHostToDevice, s));
+        FSI_CUDA(cudaStreamSynchronize(s));
+    }
+    for (int64_t j0 = 0; j0 < lev.n_blocks; j0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, lev.n_blocks - j0);
+        schur_gather_kernel<<<nb, 256, 0, s>>>(A.ptr.as<int32_t>(), A.col.as<int32_t>(), A.val64.as<double>(),
+                                               lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(), j0, (int)off3,
+                                               N1, N2, Ad.as<float>(), Bd.as<float>(), Cd.as<float>(), Dd.as<float>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+        FSI_TRY(invert_dense(Ad.as<float>(), X.as<float>(), nb, N1, tensor, flags, p1.as<int32_t>(), o1.as<int64_t>(), s));
+        FSI_CUBLAS(sgemm_rm(h, N2, N1, N1, 1.f, Cd.as<float>(), q12, X.as<float>(), q11, 0.f, U.as<float>(), q12, nb));
+        FSI_CUBLAS(sgemm_rm(h, N1, N2, N1, 1.f, X.as<float>(), q11, Bd.as<float>(), q12, 0.f, T.as<float>(), q12, nb));
+        FSI_CUBLAS(sgemm_rm(h, N2, N2, N1, -1.f, U.as<float>(), q12, Bd.as<float>(), q12, 1.f, Dd.as<float>(), q22, nb));
+        FSI_TRY(invert_dense(Dd.as<float>(), Y.as<float>(), nb, N2, tensor, flags, p2.as<int32_t>(), o2.as<int64_t>(), s));
+        FSI_CUBLAS(sgemm_rm(h, N1, N2, N2, -1.f, T.as<float>(), q12, Y.as<float>(), q22, 0.f, TR.as<float>(), q12, nb));
+        FSI_CUBLAS(sgemm_rm(h, N2, N1, N2, -1.f, Y.as<float>(), q22, U.as<float>(), q12, 0.f, BL.as<float>(), q12, nb));
+        FSI_CUDA(cudaMemcpyAsync(TL.p, X.p, (size_t)nb * q11 * 4, cudaMemcpyDeviceToDevice, s));
+        FSI_CUBLAS(sgemm_rm(h, N1, N1, N2, -1.f, T.as<float>(), q12, BL.as<float>(), q12, 1.f, TL.as<float>(), q11, nb));
+        schur_scatter_kernel<<<nb, 256, 0, s>>>(lev.blk_ptr.as<int32_t>(), lev.blk_idx.as<int32_t>(),
+                                                lev.blk_off.as<int64_t>(), j0, (int)off3, N1, N2, TL.as<float>(),
+                                                TR.as<float>(), BL.as<float>(), Y.as<float>(), lev.inv.as<float>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
 }
 
 }  // namespace fsi

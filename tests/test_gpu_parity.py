@@ -588,21 +588,43 @@ def test_as_solves_fp64_and_mixed(as_case):
     assert abs(stm["iterations"] - ostm["iterations"]) <= 1, (stm["iterations"], ostm["iterations"])
 
 
-def test_as_3d_blocks_rejected():
+def test_as_3d_split_inversion():
     """AS blocks in 3D (~750 dofs: all fields on the 5^3 nodes around a
-    vertex) exceed the inversion kernels; set-up returns FSI_ERR_ARG for every
-    factorisation and leaves the context usable with the field split."""
+    vertex) are inverted by the 2 x 2 split over the two field systems (the
+    halves by the cluster Gauss-Jordan kernel, the products by batched
+    float32 GEMMs): block sets equal the oracle's, the smoother equals the
+    oracle's float64 AS smoother to float32 accuracy of the block inverses
+    (cond(A_jj) u_32, condition numbers up to ~1e4: 1e-3), the solve reaches
+    the direct solution and needs the oracle's float32 emulation's iteration
+    count +-1.  Float64 inverses of such blocks are refused (FSI_ERR_ARG)."""
     p = I.make_valve_3d(8, 2, 1, 777)
     s = binding.FSISolver(p)
-    for prec in (binding.FSI_FP64, binding.FSI_MIXED_HALF):
-        with pytest.raises(binding.FSIError) as err:
-            s.setup_smoothers(precision=prec, variant=binding.FSI_SMOOTHER_AS)
-        assert err.value.status == binding.FSI_ERR_ARG
-    s.setup_smoothers(precision=binding.FSI_MIXED_HALF)
-    H = gmg.Hierarchy(p)
-    b = _rhs(p, H, 41)
-    x, st = s.solve(_cuda(b), rtol=1e-8)
-    assert st["converged"]
+    with pytest.raises(binding.FSIError) as err:
+        s.setup_smoothers(precision=binding.FSI_FP64, variant=binding.FSI_SMOOTHER_AS)
+    assert err.value.status == binding.FSI_ERR_ARG
+    s.setup_smoothers(precision=binding.FSI_MIXED, factor=binding.FSI_FACTOR_FP32, variant=binding.FSI_SMOOTHER_AS)
+    H = gmg.Hierarchy(p, monolithic=True)
+    l = len(H.A) - 1
+    assert s.sizes(l)["max_block"] > 512
+    ptr, idx = s.blocks(l)
+    for j, ref in enumerate(H.smoothers[l].blocks):
+        np.testing.assert_array_equal(idx[ptr[j]:ptr[j + 1]], ref)
+    rng = np.random.default_rng(42)
+    r = rng.standard_normal(H.A[l].shape[0])
+    for tr in (False, True):
+        y = s.apply_smoother(l, _cuda(r), transpose=tr).cpu().numpy()
+        S = H.smoothers[l]
+        ref = S.apply_transpose(r) if tr else S.apply(r)
+        assert np.linalg.norm(y - ref) <= 1e-3 * np.linalg.norm(ref), tr
+    b = _rhs(p, H, 43)
+    xd = _direct(H.fine, b)
+    x, st = s.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+    Hm = gmg.Hierarchy(p, monolithic=True, mixed=True)
+    _, ost = ofg.solve(Hm, b, rtol=1e-8)
+    _, st8 = s.solve(_cuda(b), rtol=1e-8)
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
+
 
 
 @pytest.mark.parametrize("prec", [binding.FSI_MIXED, binding.FSI_MIXED_HALF])
