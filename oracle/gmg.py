@@ -57,7 +57,7 @@ class Hierarchy:
     def __init__(self, prob, *, mixed: bool = False, omega: float | None = None, nu_pre: int = 1,
                  nu_post: int = 1, patch: int | None = None, classical_restriction: bool = False,
                  weighted: bool = True, monolithic: bool = False, mult_levels: int = 0,
-                 cascade: bool = False):
+                 cascade: bool = False, operators=None):
         self.prob = prob
         self.cascade = cascade
         self.mixed = bool(mixed)
@@ -67,7 +67,9 @@ class Hierarchy:
         self.wdtype = np.float32 if mixed else np.float64
         self.levels = build_levels(prob)
         ref = Reference(prob.dim)
-        self.A = [assemble(prob, lev, ref) for lev in self.levels]
+        # level operators: rediscretised linear forms, or given matrices (the
+        # Newton Jacobians of the nonlinear loop, oracle.nonlinear)
+        self.A = list(operators) if operators is not None else [assemble(prob, lev, ref) for lev in self.levels]
         nl = len(self.levels)
         self.P = [None] + [prolongation(self.levels[l], self.levels[l - 1]) for l in range(1, nl)]
         self.R = [None] + [restriction(self.P[l], self.levels[l], self.levels[l - 1],
