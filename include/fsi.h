@@ -71,6 +71,10 @@ typedef struct {
 
 typedef struct {
     int restriction;            /* 0: equation-aware R2 of Sec. 3.3 (default); 1: classical P^T */
+    int nonlinear;              /* 1: operator patterns hold every coupling of the Jacobian of the
+                                 * nonlinear residual (Sec. 2.2: the W rows also couple to d on the
+                                 * moving fluid element), as fsi_nl_setup requires; the linear
+                                 * operator then carries explicit zeros there.  0: linear patterns. */
 } fsi_hier_opts;
 
 typedef struct {
@@ -347,6 +351,93 @@ fsi_status fsi_setup_host_only(const fsi_problem *prob, const fsi_hier_opts *opt
 
 /* Host copy of the sparsity pattern of A_l: row_ptr (n+1), col (nnz). */
 fsi_status fsi_get_pattern(const fsi_ctx *ctx, int prob, int level, int64_t *row_ptr, int32_t *col);
+
+/* ---------------------------------------------------------------------------
+ * Nonlinear FSI (Sec. 2.2): the monolithic residual R(U; U_n) of the ALE
+ * formulation and one implicit time step solved by exact Newton, each
+ * Newton system J(U_k) dU = -R(U_k) solved by fsi_solve's FGMRES with the
+ * GMG / field-split preconditioner on the level Jacobians.  2D only.
+ *
+ * The residual, per element of the reference mesh (3-point Gauss rule):
+ *   solid (total Lagrangian): rho_s (u - u_n)/dt + div of the first
+ *     Piola-Kirchhoff stress of the incompressible Mooney-Rivlin law
+ *     sigma = -p I + 2 C1 (B - I) - 2 C2 (B^{-1} - I), B = F F^T
+ *     (Crank-Nicolson average of the elastic stress, pressure at t_new);
+ *     K rows M_L (u - (d - d_n)/dt); V rows -(J - 1, q);
+ *   fluid (ALE, on the element moved by d): rho (u - u_n)/dt + the
+ *     Crank-Nicolson average of rho ((u - w_m).grad) u - rho f and of the
+ *     viscous stress mu (grad u + grad u^T), the pressure at t_new, the SUPG
+ *     term of Eq. phi_SUPG with tau of Eq. tausupg, lambda_k of Eq. lambda_k
+ *     by 50 power-method steps on the element's bubble space; mesh velocity
+ *     w_m = (d - d_n)/dt; A rows: the harmonic extension k (grad d + grad
+ *     d^T) (k = 1/V_el of the fine element); W rows -(J div_x u, q);
+ *   fixed (Dirichlet) dofs: R_i = U_i.
+ * Body force f = force sin(2 pi t / period) w(x), w the problem's advection
+ * field (zero at solid-class nodes).  The Jacobian is exact (tau included),
+ * assembled on every level: level L-1 at U, coarser levels at the states
+ * injected at coinciding nodes.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double force;               /* body-force amplitude */
+    double period;              /* > 0 */
+    double C1, C2;              /* Mooney-Rivlin constants; C1 <= 0: C1 = mu_s / 3, C2 = C1 / 2 */
+} fsi_nl_params;
+
+#define FSI_NL_MAX_NEWTON 32
+
+typedef struct {
+    double nl_rtol;             /* stop when ||R(U_k)||_2 <= nl_rtol ||R(U_0)||_2 */
+    int max_newton;             /* 1..FSI_NL_MAX_NEWTON */
+    double lin_rtol;            /* relative true-residual tolerance of every Newton system */
+    int restart, max_iters;     /* FGMRES restart length and iteration limit per system */
+} fsi_nl_opts;
+
+typedef struct {
+    int newton_steps;           /* s_i of Sec. 4: Newton steps taken */
+    int converged;              /* 1: the nonlinear tolerance was met */
+    int status;                 /* fsi_status of the call */
+    int lin_iterations[FSI_NL_MAX_NEWTON];   /* N_{i,s}: FGMRES iterations of Newton step s */
+    double lin_rho[FSI_NL_MAX_NEWTON];       /* rho_{i,s} = (r_N / r_0)^(1/N) of that solve */
+    double residual[FSI_NL_MAX_NEWTON + 1];  /* ||R(U_k)||_2, k = 0 .. newton_steps */
+    double jacobian_ms;         /* Jacobian assembly on all levels, coarse inverse (host clock) */
+    double setup_ms;            /* Schwarz block set-up and inversion */
+    double solve_ms;            /* FGMRES solves */
+    double total_ms;            /* the whole call */
+} fsi_nl_stats;
+
+/* fsi_nl_setup -- prepare the nonlinear residual on every problem of the
+ * context: element tables, colour lists, injection maps.  The hierarchy must
+ * have been built with fsi_hier_opts.nonlinear = 1 (FSI_ERR_STATE otherwise)
+ * and be 2D (FSI_ERR_ARG otherwise).  Densities, mu_f and dt come from the
+ * problem description. */
+fsi_status fsi_nl_setup(fsi_ctx *ctx, const fsi_nl_params *params);
+
+/* fsi_nl_residual -- R(U; U_n) at time t_new on level `level` (device
+ * float64 vectors of that level's dof count, J2 order). */
+fsi_status fsi_nl_residual(fsi_ctx *ctx, int prob, int level, const double *U, const double *Un,
+                           double t_new, double *R);
+
+/* fsi_nl_inject -- the state of level `level` - 1 from the state of level
+ * `level` >= 1 at the coinciding nodes (fixed dofs zero). */
+fsi_status fsi_nl_inject(fsi_ctx *ctx, int prob, int level, const double *U_fine, double *U_coarse);
+
+/* fsi_nl_jacobian -- replace every level operator of problem `prob` by the
+ * exact Jacobian dR/dU (fixed rows identity, fixed columns dropped) at U, U_n
+ * (level L-1; injected below) and refactor the coarse level.  Afterwards
+ * fsi_get_matrix returns the Jacobians; the smoothers must be set up again
+ * before a solve (FSI_ERR_STATE otherwise), and fsi_adjoint no longer offers
+ * dJ/dmu_s (the stored dA/dmu_s belongs to the linear operator). */
+fsi_status fsi_nl_jacobian(fsi_ctx *ctx, int prob, const double *U, const double *Un, double t_new);
+
+/* fsi_nl_step -- one time step to t_new by exact Newton from the initial
+ * guess in U (device, level L-1; on return the new state), U_n the state at
+ * t_new - dt.  Per Newton step: the Jacobians (fsi_nl_jacobian), the
+ * smoothers with the options of the last fsi_setup_smoothers call (which
+ * must have run once), FGMRES on J dU = -R from dU = 0, U += dU.  Returns
+ * FSI_ERR_NOT_CONVERGED when max_newton steps do not reach nl_rtol (stats
+ * filled, U the last iterate), or the status of a failing linear solve. */
+fsi_status fsi_nl_step(fsi_ctx *ctx, int prob, const double *Un, double *U, double t_new, const fsi_nl_opts *opts,
+                       fsi_nl_stats *stats);
 
 /* Release everything the context owns.  NULL is a no-op. */
 void fsi_destroy(fsi_ctx *ctx);

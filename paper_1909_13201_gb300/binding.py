@@ -27,7 +27,9 @@ EXPORTED = ["fsi_setup_hierarchy", "fsi_setup_smoothers", "fsi_solve", "fsi_solv
             "fsi_get_blocks", "fsi_apply_operator", "fsi_apply_smoother", "fsi_apply_vcycle",
             "fsi_setup_host_only", "fsi_get_pattern", "fsi_profile", "fsi_apply_smoother_noalloc",
             "fsi_get_cost", "fsi_autotune_layout",
-            "fsi_autotune", "fsi_get_block_passes", "fsi_destroy", "fsi_last_error"]
+            "fsi_autotune", "fsi_get_block_passes", "fsi_nl_setup", "fsi_nl_residual", "fsi_nl_inject",
+            "fsi_nl_jacobian", "fsi_nl_step", "fsi_destroy", "fsi_last_error"]
+FSI_NL_MAX_NEWTON = 32
 
 
 class FSIError(RuntimeError):
@@ -45,7 +47,30 @@ class Problem_t(C.Structure):
 
 
 class HierOpts_t(C.Structure):
-    _fields_ = [("restriction", C.c_int)]
+    _fields_ = [("restriction", C.c_int), ("nonlinear", C.c_int)]
+
+
+class NlParams_t(C.Structure):
+    _fields_ = [("force", C.c_double), ("period", C.c_double), ("C1", C.c_double), ("C2", C.c_double)]
+
+
+class NlOpts_t(C.Structure):
+    _fields_ = [("nl_rtol", C.c_double), ("max_newton", C.c_int), ("lin_rtol", C.c_double),
+                ("restart", C.c_int), ("max_iters", C.c_int)]
+
+
+class NlStats_t(C.Structure):
+    _fields_ = [("newton_steps", C.c_int), ("converged", C.c_int), ("status", C.c_int),
+                ("lin_iterations", C.c_int * FSI_NL_MAX_NEWTON), ("lin_rho", C.c_double * FSI_NL_MAX_NEWTON),
+                ("residual", C.c_double * (FSI_NL_MAX_NEWTON + 1)), ("jacobian_ms", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("total_ms", C.c_double)]
+
+    def to_dict(self):
+        k = self.newton_steps
+        return {"newton_steps": k, "converged": bool(self.converged), "status": self.status,
+                "iterations": list(self.lin_iterations[:k]), "rho": list(self.lin_rho[:k]),
+                "residuals": list(self.residual[:k + 1]), "jacobian_ms": self.jacobian_ms,
+                "setup_ms": self.setup_ms, "solve_ms": self.solve_ms, "total_ms": self.total_ms}
 
 
 class SmootherOpts_t(C.Structure):
@@ -109,6 +134,11 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     lib.fsi_get_cost.argtypes = [P, I, C.POINTER(D)]
     lib.fsi_autotune_layout.argtypes = [P, C.POINTER(I), I, C.POINTER(SolveOpts_t), C.POINTER(I), C.POINTER(D)]
     lib.fsi_autotune.argtypes = [P, C.POINTER(I), I, C.POINTER(SolveOpts_t), C.POINTER(I), C.POINTER(D)]
+    lib.fsi_nl_setup.argtypes = [P, C.POINTER(NlParams_t)]
+    lib.fsi_nl_residual.argtypes = [P, I, I, P, P, D, P]
+    lib.fsi_nl_inject.argtypes = [P, I, I, P, P]
+    lib.fsi_nl_jacobian.argtypes = [P, I, P, P, D]
+    lib.fsi_nl_step.argtypes = [P, I, P, P, D, C.POINTER(NlOpts_t), C.POINTER(NlStats_t)]
     lib.fsi_destroy.argtypes = [P]
     lib.fsi_destroy.restype = None
     lib.fsi_last_error.restype = C.c_char_p
@@ -143,7 +173,8 @@ class FSISolver:
     host_only=True builds only the host-side structure (no GPU needed) for
     inspection: sizes, dof maps, patterns, transfers and block sets."""
 
-    def __init__(self, problems, restriction: int = 0, stream=None, host_only=False, patch=None):
+    def __init__(self, problems, restriction: int = 0, stream=None, host_only=False, patch=None,
+                 nonlinear: bool = False):
         lib = load_library()
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -157,7 +188,7 @@ class FSISolver:
             arr[i] = Problem_t(p.dim, p.n_fine, p.n_levels, _ptr(mat, C.c_uint8), _ptr(adv, C.c_double),
                                p.mu_s, p.lambda_s, p.rho_s, p.rho_f, p.mu_f, p.dt, p.bc_preset)
         self.ctx = C.c_void_p()
-        ho = HierOpts_t(restriction)
+        ho = HierOpts_t(restriction, 1 if nonlinear else 0)
         if host_only:
             if len(problems) != 1:
                 raise ValueError("host-only inspection takes one problem")
@@ -286,6 +317,42 @@ class FSISolver:
                 "prolong_launches": int(out[18]), "prolong_ms": out[19], "prolong_bytes": out[20],
                 "fp64_gflops": out[21], "gs64_launches": int(out[22]), "gs64_ms": out[23], "gs64_fma": out[24],
                 "gs1_launches": int(out[25]), "gs1_ms": out[26], "gs1_bytes": out[27]}
+
+    # ------------------------------------------------------------ nonlinear
+    def nl_setup(self, force=20.0, period=1.0, C1=0.0, C2=0.0):
+        """Prepare the nonlinear residual (fsi_nl_setup); needs nonlinear=True
+        at construction.  C1 <= 0: C1 = mu_s / 3, C2 = C1 / 2."""
+        _check(load_library().fsi_nl_setup(self.ctx, C.byref(NlParams_t(force, period, C1, C2))))
+
+    def nl_residual(self, U, Un, t_new, level=None, prob=0):
+        import torch
+        level = self.n_levels - 1 if level is None else level
+        R = torch.empty_like(U)
+        _check(load_library().fsi_nl_residual(self.ctx, prob, level, _dptr(U), _dptr(Un), float(t_new), _dptr(R)))
+        return R
+
+    def nl_inject(self, U, level, prob=0):
+        """State of level - 1 injected from the state U of level."""
+        import torch
+        n = self.sizes(level - 1, prob)["n"]
+        Uc = torch.empty(n, dtype=torch.float64, device=U.device)
+        _check(load_library().fsi_nl_inject(self.ctx, prob, level, _dptr(U), _dptr(Uc)))
+        return Uc
+
+    def nl_jacobian(self, U, Un, t_new, prob=0):
+        """Replace the level operators by the Jacobians at U (fsi_nl_jacobian)."""
+        _check(load_library().fsi_nl_jacobian(self.ctx, prob, _dptr(U), _dptr(Un), float(t_new)))
+        self.precision = None
+
+    def nl_step(self, Un, U, t_new, nl_rtol=1e-8, max_newton=10, lin_rtol=1e-8, restart=30, max_iters=1000,
+                prob=0, check=True):
+        """One Newton time step in place on U (initial guess in, new state out)."""
+        st = NlStats_t()
+        o = NlOpts_t(nl_rtol, max_newton, lin_rtol, restart, max_iters)
+        s = load_library().fsi_nl_step(self.ctx, prob, _dptr(Un), _dptr(U), float(t_new), C.byref(o), C.byref(st))
+        if check:
+            _check(s)
+        return st.to_dict()
 
     # ------------------------------------------------------------ accessors
     @property

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfsi.so")
 SOURCES = ["host_setup.cpp", "kernels_fem.cu", "kernels_sparse.cu", "kernels_block.cu",
-           "kernels_gj_tc.cu", "kernels_krylov.cu", "api.cu"]
+           "kernels_gj_tc.cu", "kernels_krylov.cu", "kernels_nl.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3",
           "-I", os.path.join(HERE, "..", "include")]

@@ -735,6 +735,7 @@ fsi_status setup_problem(Context &cx, Problem &pb, const fsi_problem &in) {
     d.bc_preset = in.bc_preset;
     d.mu_s = in.mu_s; d.lambda_s = in.lambda_s; d.rho_s = in.rho_s;
     d.rho_f = in.rho_f; d.mu_f = in.mu_f; d.dt = in.dt;
+    d.nonlinear = cx.nonlinear;
     if (!in.material || !in.advection) { set_error("material/advection is NULL"); return FSI_ERR_ARG; }
     if (in.dim != 2 && in.dim != 3) { set_error("dim must be 2 or 3"); return FSI_ERR_ARG; }
     if (in.n_fine < 1 || in.n_fine > 4096) { set_error("n_fine out of range"); return FSI_ERR_ARG; }
@@ -1146,6 +1147,7 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
     }
     pb.transposes_ready = false;
     pb.m_alloc = 0;
+    pb.ops_changed = false;
     drop_graphs(pb);
     return FSI_OK;
 }
@@ -1211,6 +1213,8 @@ fsi_status fsi_setup_hierarchy(const fsi_problem *probs, int n_probs, const fsi_
     cx->stream = static_cast<cudaStream_t>(cuda_stream);
     cx->restriction = opts ? opts->restriction : 0;
     if (cx->restriction != 0 && cx->restriction != 1) { set_error("restriction must be 0 or 1"); return FSI_ERR_ARG; }
+    cx->nonlinear = opts ? opts->nonlinear : 0;
+    if (cx->nonlinear != 0 && cx->nonlinear != 1) { set_error("nonlinear must be 0 or 1"); return FSI_ERR_ARG; }
     FSI_CUDA(cudaDeviceGetAttribute(&cx->num_sms, cudaDevAttrMultiProcessorCount, cx->device));
     FSI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&cx->h_pinned), 64 * 8));
     FSI_CUDA(cudaStreamCreateWithFlags(&cx->work, cudaStreamNonBlocking));
@@ -1247,6 +1251,8 @@ fsi_status fsi_setup_host_only(const fsi_problem *prob, const fsi_hier_opts *opt
     cx->patch = patch;
     cx->restriction = opts ? opts->restriction : 0;
     if (cx->restriction != 0 && cx->restriction != 1) { set_error("restriction must be 0 or 1"); return FSI_ERR_ARG; }
+    cx->nonlinear = opts ? opts->nonlinear : 0;
+    if (cx->nonlinear != 0 && cx->nonlinear != 1) { set_error("nonlinear must be 0 or 1"); return FSI_ERR_ARG; }
     cx->probs.resize(1);
     FSI_TRY(setup_problem(*cx, cx->probs[0], *prob));
     *out = reinterpret_cast<fsi_ctx *>(cx.release());
@@ -1298,6 +1304,7 @@ fsi_status fsi_setup_smoothers(fsi_ctx *ctx, const fsi_smoother_opts *opts) {
     FSI_CUDA(cudaStreamSynchronize(cx->stream));
     if (!cx->ev_marks.empty()) collect_marks(*cx);
     cx->smoothers_ready = true;
+    cx->smoothers_configured = true;
     return FSI_OK;
 }
 
@@ -1818,6 +1825,10 @@ fsi_status fsi_adjoint(fsi_ctx *ctx, const double *w, const double *x, double *l
     if (s != FSI_OK && s != FSI_ERR_NOT_CONVERGED) return s;
     LevelDev &F = pb.dev.back();
     if (dA_vals) FSI_TRY(launch_pattern_grad(F.A, lambda, x, dA_vals, cx->stream));
+    if (dmu_s && !pb.dA_mu.p) {
+        set_error("dJ/dmu_s is not available: the operator is a Jacobian of the nonlinear residual");
+        return FSI_ERR_STATE;
+    }
     if (dmu_s) {
         // -lambda^T (dA/dmu_s) x
         FSI_TRY(launch_spmv<double, double, double>(F.A, pb.dA_mu.as<double>(), x, (const double *)nullptr,
@@ -2291,6 +2302,306 @@ void fsi_destroy(fsi_ctx *ctx) {
             if (c) cudaStreamDestroy(c);
     }
     delete cx;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ nonlinear
+// Sec. 2.2: the residual of the nonlinear monolithic formulation and exact
+// Newton on one time step.  Host code orders the launches (residual, norms,
+// Jacobians on every level, block set-up, FGMRES, update) and reads one
+// norm per Newton step; all arithmetic runs in the kernels.
+namespace fsi {
+namespace {
+
+// level-lc dof -> level-(lc+1) dof at the coinciding node (-1: none there)
+std::vector<int32_t> nl_injection(const LevelHost &F, const LevelHost &Cc) {
+    std::vector<int32_t> map((size_t)Cc.n_dofs, -1);
+    const int64_t mc2 = 2 * (int64_t)Cc.n + 1, mf2 = 2 * (int64_t)F.n + 1;
+    for (int64_t y = 0; y < Cc.nq2; ++y) {
+        const int64_t yf = (2 * (y / mc2)) * mf2 + 2 * (y % mc2);
+        for (int i = 0; i < 2; ++i) {
+            map[Cc.d_dof[y * 2 + i]] = F.d_dof[yf * 2 + i];
+            map[Cc.v_dof[y * 2 + i]] = F.v_dof[yf * 2 + i];
+        }
+    }
+    const int64_t mc1 = Cc.n + 1, mf1 = F.n + 1;
+    for (int64_t z = 0; z < Cc.nq1; ++z) {
+        const int64_t zf = (2 * (z / mc1)) * mf1 + 2 * (z % mc1);
+        if (Cc.ps_dof[z] >= 0) map[Cc.ps_dof[z]] = F.ps_dof[zf];
+        if (Cc.pf_dof[z] >= 0) map[Cc.pf_dof[z]] = F.pf_dof[zf];
+    }
+    return map;
+}
+
+fsi_status nl_setup_problem(Context &cx, Problem &pb, const fsi_nl_params &in) {
+    cudaStream_t s = cx.stream;
+    const ProblemDesc &d = pb.desc;
+    NlParams &P = pb.nl;
+    P.rho_s = d.rho_s;
+    P.rho_f = d.rho_f;
+    P.mu_f = d.mu_f;
+    P.dt = d.dt;
+    P.C1 = in.C1 > 0 ? in.C1 : d.mu_s / 3.0;
+    P.C2 = in.C1 > 0 ? in.C2 : P.C1 / 2.0;
+    P.k_ale = (double)d.n_fine * (double)d.n_fine;
+    P.force = in.force;
+    P.period = in.period;
+    const int L = (int)pb.host.size();
+    pb.nlev.clear();
+    pb.nlev.resize(L);
+    for (int l = 0; l < L; ++l) {
+        const LevelHost &H = pb.host[l];
+        NlLevelDev &N = pb.nlev[l];
+        N.n = H.n;
+        N.ds_end = (int32_t)H.off[1];
+        FSI_TRY(upload(N.elem_dofs, H.elem_dofs.data(), H.elem_dofs.size() * 4, s));
+        FSI_TRY(upload(N.material, H.material.data(), H.material.size(), s));
+        FSI_TRY(upload(N.w, H.w.data(), H.w.size() * 8, s));
+        // colours by the parity of the element coordinates; solid elements
+        // first inside a colour (warps of one material)
+        std::vector<int32_t> el;
+        el.reserve((size_t)H.n_el);
+        N.colour_ptr[0] = 0;
+        for (int c = 0; c < 4; ++c) {
+            for (int solid = 1; solid >= 0; --solid)
+                for (int64_t e = 0; e < H.n_el; ++e) {
+                    const int64_t ex = e % H.n, ey = e / H.n;
+                    if ((int)((ex & 1) + 2 * (ey & 1)) == c && (H.material[e] != 0) == (solid == 1))
+                        el.push_back((int32_t)e);
+                }
+            N.colour_ptr[c + 1] = (int64_t)el.size();
+        }
+        FSI_TRY(upload(N.elems, el.data(), el.size() * 4, s));
+        if (l + 1 < L) {
+            const std::vector<int32_t> map = nl_injection(pb.host[l + 1], H);
+            FSI_TRY(upload(N.inj, map.data(), map.size() * 4, s));
+            FSI_TRY(N.U.alloc((size_t)H.n_dofs * 8));
+            FSI_TRY(N.Un.alloc((size_t)H.n_dofs * 8));
+        }
+    }
+    const int64_t n = pb.dev.back().n;
+    FSI_TRY(pb.nl_R.alloc((size_t)n * 8));
+    FSI_TRY(pb.nl_dU.alloc((size_t)n * 8));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    pb.nl_ready = true;
+    return FSI_OK;
+}
+
+// Jacobians of every level at U (level L-1) and the injected states, then
+// the derived data of the operators: ELL values, coarse inverse; float32
+// copies, transposes and the cascade's operators are rebuilt on demand.
+fsi_status nl_assemble(Context &cx, Problem &pb, const double *U, const double *Un, double t_new) {
+    cudaStream_t s = cx.stream;
+    const int L = (int)pb.dev.size();
+    std::vector<const double *> Us(L), Uns(L);
+    Us[L - 1] = U;
+    Uns[L - 1] = Un;
+    for (int l = L - 2; l >= 0; --l) {
+        NlLevelDev &N = pb.nlev[l];
+        const uint8_t *fx = pb.dev[l].fixed.as<uint8_t>();
+        FSI_TRY(launch_nl_inject(N.inj.as<int32_t>(), fx, Us[l + 1], N.U.as<double>(), pb.dev[l].n, s));
+        FSI_TRY(launch_nl_inject(N.inj.as<int32_t>(), fx, Uns[l + 1], N.Un.as<double>(), pb.dev[l].n, s));
+        Us[l] = N.U.as<double>();
+        Uns[l] = N.Un.as<double>();
+    }
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    for (int l = 0; l < L; ++l) {
+        LevelDev &D = pb.dev[l];
+        FSI_TRY(launch_nl_jacobian(pb.nlev[l], pb.nl, D.fixed.as<uint8_t>(), D.A, Us[l], Uns[l], t_new,
+                                   cx.flags.as<int>() + 3, s));
+        FSI_TRY(ell_refill(D.A, s));
+        D.A.val32.release();                   // float32 copies follow the new values
+        D.A.ell.val32.release();
+    }
+    int fw[4] = {0, 0, 0, 0};
+    FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    if (fw[3]) {
+        set_error("nonlinear Jacobian has an entry outside the operator pattern");
+        return FSI_ERR_STATE;
+    }
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    FSI_TRY(coarse_invert(pb.dev[0].A, pb.n0, pb.coarse_inv.as<double>(), cx.flags.as<int>(), s));
+    int flag = 0;
+    FSI_TRY(read_flag(cx, &flag));
+    if (flag) {
+        set_error("coarse-level Jacobian is singular");
+        return FSI_ERR_ZERO_PIVOT;
+    }
+    pb.coarse_inv_t.release();
+    pb.coarse_inv_c.release();
+    pb.coarse_inv_ct.release();
+    pb.transposes_ready = false;
+    pb.cascade_ready = false;
+    pb.dA_mu.release();
+    pb.ops_changed = true;
+    cx.smoothers_ready = false;
+    return FSI_OK;
+}
+
+// ||v||_2 on the host
+fsi_status nl_norm(Context &cx, Problem &pb, const double *v, int64_t n, double *out) {
+    FSI_TRY(norm2_to_host(cx, pb, v, n, 9));
+    FSI_CUDA(cudaStreamSynchronize(cx.stream));
+    *out = std::sqrt(pb.h_scal[9]);
+    return FSI_OK;
+}
+
+Problem *nl_problem(fsi_ctx *ctx, int prob) {
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || cx->host_only || prob < 0 || prob >= (int)cx->probs.size()) return nullptr;
+    return &cx->probs[prob];
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_nl_setup(fsi_ctx *ctx, const fsi_nl_params *params) {
+    g_last_error.clear();
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    if (!cx || !params) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (cx->host_only) { set_error("host-only context"); return FSI_ERR_STATE; }
+    if (!cx->nonlinear) {
+        set_error("the hierarchy was built without nonlinear patterns (fsi_hier_opts.nonlinear = 1)");
+        return FSI_ERR_STATE;
+    }
+    if (!(params->period > 0) || !std::isfinite(params->force) || params->C2 < 0) {
+        set_error("nonlinear parameters out of range");
+        return FSI_ERR_ARG;
+    }
+    for (auto &pb : cx->probs)
+        if (pb.desc.dim != 2) { set_error("the nonlinear residual is 2D"); return FSI_ERR_ARG; }
+    DeviceGuard guard(cx->device);
+    FSI_TRY(nl_upload_tables(cx->stream));
+    for (auto &pb : cx->probs) FSI_TRY(nl_setup_problem(*cx, pb, *params));
+    return FSI_OK;
+}
+
+fsi_status fsi_nl_residual(fsi_ctx *ctx, int prob, int level, const double *U, const double *Un, double t_new,
+                           double *R) {
+    g_last_error.clear();
+    Problem *pb = nl_problem(ctx, prob);
+    if (!pb || !U || !Un || !R || level < 0 || level >= (int)pb->dev.size()) {
+        set_error("invalid arguments");
+        return FSI_ERR_ARG;
+    }
+    if (!pb->nl_ready) { set_error("fsi_nl_setup has not run"); return FSI_ERR_STATE; }
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    DeviceGuard guard(cx->device);
+    LevelDev &D = pb->dev[level];
+    FSI_TRY(launch_nl_residual(pb->nlev[level], pb->nl, D.fixed.as<uint8_t>(), D.n, U, Un, t_new, R, cx->stream));
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    return FSI_OK;
+}
+
+fsi_status fsi_nl_inject(fsi_ctx *ctx, int prob, int level, const double *U_fine, double *U_coarse) {
+    g_last_error.clear();
+    Problem *pb = nl_problem(ctx, prob);
+    if (!pb || !U_fine || !U_coarse || level < 1 || level >= (int)pb->dev.size()) {
+        set_error("invalid arguments");
+        return FSI_ERR_ARG;
+    }
+    if (!pb->nl_ready) { set_error("fsi_nl_setup has not run"); return FSI_ERR_STATE; }
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    DeviceGuard guard(cx->device);
+    FSI_TRY(launch_nl_inject(pb->nlev[level - 1].inj.as<int32_t>(), pb->dev[level - 1].fixed.as<uint8_t>(), U_fine,
+                             U_coarse, pb->dev[level - 1].n, cx->stream));
+    FSI_CUDA(cudaStreamSynchronize(cx->stream));
+    return FSI_OK;
+}
+
+fsi_status fsi_nl_jacobian(fsi_ctx *ctx, int prob, const double *U, const double *Un, double t_new) {
+    g_last_error.clear();
+    Problem *pb = nl_problem(ctx, prob);
+    if (!pb || !U || !Un) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!pb->nl_ready) { set_error("fsi_nl_setup has not run"); return FSI_ERR_STATE; }
+    Context *cx = reinterpret_cast<Context *>(ctx);
+    DeviceGuard guard(cx->device);
+    return nl_assemble(*cx, *pb, U, Un, t_new);
+}
+
+fsi_status fsi_nl_step(fsi_ctx *ctx, int prob, const double *Un, double *U, double t_new, const fsi_nl_opts *o,
+                       fsi_nl_stats *st) {
+    g_last_error.clear();
+    const auto t_call = std::chrono::steady_clock::now();
+    Problem *pbp = nl_problem(ctx, prob);
+    if (!pbp || !Un || !U || !o) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!(o->nl_rtol >= 0) || o->max_newton < 1 || o->max_newton > FSI_NL_MAX_NEWTON || !(o->lin_rtol > 0) ||
+        o->restart < 1 || o->restart > 64 || o->max_iters < 1) {
+        set_error("Newton options out of range");
+        return FSI_ERR_ARG;
+    }
+    Problem &pb = *pbp;
+    Context &cx = *reinterpret_cast<Context *>(ctx);
+    if (!pb.nl_ready) { set_error("fsi_nl_setup has not run"); return FSI_ERR_STATE; }
+    if (!cx.smoothers_configured) { set_error("fsi_setup_smoothers has not run"); return FSI_ERR_STATE; }
+    DeviceGuard guard(cx.device);
+    fsi_nl_stats S;
+    std::memset(&S, 0, sizeof(S));
+    cudaStream_t s = cx.stream;
+    LevelDev &F = pb.dev.back();
+    const int64_t n = F.n;
+    FSI_TRY(ensure_workspace(cx, pb, o->restart));
+    double *R = pb.nl_R.as<double>(), *dU = pb.nl_dU.as<double>();
+    FSI_TRY(launch_nl_residual(pb.nlev.back(), pb.nl, F.fixed.as<uint8_t>(), n, U, Un, t_new, R, s));
+    double res = 0.0;
+    FSI_TRY(nl_norm(cx, pb, R, n, &res));
+    const double r0 = res;
+    S.residual[0] = res;
+    fsi_status status = FSI_ERR_NOT_CONVERGED;
+    fsi_solve_opts lo{};
+    lo.rtol = o->lin_rtol;
+    lo.restart = o->restart;
+    lo.max_iters = o->max_iters;
+    lo.use_x0 = 0;
+    for (int k = 0;; ++k) {
+        if (!std::isfinite(res)) { status = FSI_ERR_NONFINITE; set_error("non-finite nonlinear residual"); break; }
+        if (res <= o->nl_rtol * std::max(r0, 1e-300) || res == 0.0) { status = FSI_OK; S.converged = 1; break; }
+        if (k == o->max_newton) break;
+        auto t0 = std::chrono::steady_clock::now();
+        fsi_status e = nl_assemble(cx, pb, U, Un, t_new);
+        S.jacobian_ms += ms_since(t0);
+        if (e != FSI_OK) { status = e; break; }
+        t0 = std::chrono::steady_clock::now();
+        e = setup_smoothers_problem(cx, pb);
+        if (e == FSI_OK) {
+            cudaError_t ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); e = FSI_ERR_CUDA; }
+        }
+        S.setup_ms += ms_since(t0);
+        if (e != FSI_OK) { status = e; break; }
+        cx.smoothers_ready = std::none_of(cx.probs.begin(), cx.probs.end(),
+                                          [](const Problem &q) { return q.ops_changed; });
+        FSI_TRY(launch_nl_axpby(R, R, -1.0, 0.0, n, s));      // R <- -R
+        t0 = std::chrono::steady_clock::now();
+        fsi_solve_stats ls{};
+        e = solve_one(cx, pb, R, dU, &lo, &ls, false);
+        S.solve_ms += ms_since(t0);
+        S.lin_iterations[k] = ls.iterations;
+        S.lin_rho[k] = ls.rho;
+        S.newton_steps = k + 1;
+        if (e != FSI_OK) { status = e; break; }
+        FSI_TRY(launch_nl_axpby(U, dU, 1.0, 1.0, n, s));      // U <- U + dU
+        FSI_TRY(launch_nl_residual(pb.nlev.back(), pb.nl, F.fixed.as<uint8_t>(), n, U, Un, t_new, R, s));
+        FSI_TRY(nl_norm(cx, pb, R, n, &res));
+        S.residual[k + 1] = res;
+    }
+    FSI_CUDA(cudaStreamSynchronize(s));
+    S.status = status;
+    S.total_ms = ms_since(t_call);
+    if (st) *st = S;
+    if (status == FSI_ERR_NOT_CONVERGED && g_last_error.empty())
+        set_error("Newton did not reach the nonlinear tolerance in max_newton steps");
+    return status;
 }
 
 }  // extern "C"

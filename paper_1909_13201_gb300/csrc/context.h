@@ -120,6 +120,7 @@ struct DevEll {
     DevBuf perm;                    // int32[n_rows]: CSR row of each sorted position
     DevBuf col;                     // int32[size]
     DevBuf val64, val32;            // copies of the CSR val64 / val32
+    DevBuf fbase, fstride;          // fill map: first ELL position (int64) and stride (int32) of every CSR row
 };
 
 // CSR on the device: int32 row pointers and columns, float64 values and
@@ -199,6 +200,30 @@ struct FgState {
     double bnorm = 0.0, beta = 0.0, r0 = 0.0;
 };
 
+// Nonlinear problem (Sec. 2.2): physical data of the residual
+struct NlParams {
+    double rho_s = 1, rho_f = 1, mu_f = 1, dt = 1;
+    double C1 = 0, C2 = 0;      // Mooney-Rivlin constants
+    double k_ale = 1;           // harmonic-extension coefficient (1/V_el of the fine element)
+    double force = 0, period = 1;   // body force F0 sin(2 pi t / period) w(x)
+};
+
+// Per level of the nonlinear problem: element tables, elements by colour
+// (parity of the element coordinates; solid elements first inside a
+// colour), the injection map from the next finer level and the injected
+// states of the coarse levels.
+struct NlLevelDev {
+    int n = 0;
+    int32_t ds_end = 0;             // first d^f dof
+    DevBuf elem_dofs;               // int32 n_el x 40
+    DevBuf material;                // uint8 n_el
+    DevBuf w;                       // float64 2 x nq2: spatial profile of the body force
+    DevBuf elems;                   // int32 n_el, colour-major
+    int64_t colour_ptr[5] = {0, 0, 0, 0, 0};
+    DevBuf inj;                     // int32 n (l < L-1): dof of level l+1 at the coinciding node, -1 none
+    DevBuf U, Un;                   // float64 states (l < L-1: injected)
+};
+
 struct Problem {
     ProblemDesc desc;
     int patch = 1;                   // Vanka group edge of this problem's smoothers
@@ -230,6 +255,12 @@ struct Problem {
     DevBuf fg, bbuf, xbuf, zbuf;
     FgState *h_fg = nullptr;         // pinned: [0] parameters in, [1] state out
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // nonlinear problem (fsi_nl_setup)
+    bool nl_ready = false;
+    bool ops_changed = false;        // operators replaced since this problem's smoothers were set up
+    NlParams nl;
+    std::vector<NlLevelDev> nlev;    // index = level
+    DevBuf nl_R, nl_dU;              // fine residual (negated for the solve) and Newton update
 };
 
 // kernels launched by the library (all contexts), for launch accounting
@@ -267,6 +298,7 @@ struct Context {
     int device = 0;
     cudaStream_t stream = nullptr;
     int restriction = 0;
+    int nonlinear = 0;               // patterns of the nonlinear residual's Jacobian
     int precision = FSI_FP64;
     int patch = 1;
     double omega = 1.0;
@@ -278,6 +310,7 @@ struct Context {
     int ell_lanes = 0;               // lanes per row of every ELL copy (0: size rule; fsi_autotune_layout)
     void *cublas = nullptr;          // cuBLAS handle (batched GEMMs of the split inversion of large AS blocks)
     bool smoothers_ready = false;
+    bool smoothers_configured = false;   // fsi_setup_smoothers completed once (its options are set)
     bool host_only = false;          // inspection context without device state
     std::vector<Problem> probs;
     DevBuf flags;                    // int32[4]: zero pivot, nonfinite, ...
@@ -419,5 +452,18 @@ fsi_status launch_pattern_grad(const DevCSR &A, const double *lam, const double 
 fsi_status launch_jacobi_setup(const DevCSR &A, const int32_t *idx, int64_t n, double *d64, float *d32,
                                cudaStream_t s);
 fsi_status launch_set_fixed_diag(const DevCSR &A, const uint8_t *fixed, double *val, cudaStream_t s);
+
+// nonlinear residual and exact Jacobian (kernels_nl.cu)
+fsi_status nl_upload_tables(cudaStream_t s);
+fsi_status launch_nl_residual(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, int64_t n_dofs,
+                              const double *U, const double *Un, double t_new, double *R, cudaStream_t s);
+fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, const DevCSR &A,
+                              const double *U, const double *Un, double t_new, int *err, cudaStream_t s);
+fsi_status launch_nl_inject(const int32_t *map, const uint8_t *fixed_c, const double *Uf, double *Uc, int64_t nc,
+                            cudaStream_t s);
+// y = a x + b y (float64)
+fsi_status launch_nl_axpby(double *y, const double *x, double a, double b, int64_t n, cudaStream_t s);
+// re-fill the float64 (and, when present, float32) values of A's binned-ELL copy from its CSR values
+fsi_status ell_refill(DevCSR &A, cudaStream_t s);
 
 }  // namespace fsi

@@ -338,6 +338,8 @@ static void build_pattern(LevelHost &L) {
                     }
                 } else {                               // W row (p^f): fluid elements
                     if (!se) add_range(V0, P0);
+                    // on the moving fluid element div_x u depends on d through F
+                    if (!se && L.nl_pattern) add_range(D0, V0);
                 }
             }
             std::vector<int32_t> out;
@@ -390,6 +392,7 @@ std::string build_levels(const ProblemDesc &p, std::vector<LevelHost> &levels) {
         lev.dim = dim;
         lev.n = p.n_fine >> (L - 1 - l);
         lev.material = mats[l];
+        lev.nl_pattern = p.nonlinear != 0;
         fill_level(lev, p);
         build_pattern(lev);
     }

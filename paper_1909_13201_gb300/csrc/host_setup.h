@@ -36,6 +36,7 @@ struct LevelHost {
     std::vector<int32_t> elem_dofs;         // n_el * nloc local-to-global map (-1 none)
     int nloc = 0;                           // 2 * 3^dim * dim + 2^dim
     HostCSR pattern;                        // sparsity of A_l (fixed rows: diagonal only)
+    bool nl_pattern = false;                // W rows also couple to d (Jacobian of the nonlinear residual)
     int64_t group_of(int64_t dof) const;
 };
 
@@ -44,6 +45,7 @@ struct ProblemDesc {
     std::vector<uint8_t> material;
     std::vector<double> advection;          // dim * nq2_fine
     double mu_s, lambda_s, rho_s, rho_f, mu_f, dt;
+    int nonlinear = 0;                      // patterns of the nonlinear residual's Jacobian (Sec. 2.2)
 };
 
 // Build levels 0 (coarse) .. L-1 (fine) with numbering, fixed sets,

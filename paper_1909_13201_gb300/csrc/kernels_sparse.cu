@@ -380,7 +380,33 @@ fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent, int force_G) {
         count_launch();
         FSI_CUDA(cudaGetLastError());
     }
-    FSI_CUDA(cudaStreamSynchronize(s));   // temporaries and host vectors go out of scope
+    E.fbase = std::move(dbase);           // kept: refills after the CSR values change
+    E.fstride = std::move(dstride);
+    FSI_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    return FSI_OK;
+}
+
+// new CSR values, same pattern: re-fill the ELL copy's float64 values (and
+// its float32 values when both float32 copies exist) through the fill map
+fsi_status ell_refill(DevCSR &A, cudaStream_t s) {
+    DevEll &E = A.ell;
+    if (E.nbins == 0) return FSI_OK;
+    if (!E.fbase.p) { set_error("ELL copy without a fill map"); return FSI_ERR_STATE; }
+    const int64_t n = A.n_rows;
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    ell_fill_kernel<double><<<(unsigned)g, 256, 0, s>>>(n, A.ptr.as<int32_t>(), A.col.as<int32_t>(),
+                                                         A.val64.as<double>(), E.fbase.as<int64_t>(),
+                                                         E.fstride.as<int32_t>(), nullptr, E.val64.as<double>());
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    if (E.val32.p && A.val32.p) {
+        ell_fill_kernel<float><<<(unsigned)g, 256, 0, s>>>(n, A.ptr.as<int32_t>(), A.col.as<int32_t>(),
+                                                            A.val32.as<float>(), E.fbase.as<int64_t>(),
+                                                            E.fstride.as<int32_t>(), nullptr, E.val32.as<float>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
     return FSI_OK;
 }
 
@@ -388,6 +414,11 @@ fsi_status build_ell(DevCSR &A, cudaStream_t s, bool concurrent, int force_G) {
 fsi_status ell_fill_f32(DevCSR &A, cudaStream_t s) {
     DevEll &E = A.ell;
     if (E.nbins == 0 || E.val32.p || !A.val32.p) return FSI_OK;
+    if (E.fbase.p) {
+        FSI_TRY(E.val32.alloc((size_t)E.size * 4));
+        FSI_CUDA(cudaMemsetAsync(E.val32.p, 0, (size_t)E.size * 4, s));
+        return ell_refill(A, s);
+    }
     // the ELL position of CSR entry k is recovered from the float64 copy's
     // layout: rebuild the per-row bases from the bins (host)
     const int64_t n = A.n_rows;
