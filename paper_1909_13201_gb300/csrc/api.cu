@@ -664,6 +664,7 @@ fsi_status check_opts(const fsi_solve_opts *o) {
 fsi_status build_transposes(Context &cx, Problem &pb) {
     if (pb.transposes_ready) return FSI_OK;
     cudaStream_t s = cx.stream;
+    drop_graphs(pb);     // transposed copies are (re)allocated below
     if (!pb.coarse_inv_t.p) {
         FSI_TRY(pb.coarse_inv_t.alloc((size_t)pb.n0 * pb.n0 * 8));
         FSI_TRY(launch_transpose(pb.coarse_inv.as<double>(), pb.n0, pb.coarse_inv_t.as<double>(), s));
@@ -880,6 +881,56 @@ fsi_status build_cascade(Context &cx, Problem &pb) {
         return FSI_ERR_ZERO_PIVOT;
     }
     pb.cascade_ready = true;
+    return FSI_OK;
+}
+
+// the smoother options a set-up was built with
+std::vector<double> smoother_signature(const Context &cx) {
+    return {(double)cx.precision, (double)cx.patch, cx.omega, (double)cx.nu_pre, (double)cx.nu_post,
+            (double)cx.factor, (double)cx.variant, (double)cx.mult_levels, (double)cx.cascade,
+            (double)cx.ell_lanes};
+}
+
+// Gather and invert the Schwarz blocks of level l (l >= 1) with the
+// context's factor method into the level's existing inverse storage.
+fsi_status invert_level_blocks(Context &cx, Problem &pb, size_t l) {
+    cudaStream_t s = cx.stream;
+    LevelDev &D = pb.dev[l];
+    const LevelHost &H = pb.host[l];
+    const int store = D.inv_store;
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    int method = cx.factor;
+    if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
+    {
+        ProfMark pm(cx, 3, l + 1 == pb.dev.size());
+        // monolithic (AS) blocks beyond one cluster: the split inversion over
+        // the two field systems, float32 inverses
+        int cq = 0, rq = 0;
+        size_t smq = 0;
+        const bool split = cx.variant == FSI_SMOOTHER_AS && !gj_tc_plan((int)D.max_block, &cq, &rq, &smq);
+        if (split) {
+            if (store != 1) {
+                set_error("AS blocks of " + std::to_string(D.max_block) +
+                          " dofs are inverted by the split method, which needs FSI_MIXED (float32 inverses)");
+                return FSI_ERR_ARG;
+            }
+            FSI_TRY(launch_block_invert_schur(cx, D.A, D, H.off[3], method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
+        } else if (method == FSI_FACTOR_FP64)
+            FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
+        else
+            FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
+    }
+    int fw[3] = {0, 0, 0};
+    FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
+    FSI_CUDA(cudaStreamSynchronize(s));
+    if (fw[2]) {   // a bounded tensor-core wait of the factorisation gave up
+        set_error("block factorisation on level " + std::to_string(l) + " timed out waiting for the tensor cores");
+        return FSI_ERR_CUDA;
+    }
+    if (fw[0]) {
+        set_error("a Schwarz block on level " + std::to_string(l) + " is singular");
+        return FSI_ERR_ZERO_PIVOT;
+    }
     return FSI_OK;
 }
 
@@ -1111,44 +1162,42 @@ fsi_status setup_smoothers_problem(Context &cx, Problem &pb) {
                 D.fj.release();
             }
         }
-        FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
-        int method = cx.factor;
-        if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
-        {
-            ProfMark pm(cx, 3, l + 1 == pb.dev.size());
-            // monolithic (AS) blocks beyond one cluster: the split inversion over
-            // the two field systems, float32 inverses
-            int cq = 0, rq = 0;
-            size_t smq = 0;
-            const bool split = cx.variant == FSI_SMOOTHER_AS && !gj_tc_plan((int)D.max_block, &cq, &rq, &smq);
-            if (split) {
-                if (store != 1) {
-                    set_error("AS blocks of " + std::to_string(D.max_block) +
-                              " dofs are inverted by the split method, which needs FSI_MIXED (float32 inverses)");
-                    return FSI_ERR_ARG;
-                }
-                FSI_TRY(launch_block_invert_schur(cx, D.A, D, H.off[3], method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
-            } else if (method == FSI_FACTOR_FP64)
-                FSI_TRY(launch_block_invert(D.A, D, store, cx.flags.as<int>(), s, cx.num_sms));
-            else
-                FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
-        }
-        int fw[3] = {0, 0, 0};
-        FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
-        FSI_CUDA(cudaStreamSynchronize(s));
-        if (fw[2]) {   // a bounded tensor-core wait of the factorisation gave up
-            set_error("block factorisation on level " + std::to_string(l) + " timed out waiting for the tensor cores");
-            return FSI_ERR_CUDA;
-        }
-        if (fw[0]) {
-            set_error("a Schwarz block on level " + std::to_string(l) + " is singular");
-            return FSI_ERR_ZERO_PIVOT;
-        }
+        FSI_TRY(invert_level_blocks(cx, pb, l));
     }
     pb.transposes_ready = false;
     pb.m_alloc = 0;
     pb.ops_changed = false;
+    pb.smoother_sig = smoother_signature(cx);
     drop_graphs(pb);
+    return FSI_OK;
+}
+
+// New operator values with the smoother options and patterns of the last
+// full set-up: refresh in place what derives from the values (float32
+// copies, ELL values of the sweep passes, Jacobi rows, block inverses), so
+// every buffer keeps its address and captured solve graphs stay valid.
+// Anything else (first set-up, changed options, the swapped cascade, whose
+// operators are rebuilt from the values) takes the full set-up.
+fsi_status refactor_smoothers(Context &cx, Problem &pb) {
+    if (pb.smoother_sig.empty() || pb.smoother_sig != smoother_signature(cx) || cx.cascade)
+        return setup_smoothers_problem(cx, pb);
+    cudaStream_t s = cx.stream;
+    const bool mixed = cx.precision != FSI_FP64;
+    for (size_t l = 0; l < pb.dev.size(); ++l) {
+        LevelDev &D = pb.dev[l];
+        if (mixed) FSI_TRY(make_f32(D.A, s));      // no-op when the float32 copy exists (kept current)
+        if (l == 0) continue;
+        FSI_TRY(launch_jacobi_setup(D.A, D.jac_idx.as<int32_t>(), D.n_jac, mixed ? nullptr : D.jac_inv.as<double>(),
+                                    mixed ? D.jac_inv.as<float>() : nullptr, s));
+        if (D.mult) {
+            for (auto &P : D.passes)
+                FSI_TRY(ell_subset_refill(D.A, P.ell, D.keep[P.field].as<uint8_t>(), s));
+            D.mult_t_ready = false;
+        }
+        FSI_TRY(invert_level_blocks(cx, pb, l));
+    }
+    pb.transposes_ready = false;
+    pb.ops_changed = false;
     return FSI_OK;
 }
 
@@ -2410,9 +2459,9 @@ fsi_status nl_assemble(Context &cx, Problem &pb, const double *U, const double *
         LevelDev &D = pb.dev[l];
         FSI_TRY(launch_nl_jacobian(pb.nlev[l], pb.nl, D.fixed.as<uint8_t>(), D.A, Us[l], Uns[l], t_new,
                                    cx.flags.as<int>() + 3, s));
+        if (D.A.val32.p)                       // float32 copy in place (its address is in captured graphs)
+            FSI_TRY(launch_cast_f64_f32(D.A.val64.as<double>(), D.A.val32.as<float>(), D.A.nnz, s));
         FSI_TRY(ell_refill(D.A, s));
-        D.A.val32.release();                   // float32 copies follow the new values
-        D.A.ell.val32.release();
     }
     int fw[4] = {0, 0, 0, 0};
     FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
@@ -2572,7 +2621,7 @@ fsi_status fsi_nl_step(fsi_ctx *ctx, int prob, const double *Un, double *U, doub
         S.jacobian_ms += ms_since(t0);
         if (e != FSI_OK) { status = e; break; }
         t0 = std::chrono::steady_clock::now();
-        e = setup_smoothers_problem(cx, pb);
+        e = refactor_smoothers(cx, pb);
         if (e == FSI_OK) {
             cudaError_t ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); e = FSI_ERR_CUDA; }

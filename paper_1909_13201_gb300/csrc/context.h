@@ -258,6 +258,7 @@ struct Problem {
     // nonlinear problem (fsi_nl_setup)
     bool nl_ready = false;
     bool ops_changed = false;        // operators replaced since this problem's smoothers were set up
+    std::vector<double> smoother_sig;   // options of the last full smoother set-up (empty: none)
     NlParams nl;
     std::vector<NlLevelDev> nlev;    // index = level
     DevBuf nl_R, nl_dU;              // fine residual (negated for the solve) and Newton update
@@ -465,5 +466,7 @@ fsi_status launch_nl_inject(const int32_t *map, const uint8_t *fixed_c, const do
 fsi_status launch_nl_axpby(double *y, const double *x, double a, double b, int64_t n, cudaStream_t s);
 // re-fill the float64 (and, when present, float32) values of A's binned-ELL copy from its CSR values
 fsi_status ell_refill(DevCSR &A, cudaStream_t s);
+// the same for a row-subset copy built by build_ell_subset (same column mask)
+fsi_status ell_subset_refill(const DevCSR &A, DevEll &E, const uint8_t *d_keep, cudaStream_t s);
 
 }  // namespace fsi

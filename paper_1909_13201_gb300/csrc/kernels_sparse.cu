@@ -607,7 +607,35 @@ fsi_status build_ell_subset(const DevCSR &A, const HostCSR &pat, const std::vect
         count_launch();
         FSI_CUDA(cudaGetLastError());
     }
+    E.fbase = std::move(dbase);           // kept: refills after the CSR values change
+    E.fstride = std::move(dstride);
     FSI_CUDA(cudaStreamSynchronize(s));
+    return FSI_OK;
+}
+
+// new CSR values, same pattern: re-fill the values of a row-subset copy in place
+fsi_status ell_subset_refill(const DevCSR &A, DevEll &E, const uint8_t *d_keep, cudaStream_t s) {
+    const int64_t n = E.perm.p ? (int64_t)(E.perm.bytes / 4) : 0;
+    if (E.nbins == 0 || n == 0) return FSI_OK;
+    if (!E.fbase.p) { set_error("ELL subset copy without a fill map"); return FSI_ERR_STATE; }
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (E.val64.p && A.val64.p) {
+        ell_fill_subset_kernel<double><<<(unsigned)g, 256, 0, s>>>(n, E.perm.as<int32_t>(), A.ptr.as<int32_t>(),
+                                                                   A.col.as<int32_t>(), A.val64.as<double>(), d_keep,
+                                                                   E.fbase.as<int64_t>(), E.fstride.as<int32_t>(),
+                                                                   nullptr, E.val64.as<double>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
+    if (E.val32.p && A.val32.p) {
+        ell_fill_subset_kernel<float><<<(unsigned)g, 256, 0, s>>>(n, E.perm.as<int32_t>(), A.ptr.as<int32_t>(),
+                                                                  A.col.as<int32_t>(), A.val32.as<float>(), d_keep,
+                                                                  E.fbase.as<int64_t>(), E.fstride.as<int32_t>(),
+                                                                  nullptr, E.val32.as<float>());
+        count_launch();
+        FSI_CUDA(cudaGetLastError());
+    }
     return FSI_OK;
 }
 
