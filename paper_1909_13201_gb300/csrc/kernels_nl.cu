@@ -116,10 +116,14 @@ template <int KIND> struct Ty {
 
 // quantities interpolated at one quadrature point of one element
 struct QV {
-    double dq[2], gd[4], dnq[2], gdn[4];     // d, grad_X d (i-major: [i][J]); old state
-    double uq[2], gu[4], hu[6], unq[2], gun[4];   // u, grad_X u, Hessian [i][xx, yy, xy]; old u, grad
+    double dq[2], gd[4], dnq[2];             // d, grad_X d (i-major: [i][J]); old d
+    double uq[2], gu[4], hu[6], unq[2];      // u, grad_X u, Hessian [i][xx, yy, xy]; old u
     double pq, gp[2];                        // p, grad_X p
     double fn[2], fo[2];                     // body force at t_new and t_new - dt
+    double J, Fi[4];                         // new state: det F, F^{-1} (row-major)
+    double Jn, y[4];                         // old state: det F_n, grad_x u_n (fluid)
+    double bo[4];                            // old-state part of B: solid 1/2 P_el(F_n),
+                                             // fluid 1/2 J_n sigma_n F_n^{-T}
 };
 
 // gathered local values of one element
@@ -164,43 +168,6 @@ DEV void load_element(const NlArgs &A, int64_t e, EV &E) {
     }
 }
 
-DEV void interpolate(const NlArgs &A, const double *d, const double *dn, const double *u, const double *un,
-                     const double *p, const double *w, int q, QV &Q) {
-    const double ih = A.ih, ih2 = A.ih * A.ih;
-    for (int i = 0; i < 2; ++i) {
-        double s0 = 0, s1 = 0, s2 = 0, s3 = 0, g0 = 0, g1 = 0, gn0 = 0, gn1 = 0;
-        double hu0 = 0, hu1 = 0, hu2 = 0, gu0 = 0, gu1 = 0, gun0 = 0, gun1 = 0, f = 0;
-        for (int a = 0; a < 9; ++a) {
-            const double ph = c_phi[q * 9 + a], dx = c_dphi[(q * 2) * 9 + a], dy = c_dphi[(q * 2 + 1) * 9 + a];
-            const double da = d[2 * a + i], dna = dn[2 * a + i], ua = u[2 * a + i], una = un[2 * a + i];
-            s0 += da * ph; s1 += dna * ph; s2 += ua * ph; s3 += una * ph;
-            g0 += da * dx; g1 += da * dy; gn0 += dna * dx; gn1 += dna * dy;
-            gu0 += ua * dx; gu1 += ua * dy; gun0 += una * dx; gun1 += una * dy;
-            hu0 += ua * c_ddphi[(q * 3) * 9 + a];
-            hu1 += ua * c_ddphi[(q * 3 + 1) * 9 + a];
-            hu2 += ua * c_ddphi[(q * 3 + 2) * 9 + a];
-            f += w[2 * a + i] * ph;
-        }
-        Q.dq[i] = s0; Q.dnq[i] = s1; Q.uq[i] = s2; Q.unq[i] = s3;
-        Q.gd[2 * i] = g0 * ih; Q.gd[2 * i + 1] = g1 * ih;
-        Q.gdn[2 * i] = gn0 * ih; Q.gdn[2 * i + 1] = gn1 * ih;
-        Q.gu[2 * i] = gu0 * ih; Q.gu[2 * i + 1] = gu1 * ih;
-        Q.gun[2 * i] = gun0 * ih; Q.gun[2 * i + 1] = gun1 * ih;
-        Q.hu[3 * i] = hu0 * ih2; Q.hu[3 * i + 1] = hu1 * ih2; Q.hu[3 * i + 2] = hu2 * ih2;
-        Q.fn[i] = A.fnew * f;
-        Q.fo[i] = A.fold * f;
-    }
-    double pq = 0, gp0 = 0, gp1 = 0;
-    for (int b = 0; b < 4; ++b) {
-        pq += p[b] * c_psi[q * 4 + b];
-        gp0 += p[b] * c_dpsi[(q * 2) * 4 + b];
-        gp1 += p[b] * c_dpsi[(q * 2 + 1) * 4 + b];
-    }
-    Q.pq = pq;
-    Q.gp[0] = gp0 * ih;
-    Q.gp[1] = gp1 * ih;
-}
-
 // F = I + grad d, J = det F, Fi = F^{-1} (row-major 2 x 2)
 template <class T>
 DEV void kinematics(const T g[4], T &J, T Fi[4]) {
@@ -231,13 +198,106 @@ DEV void piola_el(const T g[4], const T &J, const T Fi[4], double C1, double C2,
     P[3] = J * (s01 * Fi[2] + s11 * Fi[3]);
 }
 
-// seeded grad_X d at point q (KIND 0 seeds node sa, component si)
+// Everything at quadrature point q of one element that does not depend on
+// a seed: interpolated values, gradients and Hessians, the kinematics of the
+// new and the old state and the old state's stress terms.
+DEV void prepare_point(const NlArgs &A, const double *d, const double *dn, const double *u, const double *un,
+                       const double *p, const double *w, bool solid, int q, QV &Q) {
+    const double ih = A.ih, ih2 = A.ih * A.ih;
+    double gdn[4], gun[4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0, g0 = 0, g1 = 0, gn0 = 0, gn1 = 0;
+        double hu0 = 0, hu1 = 0, hu2 = 0, gu0 = 0, gu1 = 0, gun0 = 0, gun1 = 0, f = 0;
+        for (int a = 0; a < 9; ++a) {
+            const double ph = c_phi[q * 9 + a], dx = c_dphi[(q * 2) * 9 + a], dy = c_dphi[(q * 2 + 1) * 9 + a];
+            const double da = d[2 * a + i], dna = dn[2 * a + i], ua = u[2 * a + i], una = un[2 * a + i];
+            s0 += da * ph; s1 += dna * ph; s2 += ua * ph; s3 += una * ph;
+            g0 += da * dx; g1 += da * dy; gn0 += dna * dx; gn1 += dna * dy;
+            gu0 += ua * dx; gu1 += ua * dy; gun0 += una * dx; gun1 += una * dy;
+            hu0 += ua * c_ddphi[(q * 3) * 9 + a];
+            hu1 += ua * c_ddphi[(q * 3 + 1) * 9 + a];
+            hu2 += ua * c_ddphi[(q * 3 + 2) * 9 + a];
+            f += w[2 * a + i] * ph;
+        }
+        Q.dq[i] = s0; Q.dnq[i] = s1; Q.uq[i] = s2; Q.unq[i] = s3;
+        Q.gd[2 * i] = g0 * ih; Q.gd[2 * i + 1] = g1 * ih;
+        gdn[2 * i] = gn0 * ih; gdn[2 * i + 1] = gn1 * ih;
+        Q.gu[2 * i] = gu0 * ih; Q.gu[2 * i + 1] = gu1 * ih;
+        gun[2 * i] = gun0 * ih; gun[2 * i + 1] = gun1 * ih;
+        Q.hu[3 * i] = hu0 * ih2; Q.hu[3 * i + 1] = hu1 * ih2; Q.hu[3 * i + 2] = hu2 * ih2;
+        Q.fn[i] = A.fnew * f;
+        Q.fo[i] = A.fold * f;
+    }
+    double pq = 0, gp0 = 0, gp1 = 0;
+    for (int b = 0; b < 4; ++b) {
+        pq += p[b] * c_psi[q * 4 + b];
+        gp0 += p[b] * c_dpsi[(q * 2) * 4 + b];
+        gp1 += p[b] * c_dpsi[(q * 2 + 1) * 4 + b];
+    }
+    Q.pq = pq;
+    Q.gp[0] = gp0 * ih;
+    Q.gp[1] = gp1 * ih;
+    kinematics(Q.gd, Q.J, Q.Fi);
+    double Fin[4];
+    kinematics(gdn, Q.Jn, Fin);
+    if (solid) {
+        double Pn[4];
+        piola_el(gdn, Q.Jn, Fin, A.C1, A.C2, Pn);
+        for (int k = 0; k < 4; ++k) Q.bo[k] = 0.5 * Pn[k];
+        for (int k = 0; k < 4; ++k) Q.y[k] = 0.0;
+    } else {
+        // grad_x u_n = grad_X u_n F_n^{-1}; sigma_n = mu (y + y^T); 1/2 J_n sigma_n F_n^{-T}
+        const double y00 = gun[0] * Fin[0] + gun[1] * Fin[2], y01 = gun[0] * Fin[1] + gun[1] * Fin[3];
+        const double y10 = gun[2] * Fin[0] + gun[3] * Fin[2], y11 = gun[2] * Fin[1] + gun[3] * Fin[3];
+        Q.y[0] = y00; Q.y[1] = y01; Q.y[2] = y10; Q.y[3] = y11;
+        const double mu = A.mu_f;
+        const double t00 = 2.0 * mu * y00, t01 = mu * (y01 + y10), t11 = 2.0 * mu * y11;
+        const double hj = 0.5 * Q.Jn;
+        Q.bo[0] = hj * (t00 * Fin[0] + t01 * Fin[1]);
+        Q.bo[1] = hj * (t00 * Fin[2] + t01 * Fin[3]);
+        Q.bo[2] = hj * (t01 * Fin[0] + t11 * Fin[1]);
+        Q.bo[3] = hj * (t01 * Fin[2] + t11 * Fin[3]);
+    }
+}
+
+// grad_X d, J and F^{-1} at point q with the seed of a d unknown (node sa,
+// component si): dF = e_si (x) grad_X phi_sa, dJ = J tr(F^{-1} dF),
+// dF^{-1} = -F^{-1} dF F^{-1}; plain values for the other kinds
 template <int KIND>
-DEV void seeded_gd(const QV &Q, int q, int sa, int si, double ih, typename Ty<KIND>::D g[4]) {
-    using TD = typename Ty<KIND>::D;
-    for (int i = 0; i < 2; ++i)
-        for (int J = 0; J < 2; ++J)
-            g[2 * i + J] = seeded<TD>(Q.gd[2 * i + J], si == i ? c_dphi[(q * 2 + J) * 9 + sa] * ih : 0.0);
+DEV void seeded_kin(const QV &Q, int q, int sa, int si, double ih, typename Ty<KIND>::D g[4],
+                    typename Ty<KIND>::D &J, typename Ty<KIND>::D Fi[4]) {
+    if constexpr (KIND == 0) {
+        const double g0 = c_dphi[(q * 2) * 9 + sa] * ih, g1 = c_dphi[(q * 2 + 1) * 9 + sa] * ih;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            g[2 * r] = Dl(Q.gd[2 * r], r == si ? g0 : 0.0);
+            g[2 * r + 1] = Dl(Q.gd[2 * r + 1], r == si ? g1 : 0.0);
+        }
+        const double c0 = si ? Q.Fi[1] : Q.Fi[0], c1 = si ? Q.Fi[3] : Q.Fi[2];   // column si of F^{-1}
+        J = Dl(Q.J, Q.J * (c0 * g0 + c1 * g1));
+        const double v0 = g0 * Q.Fi[0] + g1 * Q.Fi[2], v1 = g0 * Q.Fi[1] + g1 * Q.Fi[3];
+        Fi[0] = Dl(Q.Fi[0], -c0 * v0);
+        Fi[1] = Dl(Q.Fi[1], -c0 * v1);
+        Fi[2] = Dl(Q.Fi[2], -c1 * v0);
+        Fi[3] = Dl(Q.Fi[3], -c1 * v1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            g[k] = Q.gd[k];
+            Fi[k] = Q.Fi[k];
+        }
+        J = Q.J;
+    }
+}
+
+DEV double dabs(double a) { return fabs(a); }
+DEV Dl dabs(Dl a) { return a.v < 0.0 ? -a : a; }
+
+// symmetric 2 x 2 products (powers of one symmetric matrix commute)
+template <class T> DEV void sym_mul(const T a[3], const T b[3], T c[3]) {
+    const T c00 = a[0] * b[0] + a[1] * b[1], c01 = a[0] * b[1] + a[1] * b[2], c11 = a[1] * b[1] + a[2] * b[2];
+    c[0] = c00; c[1] = c01; c[2] = c11;
 }
 
 // lambda_k of the element (bubble eigenproblem, power method)
@@ -249,8 +309,7 @@ DEV typename Ty<KIND>::D element_lambda(const NlArgs &A, GetQ getQ, int sa, int 
     for (int q = 0; q < 9; ++q) {
         const QV &Q = getQ(q);
         TD g[4], J, Fi[4];
-        seeded_gd<KIND>(Q, q, sa, si, ih, g);
-        kinematics(g, J, Fi);
+        seeded_kin<KIND>(Q, q, sa, si, ih, g, J, Fi);
         // grad_x of the bubble (centre node 4) and its spatial Hessian Fi^T H Fi
         const double bx = c_dphi[(q * 2) * 9 + 4] * ih, by = c_dphi[(q * 2 + 1) * 9 + 4] * ih;
         const double Hxx = c_ddphi[(q * 3) * 9 + 4] * ih2, Hyy = c_ddphi[(q * 3 + 1) * 9 + 4] * ih2,
@@ -268,13 +327,19 @@ DEV typename Ty<KIND>::D element_lambda(const NlArgs &A, GetQ getQ, int sa, int 
         K11 = K11 + wJ * (lap * lap + 2.0 * lap * H11 + H01 * H01 + H11 * H11);
         M = M + wJ * (gb0 * gb0 + gb1 * gb1);
     }
-    TD a0 = 1.0, a1 = 1.0;
-    for (int it = 0; it < 50; ++it) {
-        const TD b0 = (K00 * a0 + K01 * a1) / M, b1 = (K01 * a0 + K11 * a1) / M;
-        const TD nr = dsqrt(b0 * b0 + b1 * b1);
-        a0 = b0 / nr;
-        a1 = b1 / nr;
-    }
+    // 50 power steps from (1, 1): the direction of K^50 (1, 1), formed by
+    // squaring K / s (s >= |lambda|_max / 4 keeps every power in range; the
+    // direction does not depend on the scale), K^50 = K^32 K^16 K^2
+    const TD is = 1.0 / (dabs(K00) + dabs(K11) + 2.0 * dabs(K01));
+    TD P1[3] = {K00 * is, K01 * is, K11 * is}, P2[3], P4[3], P8[3], P16[3], P32[3], T[3], P50[3];
+    sym_mul(P1, P1, P2);
+    sym_mul(P2, P2, P4);
+    sym_mul(P4, P4, P8);
+    sym_mul(P8, P8, P16);
+    sym_mul(P16, P16, P32);
+    sym_mul(P32, P16, T);
+    sym_mul(T, P2, P50);
+    const TD a0 = P50[0] + P50[1], a1 = P50[1] + P50[2];
     return (a0 * (K00 * a0 + K01 * a1) + a1 * (K01 * a0 + K11 * a1)) / (M * (a0 * a0 + a1 * a1));
 }
 
@@ -305,29 +370,29 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
             *kin = hh * c_lump[sa];
         }
     }
-    TD lam = 0.0;
-    const double nu = A.mu_f / A.rho_f;
-    if (!solid) lam = element_lambda<KIND>(A, getQ, sa, si);
+    // tau's element factors (Eq. tausupg): 1/(4 lambda nu) and 1/sqrt(lambda)
+    TD t1 = 0.0, rsl = 0.0;
+    if (!solid) {
+        const TD lam = element_lambda<KIND>(A, getQ, sa, si);
+        t1 = 1.0 / (4.0 * (A.mu_f / A.rho_f) * lam);
+        rsl = 1.0 / dsqrt(lam);
+    }
     for (int q = 0; q < 9; ++q) {
         const QV &Q = getQ(q);
         const double dX = c_wq[q] * hh;
         TD g[4], J, Fi[4];
-        seeded_gd<KIND>(Q, q, sa, si, ih, g);
-        kinematics(g, J, Fi);
-        double Jn, Fin[4];
-        kinematics(Q.gdn, Jn, Fin);
+        seeded_kin<KIND>(Q, q, sa, si, ih, g, J, Fi);
+        const double Jn = Q.Jn;
         const TP p = seeded<TP>(Q.pq, KIND == 2 ? c_psi[q * 4 + (t & 3)] : 0.0);
         TU uq[2];
         for (int i = 0; i < 2; ++i) uq[i] = seeded<TU>(Q.uq[i], si == i ? c_phi[q * 9 + sa] : 0.0);
         TW Ai[2], B[4], C;
         if (solid) {
             TD P[4];
-            double Pn[4];
             piola_el(g, J, Fi, A.C1, A.C2, P);
-            piola_el(Q.gdn, Jn, Fin, A.C1, A.C2, Pn);
             for (int i = 0; i < 2; ++i) {
                 Ai[i] = A.rho_s * (uq[i] - Q.unq[i]) * idt;
-                for (int K = 0; K < 2; ++K) B[2 * i + K] = 0.5 * (P[2 * i + K] + Pn[2 * i + K]) - p * J * Fi[2 * K + i];
+                for (int K = 0; K < 2; ++K) B[2 * i + K] = 0.5 * P[2 * i + K] + Q.bo[2 * i + K] - p * J * Fi[2 * K + i];
             }
             C = -(J - 1.0);
         } else {
@@ -351,11 +416,8 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
             const double mu = A.mu_f, rho = A.rho_f;
             const auto s00 = 2.0 * mu * x00, s01 = mu * (x01 + x10), s11 = 2.0 * mu * x11;
             // old state (its mesh velocity is the new one)
-            const double y00 = Q.gun[0] * Fin[0] + Q.gun[1] * Fin[2], y01 = Q.gun[0] * Fin[1] + Q.gun[1] * Fin[3];
-            const double y10 = Q.gun[2] * Fin[0] + Q.gun[3] * Fin[2], y11 = Q.gun[2] * Fin[1] + Q.gun[3] * Fin[3];
             const auto n0 = Q.unq[0] - wm[0], n1 = Q.unq[1] - wm[1];
-            const auto cn0 = n0 * y00 + n1 * y01, cn1 = n0 * y10 + n1 * y11;
-            const double t00 = 2.0 * mu * y00, t01 = mu * (y01 + y10), t11 = 2.0 * mu * y11;
+            const auto cn0 = n0 * Q.y[0] + n1 * Q.y[1], cn1 = n0 * Q.y[2] + n1 * Q.y[3];
             // SUPG: strong residual at the new state
             const TU Hx0[3] = {hu[0], hu[1], hu[2]}, Hx1[3] = {hu[3], hu[4], hu[5]};
             // spatial Hessian of u_i: Fi^T H Fi ([jk]: 00, 11, 01)
@@ -376,11 +438,11 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
             const auto gp0 = gpr0 * Fi[0] + gpr1 * Fi[2], gp1 = gpr0 * Fi[1] + gpr1 * Fi[3];
             const auto r0 = rho * (uq[0] - Q.unq[0]) * idt + rho * cv0 + gp0 - mu * visc0 - rho * Q.fn[0];
             const auto r1 = rho * (uq[1] - Q.unq[1]) * idt + rho * cv1 + gp1 - mu * visc1 - rho * Q.fn[1];
-            // tau (Eq. tausupg)
-            TW tau = 1.0 / (4.0 * lam * nu);
+            // tau (Eq. tausupg): min(1/(4 lambda nu), 1/(sqrt(lambda) |u|))
+            TW tau = t1;
             const auto sp2 = uq[0] * uq[0] + uq[1] * uq[1];
             if (vpart(sp2) > 0.0) {
-                const TW t2 = 1.0 / (dsqrt(lam) * dsqrt(sp2));
+                const TW t2 = rsl * (1.0 / dsqrt(sp2));
                 if (vpart(t2) < vpart(tau)) tau = t2;
             }
             // convecting direction pulled back: c_J = rho sum_j c_j Fi_Jj
@@ -389,10 +451,11 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
             Ai[0] = rho * J * (uq[0] - Q.unq[0]) * idt + 0.5 * (J * rho * (cv0 - Q.fn[0]) + Jn * rho * (cn0 - Q.fo[0]));
             Ai[1] = rho * J * (uq[1] - Q.unq[1]) * idt + 0.5 * (J * rho * (cv1 - Q.fn[1]) + Jn * rho * (cn1 - Q.fo[1]));
             // B_iJ = 1/2 (J sigma Fi^T + J_n sigma_n Fi_n^T)_iJ - J p Fi_Ji + J tau r_i c_J
-            B[0] = 0.5 * (J * (s00 * Fi[0] + s01 * Fi[1]) + Jn * (t00 * Fin[0] + t01 * Fin[1])) - J * p * Fi[0] + Jt * r0 * k0;
-            B[1] = 0.5 * (J * (s00 * Fi[2] + s01 * Fi[3]) + Jn * (t00 * Fin[2] + t01 * Fin[3])) - J * p * Fi[2] + Jt * r0 * k1;
-            B[2] = 0.5 * (J * (s01 * Fi[0] + s11 * Fi[1]) + Jn * (t01 * Fin[0] + t11 * Fin[1])) - J * p * Fi[1] + Jt * r1 * k0;
-            B[3] = 0.5 * (J * (s01 * Fi[2] + s11 * Fi[3]) + Jn * (t01 * Fin[2] + t11 * Fin[3])) - J * p * Fi[3] + Jt * r1 * k1;
+            const auto hJ = 0.5 * J;
+            B[0] = hJ * (s00 * Fi[0] + s01 * Fi[1]) + Q.bo[0] - J * p * Fi[0] + Jt * r0 * k0;
+            B[1] = hJ * (s00 * Fi[2] + s01 * Fi[3]) + Q.bo[1] - J * p * Fi[2] + Jt * r0 * k1;
+            B[2] = hJ * (s01 * Fi[0] + s11 * Fi[1]) + Q.bo[2] - J * p * Fi[1] + Jt * r1 * k0;
+            B[3] = hJ * (s01 * Fi[2] + s11 * Fi[3]) + Q.bo[3] - J * p * Fi[3] + Jt * r1 * k1;
             C = -J * (x00 + x11);
             // harmonic extension rows: k (grad d + grad d^T)
             if constexpr (live<JAC, TD>) {
@@ -453,7 +516,7 @@ __global__ void __launch_bounds__(128) nl_residual_kernel(NlArgs A) {
     const bool solid = A.material[e] != 0;
     QV Qs;
     auto getQ = [&](int q) -> const QV & {
-        interpolate(A, E.d, E.dn, E.u, E.un, E.p, E.w, q, Qs);
+        prepare_point(A, E.d, E.dn, E.u, E.un, E.p, E.w, solid, q, Qs);
         return Qs;
     };
     double out[40], kin;
@@ -501,7 +564,8 @@ __global__ void __launch_bounds__(EPB *NT) nl_jacobian_kernel(NlArgs A) {
         const int el = k / 9, q = k % 9;
         if (base + el >= A.n_elems) continue;
         const double *v = s_ev[el];
-        interpolate(A, v, v + 18, v + 36, v + 54, v + 72, v + 76, q, s_q[el][q]);
+        const bool solid_e = A.material[A.elems[base + el]] != 0;
+        prepare_point(A, v, v + 18, v + 36, v + 54, v + 72, v + 76, solid_e, q, s_q[el][q]);
     }
     __syncthreads();
     const int el = tid / NT, t = tid % NT;
