@@ -2422,6 +2422,9 @@ fsi_status nl_setup_problem(Context &cx, Problem &pb, const fsi_nl_params &in) {
             N.colour_ptr[c + 1] = (int64_t)el.size();
         }
         FSI_TRY(upload(N.elems, el.data(), el.size() * 4, s));
+        size_t pbytes = 0;
+        FSI_TRY(nl_point_bytes(N, &pbytes));
+        FSI_TRY(N.pts.alloc(pbytes));
         if (l + 1 < L) {
             const std::vector<int32_t> map = nl_injection(pb.host[l + 1], H);
             FSI_TRY(upload(N.inj, map.data(), map.size() * 4, s));
@@ -2432,6 +2435,7 @@ fsi_status nl_setup_problem(Context &cx, Problem &pb, const fsi_nl_params &in) {
     const int64_t n = pb.dev.back().n;
     FSI_TRY(pb.nl_R.alloc((size_t)n * 8));
     FSI_TRY(pb.nl_dU.alloc((size_t)n * 8));
+    for (auto &f : pb.nl_fj) FSI_CUDA(f.create());
     FSI_CUDA(cudaStreamSynchronize(s));
     pb.nl_ready = true;
     return FSI_OK;
@@ -2458,7 +2462,7 @@ fsi_status nl_assemble(Context &cx, Problem &pb, const double *U, const double *
     for (int l = 0; l < L; ++l) {
         LevelDev &D = pb.dev[l];
         FSI_TRY(launch_nl_jacobian(pb.nlev[l], pb.nl, D.fixed.as<uint8_t>(), D.A, Us[l], Uns[l], t_new,
-                                   cx.flags.as<int>() + 3, s));
+                                   cx.flags.as<int>() + 3, s, pb.nl_fj));
         if (D.A.val32.p)                       // float32 copy in place (its address is in captured graphs)
             FSI_TRY(launch_cast_f64_f32(D.A.val64.as<double>(), D.A.val32.as<float>(), D.A.nnz, s));
         FSI_TRY(ell_refill(D.A, s));

@@ -222,6 +222,7 @@ struct NlLevelDev {
     int64_t colour_ptr[5] = {0, 0, 0, 0, 0};
     DevBuf inj;                     // int32 n (l < L-1): dof of level l+1 at the coinciding node, -1 none
     DevBuf U, Un;                   // float64 states (l < L-1: injected)
+    DevBuf pts;                     // point scratch of the Jacobian: n_el x 9 records
 };
 
 struct Problem {
@@ -262,6 +263,7 @@ struct Problem {
     NlParams nl;
     std::vector<NlLevelDev> nlev;    // index = level
     DevBuf nl_R, nl_dU;              // fine residual (negated for the solve) and Newton update
+    ForkJoin nl_fj[2];               // side streams of the Jacobian's seed kinds
 };
 
 // kernels launched by the library (all contexts), for launch accounting
@@ -459,7 +461,10 @@ fsi_status nl_upload_tables(cudaStream_t s);
 fsi_status launch_nl_residual(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, int64_t n_dofs,
                               const double *U, const double *Un, double t_new, double *R, cudaStream_t s);
 fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, const DevCSR &A,
-                              const double *U, const double *Un, double t_new, int *err, cudaStream_t s);
+                              const double *U, const double *Un, double t_new, int *err, cudaStream_t s,
+                              ForkJoin *fj);
+// bytes of a level's point scratch
+fsi_status nl_point_bytes(const NlLevelDev &L, size_t *bytes);
 fsi_status launch_nl_inject(const int32_t *map, const uint8_t *fixed_c, const double *Uf, double *Uc, int64_t nc,
                             cudaStream_t s);
 // y = a x + b y (float64)

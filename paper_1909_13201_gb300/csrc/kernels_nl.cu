@@ -529,21 +529,20 @@ __global__ void __launch_bounds__(128) nl_residual_kernel(NlArgs A) {
     }
 }
 
-// Jacobian: EPB elements per CTA, NT threads per element (18 for d and u
-// seeds, 4 for p seeds); phase 1 gathers the elements and interpolates
-// every quadrature point into shared memory, phase 2 evaluates one column
-// of an element Jacobian per thread and adds it into the CSR values.
-template <int KIND, int EPB, int NT>
-__global__ void __launch_bounds__(EPB *NT) nl_jacobian_kernel(NlArgs A) {
-    __shared__ double s_ev[EPB][94];
-    __shared__ QV s_q[EPB][9];
+// Point data of every element of a level (the seed-independent part of the
+// Jacobian): a CTA gathers the local values of 8 elements into shared
+// memory, then one thread per (element, point) writes its QV record to
+// pts[(e * 9 + q)].  Run once per assembly and level, read by all three
+// seed kinds.
+constexpr int PT_EPB = 8;
+__global__ void __launch_bounds__(PT_EPB * 9) nl_point_kernel(NlArgs A, int64_t n_el, QV *pts) {
+    __shared__ double s_ev[PT_EPB][94];
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * EPB;
-    // phase 1a: local values (d, dn, u, un, p, w) of the CTA's elements
-    for (int k = tid; k < EPB * 94; k += EPB * NT) {
+    const int64_t base = (int64_t)blockIdx.x * PT_EPB;
+    for (int k = tid; k < PT_EPB * 94; k += PT_EPB * 9) {
         const int el = k / 94, j = k % 94;
-        if (base + el >= A.n_elems) continue;
-        const int64_t e = A.elems[base + el];
+        const int64_t e = base + el;
+        if (e >= n_el) continue;
         const int32_t *ed = A.elem_dofs + e * 40;
         double v;
         if (j < 18) v = A.U[ed[j]];
@@ -559,13 +558,31 @@ __global__ void __launch_bounds__(EPB *NT) nl_jacobian_kernel(NlArgs A) {
         s_ev[el][j] = v;
     }
     __syncthreads();
-    // phase 1b: interpolation at the 9 points of every element
-    for (int k = tid; k < EPB * 9; k += EPB * NT) {
-        const int el = k / 9, q = k % 9;
+    const int el = tid / 9, q = tid % 9;
+    const int64_t e = base + el;
+    if (e >= n_el) return;
+    const double *v = s_ev[el];
+    QV Q;
+    prepare_point(A, v, v + 18, v + 36, v + 54, v + 72, v + 76, A.material[e] != 0, q, Q);
+    pts[e * 9 + q] = Q;
+}
+
+// Jacobian: EPB elements per CTA, NT threads per element (18 for d and u
+// seeds, 4 for p seeds); the elements' point records are copied from the
+// point scratch into shared memory, then every thread evaluates one column
+// of an element Jacobian and adds it into the CSR values.
+template <int KIND, int EPB, int NT, int MINB>
+__global__ void __launch_bounds__(EPB *NT, MINB) nl_jacobian_kernel(NlArgs A, const QV *__restrict__ pts) {
+    __shared__ QV s_q[EPB][9];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * EPB;
+    constexpr int QD = sizeof(QV) / sizeof(double);
+    double *sq = reinterpret_cast<double *>(&s_q[0][0]);
+    for (int k = tid; k < EPB * 9 * QD; k += EPB * NT) {
+        const int el = k / (9 * QD), r = k % (9 * QD);
         if (base + el >= A.n_elems) continue;
-        const double *v = s_ev[el];
-        const bool solid_e = A.material[A.elems[base + el]] != 0;
-        prepare_point(A, v, v + 18, v + 36, v + 54, v + 72, v + 76, solid_e, q, s_q[el][q]);
+        const int64_t e = A.elems[base + el];
+        sq[k] = reinterpret_cast<const double *>(pts + e * 9)[r];
     }
     __syncthreads();
     const int el = tid / NT, t = tid % NT;
@@ -719,8 +736,14 @@ fsi_status launch_nl_residual(const NlLevelDev &L, const NlParams &P, const uint
     return FSI_OK;
 }
 
+fsi_status nl_point_bytes(const NlLevelDev &L, size_t *bytes) {
+    *bytes = (size_t)L.n * L.n * 9 * sizeof(QV);
+    return FSI_OK;
+}
+
 fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, const DevCSR &Aop,
-                              const double *U, const double *Un, double t_new, int *err, cudaStream_t s) {
+                              const double *U, const double *Un, double t_new, int *err, cudaStream_t s,
+                              ForkJoin *fj) {
     FSI_CUDA(cudaMemsetAsync(Aop.val64.p, 0, (size_t)Aop.nnz * 8, s));
     NlArgs A = make_args(L, P, U, Un, t_new);
     A.fixed = fixed;
@@ -728,6 +751,14 @@ fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint
     A.col = Aop.col.as<int32_t>();
     A.val = Aop.val64.as<double>();
     A.err = err;
+    const int64_t n_el = (int64_t)L.n * L.n;
+    QV *pts = L.pts.as<QV>();
+    if (!pts || L.pts.bytes < (size_t)n_el * 9 * sizeof(QV)) { set_error("nonlinear point scratch missing"); return FSI_ERR_STATE; }
+    nl_point_kernel<<<(unsigned)((n_el + PT_EPB - 1) / PT_EPB), PT_EPB * 9, 0, s>>>(A, n_el, pts);
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
+    // the three seed kinds write disjoint columns: side by side on two
+    // auxiliary streams; colours (which share rows) one after another
     constexpr int EPB = 8;
     for (int c = 0; c < 4; ++c) {
         const int64_t ne = L.colour_ptr[c + 1] - L.colour_ptr[c];
@@ -735,11 +766,19 @@ fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint
         A.elems = L.elems.as<int32_t>() + L.colour_ptr[c];
         A.n_elems = ne;
         const unsigned g = (unsigned)((ne + EPB - 1) / EPB);
-        nl_jacobian_kernel<0, EPB, 18><<<g, EPB * 18, 0, s>>>(A);
-        nl_jacobian_kernel<1, EPB, 18><<<g, EPB * 18, 0, s>>>(A);
-        nl_jacobian_kernel<2, EPB, 4><<<g, EPB * 4, 0, s>>>(A);
+        for (int k = 0; k < 2; ++k) {
+            FSI_CUDA(cudaEventRecord(fj[k].fork, s));
+            FSI_CUDA(cudaStreamWaitEvent(fj[k].aux, fj[k].fork, 0));
+        }
+        nl_jacobian_kernel<0, EPB, 18, 2><<<g, EPB * 18, 0, s>>>(A, pts);
+        nl_jacobian_kernel<1, EPB, 18, 1><<<g, EPB * 18, 0, fj[0].aux>>>(A, pts);
+        nl_jacobian_kernel<2, EPB, 4, 1><<<g, EPB * 4, 0, fj[1].aux>>>(A, pts);
         count_launch(3);
         FSI_CUDA(cudaGetLastError());
+        for (int k = 0; k < 2; ++k) {
+            FSI_CUDA(cudaEventRecord(fj[k].join, fj[k].aux));
+            FSI_CUDA(cudaStreamWaitEvent(s, fj[k].join, 0));
+        }
     }
     FSI_TRY(launch_set_fixed_diag(Aop, fixed, Aop.val64.as<double>(), s));
     return FSI_OK;
