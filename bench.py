@@ -23,6 +23,9 @@ smoothing, Arnoldi, refinement): every step of the solve path.  Set-up
   roofline   the fine-level sweep (its apply and pass-residual launches on
              two streams): algorithmic bytes / its mean time from CUDA
              events, against the measured HBM copy bandwidth;
+  nonlinear  implicit time steps of the nonlinear problem (Sec. 2.2) on the
+             same channel from rest: exact Newton, every Newton system solved
+             by the headline configuration; the paper's s^max, N and rho;
   cpu_baseline  the FP64 oracle on this host, bounded sample (see "sample").
 
 --impl reference runs the oracle itself as the reference arm.  With
@@ -53,6 +56,9 @@ if ROOT not in sys.path:
 METRIC = "fine DOF/s to 1e-8 rel residual (mixed vs FP64 GPU); smoother % HBM peak"
 UNIT = "DOF/s"
 RTOL = 1e-8
+NL_FORCE = 20.0       # body-force amplitude of the nonlinear leg
+NL_STEPS = 4          # implicit time steps of the nonlinear leg
+NL_RTOL = 1e-8        # Newton tolerance on ||R|| relative to the step's initial residual
 # the timed smoother: the locally multiplicative sweep on this many finest
 # levels (additive below); 0 = additive everywhere
 HEAD_MULT = 1
@@ -577,6 +583,62 @@ def run_ours(args, rank, world, local):
     conv_as3 = bool(st3.get("converged"))
     del s3, b3, x3
     torch.cuda.empty_cache()
+    # ---- the nonlinear time loop (Sec. 2.2): implicit steps of the same 256^2
+    # channel from rest under the pulsatile body force, exact Newton with the
+    # headline solver on every Newton system (Jacobians on all levels, blocks
+    # refactored per Newton step); the paper's s^max, N and rho (Sec. 4)
+    t0 = time.time()
+    snl = FSISolver(p, stream=stream, nonlinear=True)
+    snl.nl_setup(force=NL_FORCE)
+    snl.setup_smoothers(precision=FSI_MIXED_HALF, mult_levels=1)
+    torch.cuda.synchronize()
+    setup_nl_s = time.time() - t0
+    Un_nl = torch.zeros(n, dtype=torch.float64, device=dev)
+    U_nl = torch.empty_like(Un_nl)
+    nl_steps = []
+    for k in range(NL_STEPS):
+        U_nl.copy_(Un_nl)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = snl.nl_step(Un_nl, U_nl, (k + 1) * p.dt, nl_rtol=NL_RTOL, lin_rtol=RTOL, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g["ms"] = e0.elapsed_time(e1)
+        nl_steps.append(g)
+        Un_nl.copy_(U_nl)
+    jac_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        snl.nl_jacobian(U_nl, Un_nl, NL_STEPS * p.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        jac_ms.append(e0.elapsed_time(e1))
+    del snl, Un_nl, U_nl
+    torch.cuda.empty_cache()
+    nl_newton = [st["newton_steps"] for st in nl_steps]
+    nl_its = [i for st in nl_steps for i in st["iterations"]]
+    nl_rho = [r for st in nl_steps for r in st["rho"]]
+    nl_ms = [st["ms"] for st in nl_steps]
+    nonlinear = {
+        "what": "implicit time steps of the nonlinear FSI problem (Mooney-Rivlin solid, ALE Navier-Stokes with "
+                "SUPG, Crank-Nicolson) from rest, exact Newton, each Newton system solved by the headline "
+                "solver; Jacobians on every level by dual-number kernels",
+        "workload": p.name + "-nonlinear", "force": NL_FORCE, "time_steps": NL_STEPS, "nl_rtol": NL_RTOL,
+        "s_max": sum(nl_newton) / len(nl_newton), "N": sum(nl_its) / max(len(nl_its), 1),
+        "rho": sum(nl_rho) / max(len(nl_rho), 1), "all_converged": all(st["converged"] for st in nl_steps),
+        "ms_per_time_step": sum(nl_ms) / len(nl_ms),
+        "ms_per_newton_step": {"jacobian": sum(st["jacobian_ms"] for st in nl_steps) / max(sum(nl_newton), 1),
+                               "block_setup": sum(st["setup_ms"] for st in nl_steps) / max(sum(nl_newton), 1),
+                               "solve": sum(st["solve_ms"] for st in nl_steps) / max(sum(nl_newton), 1)},
+        "jacobian_all_levels_ms": min(jac_ms),
+        "jacobian_elements_per_s": sum((p.n_fine >> l) ** 2 for l in range(p.n_levels)) / (min(jac_ms) * 1e-3),
+        "newton_fine_dof_per_s": job_throughput(n * sum(nl_newton), sum(nl_ms), world),
+        "setup_s": setup_nl_s,
+        "steps": [{"newton": st["newton_steps"], "its": st["iterations"], "ms": round(st["ms"], 2)}
+                  for st in nl_steps],
+    }
 
     value = job_throughput(n, ms, world)
     if rank != 0:
@@ -646,6 +708,7 @@ def run_ours(args, rank, world, local):
                            "ms_per_solve": ms_as3, "iterations": its_as3, "converged": conv_as3,
                            "setup_s": setup_as3_s, "fs_ms_per_solve": ms_3d,
                            "fs_speedup_over_as": ms_as3 / ms_3d},
+        "nonlinear": nonlinear,
         "adjoint": {"workload": pa.name, "unknowns": na, "ms_forward_plus_adjoint": ms_adj,
                     "iterations": astats, "dof_per_s": job_throughput(na, ms_adj, world)},
         "factorization": fact,
@@ -688,6 +751,9 @@ def run_ours(args, rank, world, local):
         "cascade": {"ms_per_step": round(ms_casc, 3), "its": its_casc["median"]},
         "as": {"ms_per_step": round(ms_as, 3), "its": its_as["median"]},
         "fs_vs_as_3d": {"fs_ms": round(ms_3d, 2), "as_ms": round(ms_as3, 2), "as_its": its_as3["median"]},
+        "nonlinear": {"ms_per_time_step": round(nonlinear["ms_per_time_step"], 1),
+                      "s_max": nonlinear["s_max"], "N": round(nonlinear["N"], 2), "rho": round(nonlinear["rho"], 3),
+                      "jacobian_ms": round(nonlinear["jacobian_all_levels_ms"], 2)},
         "e2e": {"value": job_throughput(n, ms_e2e, world), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
         "roofline": {"bound": "hbm", "kernel": "fine-level sweep (12 apply + 11 residual passes, 2 streams)",
