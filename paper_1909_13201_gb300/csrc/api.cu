@@ -2425,6 +2425,7 @@ fsi_status nl_setup_problem(Context &cx, Problem &pb, const fsi_nl_params &in) {
         size_t pbytes = 0;
         FSI_TRY(nl_point_bytes(N, &pbytes));
         FSI_TRY(N.pts.alloc(pbytes));
+        FSI_TRY(launch_nl_positions(N, pb.dev[l].A, pb.dev[l].fixed.as<uint8_t>(), s));
         if (l + 1 < L) {
             const std::vector<int32_t> map = nl_injection(pb.host[l + 1], H);
             FSI_TRY(upload(N.inj, map.data(), map.size() * 4, s));

@@ -223,6 +223,7 @@ struct NlLevelDev {
     DevBuf inj;                     // int32 n (l < L-1): dof of level l+1 at the coinciding node, -1 none
     DevBuf U, Un;                   // float64 states (l < L-1: injected)
     DevBuf pts;                     // point scratch of the Jacobian: n_el x 9 records
+    DevBuf pos;                     // int32 n_el x 40 x 40: CSR position of each element-matrix entry
 };
 
 struct Problem {
@@ -463,6 +464,8 @@ fsi_status launch_nl_residual(const NlLevelDev &L, const NlParams &P, const uint
 fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint8_t *fixed, const DevCSR &A,
                               const double *U, const double *Un, double t_new, int *err, cudaStream_t s,
                               ForkJoin *fj);
+// the element-matrix -> CSR position table of a level (built once; the pattern is fixed)
+fsi_status launch_nl_positions(NlLevelDev &L, const DevCSR &A, const uint8_t *fixed, cudaStream_t s);
 // bytes of a level's point scratch
 fsi_status nl_point_bytes(const NlLevelDev &L, size_t *bytes);
 fsi_status launch_nl_inject(const int32_t *map, const uint8_t *fixed_c, const double *Uf, double *Uc, int64_t nc,

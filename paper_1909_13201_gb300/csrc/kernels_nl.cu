@@ -131,6 +131,14 @@ struct EV {
     double d[18], dn[18], u[18], un[18], p[4], w[18];
 };
 
+// shape tables addressed by a thread's own seed (node or vertex index
+// differs across the warp): a shared-memory copy in the Jacobian kernels,
+// the constant tables in the residual kernel (which has no seed)
+struct Tab {
+    const double *phi, *dphi, *ddphi, *psi, *dpsi;
+};
+constexpr int TAB_DOUBLES = 81 + 162 + 243 + 36 + 72;
+
 struct NlArgs {
     int n;                      // elements per direction of the level
     double h, ih, dt, idt, rho_s, rho_f, mu_f, C1, C2, k_ale, fnew, fold;
@@ -146,6 +154,7 @@ struct NlArgs {
     double *R;
     // Jacobian (CSR)
     const int32_t *row_ptr, *col;
+    const int32_t *pos;         // n_el x 40 (local column) x 40 (local row): CSR position, -1 none, -2 absent
     double *val;
     int *err;
 };
@@ -265,10 +274,10 @@ DEV void prepare_point(const NlArgs &A, const double *d, const double *dn, const
 // component si): dF = e_si (x) grad_X phi_sa, dJ = J tr(F^{-1} dF),
 // dF^{-1} = -F^{-1} dF F^{-1}; plain values for the other kinds
 template <int KIND>
-DEV void seeded_kin(const QV &Q, int q, int sa, int si, double ih, typename Ty<KIND>::D g[4],
+DEV void seeded_kin(const Tab &T, const QV &Q, int q, int sa, int si, double ih, typename Ty<KIND>::D g[4],
                     typename Ty<KIND>::D &J, typename Ty<KIND>::D Fi[4]) {
     if constexpr (KIND == 0) {
-        const double g0 = c_dphi[(q * 2) * 9 + sa] * ih, g1 = c_dphi[(q * 2 + 1) * 9 + sa] * ih;
+        const double g0 = T.dphi[(q * 2) * 9 + sa] * ih, g1 = T.dphi[(q * 2 + 1) * 9 + sa] * ih;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             g[2 * r] = Dl(Q.gd[2 * r], r == si ? g0 : 0.0);
@@ -302,14 +311,14 @@ template <class T> DEV void sym_mul(const T a[3], const T b[3], T c[3]) {
 
 // lambda_k of the element (bubble eigenproblem, power method)
 template <int KIND, class GetQ>
-DEV typename Ty<KIND>::D element_lambda(const NlArgs &A, GetQ getQ, int sa, int si) {
+DEV typename Ty<KIND>::D element_lambda(const NlArgs &A, const Tab &Tb, GetQ getQ, int sa, int si) {
     using TD = typename Ty<KIND>::D;
     const double ih = A.ih, ih2 = A.ih * A.ih, hh = A.h * A.h;
     TD K00 = 0.0, K01 = 0.0, K11 = 0.0, M = 0.0;
     for (int q = 0; q < 9; ++q) {
         const QV &Q = getQ(q);
         TD g[4], J, Fi[4];
-        seeded_kin<KIND>(Q, q, sa, si, ih, g, J, Fi);
+        seeded_kin<KIND>(Tb, Q, q, sa, si, ih, g, J, Fi);
         // grad_x of the bubble (centre node 4) and its spatial Hessian Fi^T H Fi
         const double bx = c_dphi[(q * 2) * 9 + 4] * ih, by = c_dphi[(q * 2 + 1) * 9 + 4] * ih;
         const double Hxx = c_ddphi[(q * 3) * 9 + 4] * ih2, Hyy = c_ddphi[(q * 3 + 1) * 9 + 4] * ih2,
@@ -350,7 +359,8 @@ DEV typename Ty<KIND>::D element_lambda(const NlArgs &A, GetQ getQ, int sa, int 
 // K rows (row 18 + t of a d or u seed) is returned in *kin instead, so that
 // out[] is only indexed by unrolled loop counters (it stays in registers).
 template <int KIND, bool JAC, class GetQ>
-DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E, double *out, double *kin) {
+DEV void element_rows(const NlArgs &A, const Tab &Tb, GetQ getQ, bool solid, int t, const EV *E, double *out,
+                      double *kin) {
     using TD = typename Ty<KIND>::D;
     using TU = typename Ty<KIND>::U;
     using TP = typename Ty<KIND>::P;
@@ -373,7 +383,7 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
     // tau's element factors (Eq. tausupg): 1/(4 lambda nu) and 1/sqrt(lambda)
     TD t1 = 0.0, rsl = 0.0;
     if (!solid) {
-        const TD lam = element_lambda<KIND>(A, getQ, sa, si);
+        const TD lam = element_lambda<KIND>(A, Tb, getQ, sa, si);
         t1 = 1.0 / (4.0 * (A.mu_f / A.rho_f) * lam);
         rsl = 1.0 / dsqrt(lam);
     }
@@ -381,11 +391,11 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
         const QV &Q = getQ(q);
         const double dX = c_wq[q] * hh;
         TD g[4], J, Fi[4];
-        seeded_kin<KIND>(Q, q, sa, si, ih, g, J, Fi);
+        seeded_kin<KIND>(Tb, Q, q, sa, si, ih, g, J, Fi);
         const double Jn = Q.Jn;
-        const TP p = seeded<TP>(Q.pq, KIND == 2 ? c_psi[q * 4 + (t & 3)] : 0.0);
+        const TP p = seeded<TP>(Q.pq, KIND == 2 ? Tb.psi[q * 4 + (t & 3)] : 0.0);
         TU uq[2];
-        for (int i = 0; i < 2; ++i) uq[i] = seeded<TU>(Q.uq[i], si == i ? c_phi[q * 9 + sa] : 0.0);
+        for (int i = 0; i < 2; ++i) uq[i] = seeded<TU>(Q.uq[i], si == i ? Tb.phi[q * 9 + sa] : 0.0);
         TW Ai[2], B[4], C;
         if (solid) {
             TD P[4];
@@ -398,15 +408,15 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
         } else {
             TD dq[2], wm[2];
             for (int i = 0; i < 2; ++i) {
-                dq[i] = seeded<TD>(Q.dq[i], si == i ? c_phi[q * 9 + sa] : 0.0);
+                dq[i] = seeded<TD>(Q.dq[i], si == i ? Tb.phi[q * 9 + sa] : 0.0);
                 wm[i] = (dq[i] - Q.dnq[i]) * idt;
             }
             TU gu[4], hu[6];
             for (int i = 0; i < 2; ++i) {
                 for (int Jd = 0; Jd < 2; ++Jd)
-                    gu[2 * i + Jd] = seeded<TU>(Q.gu[2 * i + Jd], si == i ? c_dphi[(q * 2 + Jd) * 9 + sa] * ih : 0.0);
+                    gu[2 * i + Jd] = seeded<TU>(Q.gu[2 * i + Jd], si == i ? Tb.dphi[(q * 2 + Jd) * 9 + sa] * ih : 0.0);
                 for (int k = 0; k < 3; ++k)
-                    hu[3 * i + k] = seeded<TU>(Q.hu[3 * i + k], si == i ? c_ddphi[(q * 3 + k) * 9 + sa] * ih2 : 0.0);
+                    hu[3 * i + k] = seeded<TU>(Q.hu[3 * i + k], si == i ? Tb.ddphi[(q * 3 + k) * 9 + sa] * ih2 : 0.0);
             }
             // new state: grad_x u = grad_X u F^{-1}
             const auto x00 = gu[0] * Fi[0] + gu[1] * Fi[2], x01 = gu[0] * Fi[1] + gu[1] * Fi[3];
@@ -433,8 +443,8 @@ DEV void element_rows(const NlArgs &A, GetQ getQ, bool solid, int t, const EV *E
             push(Hx1, b00, b11, b01);
             // div_x (grad_x u + grad_x u^T): i = 0: 2 u0,xx + u0,yy + u1,xy; i = 1: u1,xx + 2 u1,yy + u0,xy
             const auto visc0 = 2.0 * a00 + a11 + b01, visc1 = b00 + 2.0 * b11 + a01;
-            const TP gpr0 = seeded<TP>(Q.gp[0], KIND == 2 ? c_dpsi[(q * 2) * 4 + (t & 3)] * ih : 0.0);
-            const TP gpr1 = seeded<TP>(Q.gp[1], KIND == 2 ? c_dpsi[(q * 2 + 1) * 4 + (t & 3)] * ih : 0.0);
+            const TP gpr0 = seeded<TP>(Q.gp[0], KIND == 2 ? Tb.dpsi[(q * 2) * 4 + (t & 3)] * ih : 0.0);
+            const TP gpr1 = seeded<TP>(Q.gp[1], KIND == 2 ? Tb.dpsi[(q * 2 + 1) * 4 + (t & 3)] * ih : 0.0);
             const auto gp0 = gpr0 * Fi[0] + gpr1 * Fi[2], gp1 = gpr0 * Fi[1] + gpr1 * Fi[3];
             const auto r0 = rho * (uq[0] - Q.unq[0]) * idt + rho * cv0 + gp0 - mu * visc0 - rho * Q.fn[0];
             const auto r1 = rho * (uq[1] - Q.unq[1]) * idt + rho * cv1 + gp1 - mu * visc1 - rho * Q.fn[1];
@@ -520,7 +530,8 @@ __global__ void __launch_bounds__(128) nl_residual_kernel(NlArgs A) {
         return Qs;
     };
     double out[40], kin;
-    element_rows<-1, false>(A, getQ, solid, 0, &E, out, &kin);
+    const Tab Tb{c_phi, c_dphi, c_ddphi, c_psi, c_dpsi};
+    element_rows<-1, false>(A, Tb, getQ, solid, 0, &E, out, &kin);
     const int32_t *ed = A.elem_dofs + e * 40;
 #pragma unroll
     for (int r = 0; r < 40; ++r) {
@@ -574,9 +585,14 @@ __global__ void __launch_bounds__(PT_EPB * 9) nl_point_kernel(NlArgs A, int64_t 
 template <int KIND, int EPB, int NT, int MINB>
 __global__ void __launch_bounds__(EPB *NT, MINB) nl_jacobian_kernel(NlArgs A, const QV *__restrict__ pts) {
     __shared__ QV s_q[EPB][9];
+    __shared__ double s_tab[TAB_DOUBLES];
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * EPB;
     constexpr int QD = sizeof(QV) / sizeof(double);
+    for (int k = tid; k < TAB_DOUBLES; k += EPB * NT)
+        s_tab[k] = k < 81 ? c_phi[k]
+                          : (k < 243 ? c_dphi[k - 81]
+                                     : (k < 486 ? c_ddphi[k - 243] : (k < 522 ? c_psi[k - 486] : c_dpsi[k - 522])));
     double *sq = reinterpret_cast<double *>(&s_q[0][0]);
     for (int k = tid; k < EPB * 9 * QD; k += EPB * NT) {
         const int el = k / (9 * QD), r = k % (9 * QD);
@@ -590,23 +606,52 @@ __global__ void __launch_bounds__(EPB *NT, MINB) nl_jacobian_kernel(NlArgs A, co
     const int64_t e = A.elems[base + el];
     const bool solid = A.material[e] != 0;
     auto getQ = [&](int q) -> const QV & { return s_q[el][q]; };
+    const Tab Tb{s_tab, s_tab + 81, s_tab + 243, s_tab + 486, s_tab + 522};
     double out[40], kin;
-    element_rows<KIND, true>(A, getQ, solid, t, nullptr, out, &kin);
-    const int32_t *ed = A.elem_dofs + e * 40;
-    const int32_t Cg = ed[KIND == 0 ? t : (KIND == 1 ? 18 + t : 36 + t)];
-    if (A.fixed[Cg]) return;
+    element_rows<KIND, true>(A, Tb, getQ, solid, t, nullptr, out, &kin);
+    const int lc = KIND == 0 ? t : (KIND == 1 ? 18 + t : 36 + t);
+    const int4 *pp = reinterpret_cast<const int4 *>(A.pos + (e * 40 + lc) * 40);
 #pragma unroll
-    for (int r = 0; r < 40; ++r) {
-        const int32_t R = local_row(ed, solid, A.ds_end, r);
-        if (R < 0 || A.fixed[R]) continue;
-        const double v = out[r] + (r == 18 + t ? kin : 0.0);
-        if (v == 0.0) continue;          // structural zero (pairs the weak form does not couple)
-        const int pos = find_col(A.col, A.row_ptr[R], A.row_ptr[R + 1], Cg);
-        if (pos < 0) {
-            atomicOr(A.err, 1);
-            continue;
+    for (int r4 = 0; r4 < 10; ++r4) {
+        const int4 p4 = pp[r4];
+        const int pr[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = 4 * r4 + u;
+            const double v = out[r] + (r == 18 + t ? kin : 0.0);
+            if (v == 0.0 || pr[u] == -1) continue;   // structural zero, or a row/column not assembled
+            if (pr[u] < 0) {                         // a coupling outside the operator pattern
+                atomicOr(A.err, 1);
+                continue;
+            }
+            A.val[pr[u]] += v;
         }
-        A.val[pos] += v;
+    }
+}
+
+// CSR position of every (local row, local column) pair of every element:
+// -1 where the pair is not assembled (no row there, fixed row or column),
+// -2 where the operator pattern lacks the pair (an error if a nonzero lands there)
+__global__ void nl_pos_kernel(const int32_t *elem_dofs, const uint8_t *material, const uint8_t *fixed,
+                              int32_t ds_end, const int32_t *row_ptr, const int32_t *col, int64_t n_el,
+                              int32_t *pos) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_el * 40;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = k / 40;
+        const int lc = (int)(k % 40);
+        const int32_t *ed = elem_dofs + e * 40;
+        const bool solid = material[e] != 0;
+        const int32_t C = ed[lc];
+        int32_t *out = pos + k * 40;
+        for (int r = 0; r < 40; ++r) {
+            const int32_t R = local_row(ed, solid, ds_end, r);
+            if (R < 0 || fixed[R] || fixed[C]) {
+                out[r] = -1;
+                continue;
+            }
+            const int p = find_col(col, row_ptr[R], row_ptr[R + 1], C);
+            out[r] = p >= 0 ? p : -2;
+        }
     }
 }
 
@@ -751,7 +796,9 @@ fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint
     A.col = Aop.col.as<int32_t>();
     A.val = Aop.val64.as<double>();
     A.err = err;
+    A.pos = L.pos.as<int32_t>();
     const int64_t n_el = (int64_t)L.n * L.n;
+    if (!A.pos || L.pos.bytes < (size_t)n_el * 1600 * 4) { set_error("nonlinear position table missing"); return FSI_ERR_STATE; }
     QV *pts = L.pts.as<QV>();
     if (!pts || L.pts.bytes < (size_t)n_el * 9 * sizeof(QV)) { set_error("nonlinear point scratch missing"); return FSI_ERR_STATE; }
     nl_point_kernel<<<(unsigned)((n_el + PT_EPB - 1) / PT_EPB), PT_EPB * 9, 0, s>>>(A, n_el, pts);
@@ -781,6 +828,17 @@ fsi_status launch_nl_jacobian(const NlLevelDev &L, const NlParams &P, const uint
         }
     }
     FSI_TRY(launch_set_fixed_diag(Aop, fixed, Aop.val64.as<double>(), s));
+    return FSI_OK;
+}
+
+fsi_status launch_nl_positions(NlLevelDev &L, const DevCSR &Aop, const uint8_t *fixed, cudaStream_t s) {
+    const int64_t n_el = (int64_t)L.n * L.n;
+    FSI_TRY(L.pos.alloc((size_t)n_el * 1600 * 4));
+    nl_pos_kernel<<<grid_of(n_el * 40, 256), 256, 0, s>>>(L.elem_dofs.as<int32_t>(), L.material.as<uint8_t>(), fixed,
+                                                           L.ds_end, Aop.ptr.as<int32_t>(), Aop.col.as<int32_t>(), n_el,
+                                                           L.pos.as<int32_t>());
+    count_launch();
+    FSI_CUDA(cudaGetLastError());
     return FSI_OK;
 }
 
