@@ -59,6 +59,7 @@ RTOL = 1e-8
 NL_FORCE = 20.0       # body-force amplitude of the nonlinear leg
 NL_STEPS = 4          # implicit time steps of the nonlinear leg
 NL_RTOL = 1e-8        # Newton tolerance on ||R|| relative to the step's initial residual
+NL_JAC_INST_PER_ELEMENT = 142.1e3   # float64 thread-instructions per element of one Jacobian (ncu)
 # the timed smoother: the locally multiplicative sweep on this many finest
 # levels (additive below); 0 = additive everywhere
 HEAD_MULT = 1
@@ -388,9 +389,12 @@ def run_ours(args, rank, world, local):
     outer_gbs = prof["outer_bytes"] / (outer_ms * 1e-3) / 1e9
     outer_gflops = 2.0 * prof["outer_fma"] / (outer_ms * 1e-3) / 1e9
     gs64_gflops = 2.0 * prof["gs64_fma"] / (prof["gs64_ms"] * 1e-3) / 1e9 if prof["gs64_ms"] > 0 else None
+    gs64_gbs = prof["gs64_bytes"] / (prof["gs64_ms"] * 1e-3) / 1e9 if prof["gs64_ms"] > 0 else None
     gs1_gbs = prof["gs1_bytes"] / (prof["gs1_ms"] * 1e-3) / 1e9 if prof["gs1_ms"] > 0 else None
     fp64_peak = s.profile(3)["fp64_gflops"]          # measured float64 FMA rate of this GPU
     peak, peak_kind = measured_peaks()
+    gs64_bound_frac = (max(2.0 * prof["gs64_fma"] / (fp64_peak * 1e9), prof["gs64_bytes"] / (peak * 1e9))
+                       / (prof["gs64_ms"] * 1e-3) if prof["gs64_ms"] > 0 and fp64_peak else None)
     # ---- end to end through the public call with host buffers (mixed)
     b_pin = torch.from_numpy(b_host).pin_memory()
     x_pin = torch.empty_like(b_pin).pin_memory()
@@ -617,6 +621,7 @@ def run_ours(args, rank, world, local):
         jac_ms.append(e0.elapsed_time(e1))
     del snl, Un_nl, U_nl
     torch.cuda.empty_cache()
+    n_el_all = sum((p.n_fine >> l) ** 2 for l in range(p.n_levels))
     nl_newton = [st["newton_steps"] for st in nl_steps]
     nl_its = [i for st in nl_steps for i in st["iterations"]]
     nl_rho = [r for st in nl_steps for r in st["rho"]]
@@ -633,7 +638,18 @@ def run_ours(args, rank, world, local):
                                "block_setup": sum(st["setup_ms"] for st in nl_steps) / max(sum(nl_newton), 1),
                                "solve": sum(st["solve_ms"] for st in nl_steps) / max(sum(nl_newton), 1)},
         "jacobian_all_levels_ms": min(jac_ms),
-        "jacobian_elements_per_s": sum((p.n_fine >> l) ** 2 for l in range(p.n_levels)) / (min(jac_ms) * 1e-3),
+        # float64-pipe roofline of the assembly: float64 thread-instructions per
+        # element counted by ncu on the 128^2 fine level (point + d/u/p seed
+        # kernels, profiles/nl_jacobian_c4.md) x elements of all levels, over
+        # the measured float64 FMA rate in instructions (half its flop rate)
+        "jacobian_roofline": {
+            "bound": "fp64", "inst_per_element": NL_JAC_INST_PER_ELEMENT,
+            "achieved_ginst_s": NL_JAC_INST_PER_ELEMENT * n_el_all / (min(jac_ms) * 1e-3) / 1e9,
+            "peak_ginst_s": fp64_peak / 2.0 if fp64_peak else None,
+            "frac": (NL_JAC_INST_PER_ELEMENT * n_el_all / (min(jac_ms) * 1e-3) / 1e9 / (fp64_peak / 2.0)
+                     if fp64_peak else None),
+            "note": "includes the coarse-level inverse and the ELL refills of nl_jacobian"},
+        "jacobian_elements_per_s": n_el_all / (min(jac_ms) * 1e-3),
         "newton_fine_dof_per_s": job_throughput(n * sum(nl_newton), sum(nl_ms), world),
         "setup_s": setup_nl_s,
         "steps": [{"newton": st["newton_steps"], "its": st["iterations"], "ms": round(st["ms"], 2)}
@@ -727,9 +743,15 @@ def run_ours(args, rank, world, local):
                                        "achieved_fp64_gflops": outer_gflops,
                                        "frac_fp64_measured": outer_gflops / fp64_peak if fp64_peak else None,
                                        "mean_launch_ms": outer_ms},
-                    "gram_schmidt_f64": {"bound": "fp64", "achieved_gflops": gs64_gflops,
+                    "gram_schmidt_f64": {"bound": "fp64 and hbm", "achieved_gflops": gs64_gflops,
                                          "frac_fp64_measured": (gs64_gflops / fp64_peak
                                                                 if gs64_gflops and fp64_peak else None),
+                                         "achieved_gbs": gs64_gbs,
+                                         "frac_hbm": gs64_gbs / peak if gs64_gbs else None,
+                                         # time the passes need at the slower of their two bounds
+                                         # (float64 FMAs at the measured rate, bytes at the measured
+                                         # copy bandwidth) over the time they take
+                                         "frac_of_bound": gs64_bound_frac,
                                          "launches_timed": prof["gs64_launches"]},
                     "gram_schmidt_first_pass_f32": {"bound": "hbm", "achieved_gbs": gs1_gbs,
                                                     "frac": gs1_gbs / peak if gs1_gbs else None,
@@ -753,7 +775,9 @@ def run_ours(args, rank, world, local):
         "fs_vs_as_3d": {"fs_ms": round(ms_3d, 2), "as_ms": round(ms_as3, 2), "as_its": its_as3["median"]},
         "nonlinear": {"ms_per_time_step": round(nonlinear["ms_per_time_step"], 1),
                       "s_max": nonlinear["s_max"], "N": round(nonlinear["N"], 2), "rho": round(nonlinear["rho"], 3),
-                      "jacobian_ms": round(nonlinear["jacobian_all_levels_ms"], 2)},
+                      "jacobian_ms": round(nonlinear["jacobian_all_levels_ms"], 2),
+                      "jacobian_fp64_frac": (round(nonlinear["jacobian_roofline"]["frac"], 3)
+                                             if nonlinear["jacobian_roofline"]["frac"] else None)},
         "e2e": {"value": job_throughput(n, ms_e2e, world), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": int(b_pin.numel() * 8), "d2h_bytes_per_step": int(x_pin.numel() * 8)},
         "roofline": {"bound": "hbm", "kernel": "fine-level sweep (12 apply + 11 residual passes, 2 streams)",

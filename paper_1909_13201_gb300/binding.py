@@ -316,7 +316,7 @@ class FSISolver:
                 "restrict_launches": int(out[15]), "restrict_ms": out[16], "restrict_bytes": out[17],
                 "prolong_launches": int(out[18]), "prolong_ms": out[19], "prolong_bytes": out[20],
                 "fp64_gflops": out[21], "gs64_launches": int(out[22]), "gs64_ms": out[23], "gs64_fma": out[24],
-                "gs1_launches": int(out[25]), "gs1_ms": out[26], "gs1_bytes": out[27]}
+                "gs1_launches": int(out[25]), "gs1_ms": out[26], "gs1_bytes": out[27], "gs64_bytes": out[28]}
 
     # ------------------------------------------------------------ nonlinear
     def nl_setup(self, force=20.0, period=1.0, C1=0.0, C2=0.0):

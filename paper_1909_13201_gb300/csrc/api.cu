@@ -414,13 +414,19 @@ fsi_status issue_step(Context &cx, Problem &pb, int j, int m, bool tr) {
         FSI_TRY(launch_reduce_partials(part, NDOT, nv, h1, 0, s));
         {
             ProfMark pm(cx, 6, true);       // float64 update (+ float64 dots): nv (2 nv) FMAs per row
-            if (cx.profile) cx.prof_work[6] += (V32 ? 1.0 : 2.0) * nv * n;
+            if (cx.profile) {
+                cx.prof_work[6] += (V32 ? 1.0 : 2.0) * nv * n;
+                cx.prof_gs64_bytes += (double)nv * n * (V32 ? 12.0 : 8.0) + 16.0 * n;   // V (+ V32), w in and out
+            }
             FSI_TRY(launch_update_dot(w, V, n, nv, h1, n, part, NRED, 0, s, nullptr, V32));
         }
         FSI_TRY(launch_reduce_partials(part, NRED, nv, h2, 0, s));
         {
             ProfMark pm(cx, 6, true);       // float64 update + norm: nv + 1 FMAs per row
-            if (cx.profile) cx.prof_work[6] += (nv + 1.0) * n;
+            if (cx.profile) {
+                cx.prof_work[6] += (nv + 1.0) * n;
+                cx.prof_gs64_bytes += (double)nv * n * 8.0 + 16.0 * n;
+            }
             FSI_TRY(launch_update_dot(w, V, n, nv, h2, n, part, NRED, 1, s));
         }
         FSI_TRY(launch_reduce_partials(part, NRED, 1, scal + 7, 0, s));
@@ -1906,6 +1912,7 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
             cx->prof_ms[k] = 0;
             cx->prof_n[k] = 0;
             cx->prof_work[k] = 0;
+            cx->prof_gs64_bytes = 0;
         }
         cx->launch_base = launches_so_far();
         cx->profile = true;
@@ -1953,7 +1960,8 @@ fsi_status fsi_profile(fsi_ctx *ctx, int mode, double *out) {
     out[25] = (double)cx->prof_n[7];
     out[26] = cx->prof_ms[7];
     out[27] = cx->prof_work[7];
-    for (int k = 28; k < 32; ++k) out[k] = 0.0;
+    out[28] = cx->prof_gs64_bytes;
+    for (int k = 29; k < 32; ++k) out[k] = 0.0;
     return FSI_OK;
 }
 

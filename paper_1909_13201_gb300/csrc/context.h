@@ -330,6 +330,7 @@ struct Context {
     double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double prof_work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_gs64_bytes = 0;      // bytes the float64 Gram-Schmidt passes must move (basis, w)
     int64_t launch_base = 0;
     // solves run on a context-owned non-blocking stream
     cudaStream_t work = nullptr;
