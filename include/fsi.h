@@ -304,7 +304,9 @@ fsi_status fsi_apply_vcycle(fsi_ctx *ctx, int prob, const double *v, double *z, 
  * by mode 3 (independent FMA chains on every SM; 0 otherwise), [22] float64
  * Gram-Schmidt passes timed (update and dots, update and norm), [23] their
  * ms, [24] their float64 FMAs in total, [25] first Gram-Schmidt passes timed,
- * [26] their ms, [27] their bytes in total, [28..31] reserved.  The
+ * [26] their ms, [27] their bytes in total, [28] bytes the float64
+ * Gram-Schmidt passes of [22] must move in total (basis columns, their
+ * float32 copy where read, w in and out), [29..31] reserved.  The
  * Gram-Schmidt passes are timed in host-driven solves only (solves run
  * host-driven while recording).  On a fine level with the multiplicative
  * sweep (mult_levels) a timed "smoother launch" is the whole sweep (its pass
