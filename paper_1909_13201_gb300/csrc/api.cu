@@ -899,12 +899,11 @@ std::vector<double> smoother_signature(const Context &cx) {
 
 // Gather and invert the Schwarz blocks of level l (l >= 1) with the
 // context's factor method into the level's existing inverse storage.
-fsi_status invert_level_blocks(Context &cx, Problem &pb, size_t l) {
-    cudaStream_t s = cx.stream;
+// (launch only, on stream s; flags accumulate in cx.flags)
+fsi_status launch_level_inversion(Context &cx, Problem &pb, size_t l, cudaStream_t s) {
     LevelDev &D = pb.dev[l];
     const LevelHost &H = pb.host[l];
     const int store = D.inv_store;
-    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
     int method = cx.factor;
     if (method == FSI_FACTOR_AUTO) method = store == 0 ? FSI_FACTOR_FP64 : FSI_FACTOR_TF32;
     {
@@ -926,6 +925,13 @@ fsi_status invert_level_blocks(Context &cx, Problem &pb, size_t l) {
         else
             FSI_TRY(launch_block_invert_tc(D.A, D, store, method == FSI_FACTOR_TF32, cx.flags.as<int>(), s));
     }
+    return FSI_OK;
+}
+
+fsi_status invert_level_blocks(Context &cx, Problem &pb, size_t l) {
+    cudaStream_t s = cx.stream;
+    FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
+    FSI_TRY(launch_level_inversion(cx, pb, l, s));
     int fw[3] = {0, 0, 0};
     FSI_CUDA(cudaMemcpyAsync(fw, cx.flags.p, sizeof(fw), cudaMemcpyDeviceToHost, s));
     FSI_CUDA(cudaStreamSynchronize(s));
@@ -2445,6 +2451,7 @@ fsi_status nl_setup_problem(Context &cx, Problem &pb, const fsi_nl_params &in) {
     FSI_TRY(pb.nl_R.alloc((size_t)n * 8));
     FSI_TRY(pb.nl_dU.alloc((size_t)n * 8));
     for (auto &f : pb.nl_fj) FSI_CUDA(f.create());
+    FSI_TRY(pb.nl_coarse_work.alloc((size_t)pb.n0 * 2 * pb.n0 * 8));
     FSI_CUDA(cudaStreamSynchronize(s));
     pb.nl_ready = true;
     return FSI_OK;
@@ -2484,7 +2491,8 @@ fsi_status nl_assemble(Context &cx, Problem &pb, const double *U, const double *
         return FSI_ERR_STATE;
     }
     FSI_CUDA(cudaMemsetAsync(cx.flags.p, 0, 16, s));
-    FSI_TRY(coarse_invert(pb.dev[0].A, pb.n0, pb.coarse_inv.as<double>(), cx.flags.as<int>(), s));
+    FSI_TRY(coarse_invert(pb.dev[0].A, pb.n0, pb.coarse_inv.as<double>(), cx.flags.as<int>(), s,
+                          pb.nl_coarse_work.as<double>()));
     int flag = 0;
     FSI_TRY(read_flag(cx, &flag));
     if (flag) {
@@ -2500,6 +2508,23 @@ fsi_status nl_assemble(Context &cx, Problem &pb, const double *U, const double *
     pb.ops_changed = true;
     cx.smoothers_ready = false;
     return FSI_OK;
+}
+
+// The operators of one Newton step: the Jacobians of every level with the
+// coarse inverse, then the in-place refactorisation of the Schwarz blocks.
+// (Running the coarse levels' refactorisation beside the fine Jacobian on a
+// second stream was measured: no gain on 256^2, the fine Jacobian's CTAs
+// fill every SM.)
+fsi_status nl_operators(Context &cx, Problem &pb, const double *U, const double *Un, double t_new, double *jac_ms,
+                        double *setup_ms) {
+    auto t0 = std::chrono::steady_clock::now();
+    FSI_TRY(nl_assemble(cx, pb, U, Un, t_new));
+    *jac_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    t0 = std::chrono::steady_clock::now();
+    fsi_status e = refactor_smoothers(cx, pb);
+    if (e == FSI_OK) FSI_CUDA(cudaStreamSynchronize(cx.stream));
+    *setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return e;
 }
 
 // ||v||_2 on the host
@@ -2629,22 +2654,12 @@ fsi_status fsi_nl_step(fsi_ctx *ctx, int prob, const double *Un, double *U, doub
         if (!std::isfinite(res)) { status = FSI_ERR_NONFINITE; set_error("non-finite nonlinear residual"); break; }
         if (res <= o->nl_rtol * std::max(r0, 1e-300) || res == 0.0) { status = FSI_OK; S.converged = 1; break; }
         if (k == o->max_newton) break;
-        auto t0 = std::chrono::steady_clock::now();
-        fsi_status e = nl_assemble(cx, pb, U, Un, t_new);
-        S.jacobian_ms += ms_since(t0);
-        if (e != FSI_OK) { status = e; break; }
-        t0 = std::chrono::steady_clock::now();
-        e = refactor_smoothers(cx, pb);
-        if (e == FSI_OK) {
-            cudaError_t ce = cudaStreamSynchronize(s);
-            if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); e = FSI_ERR_CUDA; }
-        }
-        S.setup_ms += ms_since(t0);
+        fsi_status e = nl_operators(cx, pb, U, Un, t_new, &S.jacobian_ms, &S.setup_ms);
         if (e != FSI_OK) { status = e; break; }
         cx.smoothers_ready = std::none_of(cx.probs.begin(), cx.probs.end(),
                                           [](const Problem &q) { return q.ops_changed; });
         FSI_TRY(launch_nl_axpby(R, R, -1.0, 0.0, n, s));      // R <- -R
-        t0 = std::chrono::steady_clock::now();
+        const auto t0 = std::chrono::steady_clock::now();
         fsi_solve_stats ls{};
         e = solve_one(cx, pb, R, dU, &lo, &ls, false);
         S.solve_ms += ms_since(t0);

@@ -265,6 +265,7 @@ struct Problem {
     std::vector<NlLevelDev> nlev;    // index = level
     DevBuf nl_R, nl_dU;              // fine residual (negated for the solve) and Newton update
     ForkJoin nl_fj[2];               // side streams of the Jacobian's seed kinds
+    DevBuf nl_coarse_work;           // n0 x 2 n0 float64: the coarse inverse's working storage
 };
 
 // kernels launched by the library (all contexts), for launch accounting
@@ -396,7 +397,10 @@ bool gj_tc_plan(int n, int *C_out, int *R_out, size_t *smem_out);
 fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int storage, bool tensor, int *flags,
                                   cudaStream_t s);
 
-fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s);
+// work: n0 x 2 n0 float64 scratch (nullable: a temporary, and the call
+// synchronises the stream before freeing it)
+fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s,
+                         double *work = nullptr);
 // t = m^T for an n x n row-major float64 matrix
 fsi_status launch_transpose(const double *m, int64_t n, double *t, cudaStream_t s);
 

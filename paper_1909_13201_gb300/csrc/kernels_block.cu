@@ -836,26 +836,32 @@ fsi_status launch_transpose(const double *m, int64_t n, double *t, cudaStream_t 
     return FSI_OK;
 }
 
-fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s) {
-    DevBuf M;
-    FSI_TRY(M.alloc((size_t)n0 * 2 * n0 * 8));
-    coarse_init_kernel<<<256, 256, 0, s>>>(nullptr, nullptr, nullptr, n0, M.as<double>());
+fsi_status coarse_invert(const DevCSR &A0, int64_t n0, double *inv, int *flags, cudaStream_t s, double *work) {
+    // [A | I] -> [I | A^{-1}] in n0 x 2 n0 working storage: the caller's
+    // (no allocation, no synchronisation) or a temporary
+    DevBuf Mb;
+    if (!work) {
+        FSI_TRY(Mb.alloc((size_t)n0 * 2 * n0 * 8));
+        work = Mb.as<double>();
+    }
+    double *M = work;
+    coarse_init_kernel<<<256, 256, 0, s>>>(nullptr, nullptr, nullptr, n0, M);
     count_launch();
     coarse_fill_kernel<<<64, 256, 0, s>>>(A0.ptr.as<int32_t>(), A0.col.as<int32_t>(), A0.val64.as<double>(), n0,
-                                          M.as<double>());
+                                          M);
     count_launch();
     FSI_CUDA(cudaGetLastError());
     for (int64_t k = 0; k < n0; ++k) {
-        coarse_pivot_kernel<<<1, 1024, 0, s>>>(M.as<double>(), n0, k, flags);
+        coarse_pivot_kernel<<<1, 1024, 0, s>>>(M, n0, k, flags);
         count_launch();
-        coarse_elim_kernel<<<(unsigned)n0, 256, 0, s>>>(M.as<double>(), n0, k);
+        coarse_elim_kernel<<<(unsigned)n0, 256, 0, s>>>(M, n0, k);
         count_launch();
     }
     FSI_CUDA(cudaGetLastError());
-    coarse_extract_kernel<<<256, 256, 0, s>>>(M.as<double>(), n0, inv);
+    coarse_extract_kernel<<<256, 256, 0, s>>>(M, n0, inv);
     count_launch();
     FSI_CUDA(cudaGetLastError());
-    FSI_CUDA(cudaStreamSynchronize(s));
+    if (Mb.p) FSI_CUDA(cudaStreamSynchronize(s));     // the temporary goes out of scope
     return FSI_OK;
 }
 
