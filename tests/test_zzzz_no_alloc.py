@@ -7,8 +7,8 @@ the library's static device array: on additive levels and on a level smoothed
 by the multiplicative sweep, where a transposed call before the transposed
 operators exist is refused (it would have to build them, which allocates).
 A level above FSI_NOALLOC_MAX_DOFS is refused with FSI_ERR_ARG.  Collected
-after the parity tests so that a run stopping at the first failure has
-already run them (only the full-size tests follow).
+last (file name) so that a run stopping at the first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
