@@ -415,7 +415,8 @@ typedef struct {
 fsi_status fsi_nl_setup(fsi_ctx *ctx, const fsi_nl_params *params);
 
 /* fsi_nl_residual -- R(U; U_n) at time t_new on level `level` (device
- * float64 vectors of that level's dof count, J2 order). */
+ * float64 vectors of that level's dof count, J2 order; R must not overlap U
+ * or U_n). */
 fsi_status fsi_nl_residual(fsi_ctx *ctx, int prob, int level, const double *U, const double *Un,
                            double t_new, double *R);
 
@@ -433,7 +434,7 @@ fsi_status fsi_nl_jacobian(fsi_ctx *ctx, int prob, const double *U, const double
 
 /* fsi_nl_step -- one time step to t_new by exact Newton from the initial
  * guess in U (device, level L-1; on return the new state), U_n the state at
- * t_new - dt.  Per Newton step: the Jacobians (fsi_nl_jacobian), the
+ * t_new - dt (U and U_n must not overlap).  Per Newton step: the Jacobians (fsi_nl_jacobian), the
  * smoothers with the options of the last fsi_setup_smoothers call (which
  * must have run once), FGMRES on J dU = -R from dU = 0, U += dU.  Returns
  * FSI_ERR_NOT_CONVERGED when max_newton steps do not reach nl_rtol (stats
