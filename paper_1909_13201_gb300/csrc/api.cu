@@ -2577,7 +2577,7 @@ fsi_status fsi_nl_residual(fsi_ctx *ctx, int prob, int level, const double *U, c
                            double *R) {
     g_last_error.clear();
     Problem *pb = nl_problem(ctx, prob);
-    if (!pb || !U || !Un || !R || level < 0 || level >= (int)pb->dev.size()) {
+    if (!pb || !U || !Un || !R || level < 0 || level >= (int)pb->dev.size() || R == U || R == Un) {
         set_error("invalid arguments");
         return FSI_ERR_ARG;
     }
@@ -2621,7 +2621,7 @@ fsi_status fsi_nl_step(fsi_ctx *ctx, int prob, const double *Un, double *U, doub
     g_last_error.clear();
     const auto t_call = std::chrono::steady_clock::now();
     Problem *pbp = nl_problem(ctx, prob);
-    if (!pbp || !Un || !U || !o) { set_error("invalid arguments"); return FSI_ERR_ARG; }
+    if (!pbp || !Un || !U || !o || U == Un) { set_error("invalid arguments"); return FSI_ERR_ARG; }
     if (!(o->nl_rtol >= 0) || o->max_newton < 1 || o->max_newton > FSI_NL_MAX_NEWTON || !(o->lin_rtol > 0) ||
         o->restart < 1 || o->restart > 64 || o->max_iters < 1) {
         set_error("Newton options out of range");
