@@ -142,3 +142,143 @@ def test_newton_converges_quadratically():
     for k in range(1, len(r) - 1):
         if r[k] < 1e-3 * r[0] and r[k + 1] > 1e-12 * r[0]:
             assert r[k + 1] <= 100.0 * r[k] ** 2 / r[0], r
+
+
+# ---------------------------------------------------------------------------
+# single fluid elements with fields the Q2/Q1 spaces hold exactly, against
+# integrals sympy evaluates in closed form (an evaluation independent of the
+# oracle's tensor contractions and quadrature)
+
+def _fluid_element(pr):
+    lev = pr.levels[-1]
+    m = pr.nl[-1].maps
+    e = int(np.flatnonzero(lev.material == 0)[-1])            # top row: fluid
+    one = NL.ElementMaps.__new__(NL.ElementMaps)
+    one.solid, one.cols, one.rows = m.solid[[e]], m.cols[[e]], m.rows[[e]]
+    return lev, one
+
+
+def _sym_q2(h):
+    """sympy Q2 basis on [0, h]^2 in the oracle's local order (x fastest) and
+    Q1 basis; node coordinates."""
+    sympy = pytest.importorskip("sympy")
+    x, y = sympy.symbols("x y")
+    s, t = x / h, y / h
+    L = [(2 * s - 1) * (s - 1), 4 * s * (1 - s), s * (2 * s - 1)]
+    M = [(2 * t - 1) * (t - 1), 4 * t * (1 - t), t * (2 * t - 1)]
+    phi = [L[a % 3] * M[a // 3] for a in range(9)]
+    X = [(sympy.Rational(a % 3, 2) * h, sympy.Rational(a // 3, 2) * h) for a in range(9)]
+    l1 = [1 - s, s]
+    m1 = [1 - t, t]
+    psi = [l1[b % 2] * m1[b // 2] for b in range(4)]
+    return sympy, x, y, phi, X, psi
+
+
+def _integrate(sympy, f, x, y, h):
+    return float(sympy.integrate(sympy.integrate(sympy.expand(f), (x, 0, h)), (y, 0, h)))
+
+
+def sympy_rational(h):
+    sympy = pytest.importorskip("sympy")
+    return sympy.nsimplify(h)
+
+
+def test_fluid_convection_ale_and_viscous_terms_closed_form(c0):
+    """Moving mesh with a uniform displacement increment (F = I, mesh velocity
+    w0), a linear velocity field u with u_n = u, p = 0, f = 0, tau = 0:
+    momentum row (a, i) = int rho ((u - w0).grad) u_i phi_a + mu (d_j u_i +
+    d_i u_j) d_j phi_a, continuity row b = -int div u psi_b, A rows zero."""
+    p, pr = c0
+    lev, one = _fluid_element(pr)
+    h = lev.h
+    P = NL.Params(p, force=0.0)
+    sympy_h = sympy_rational(h)
+    sympy, x, y, phi, X, psi = _sym_q2(sympy_h)
+    c = [0.3, -1.2, 0.7, 0.5, 0.9, -0.4]
+    w0 = (0.8, -0.6)
+    u = (c[0] + c[1] * x + c[2] * y, c[3] + c[4] * x + c[5] * y)
+    Ul = np.zeros((1, NL.NLOC))
+    Unl = np.zeros((1, NL.NLOC))
+    for a in range(9):
+        xa, ya = float(X[a][0]), float(X[a][1])
+        for i in range(2):
+            Ul[0, 2 * a + i] = P.dt * w0[i]                                   # d = d_n + dt w0
+            val = float(u[i].subs({x: xa, y: ya}))
+            Ul[0, 18 + 2 * a + i] = val
+            Unl[0, 18 + 2 * a + i] = val
+    fq = np.zeros((1, 9, 2))
+    R = NL.element_residual(lev, P, Ul, Unl, np.zeros((1, 9)), fq, fq, one, NL.shape_tables())
+    rho, mu = P.rho_f, P.mu_f
+    grad = [[sympy.diff(u[i], v) for v in (x, y)] for i in range(2)]
+    for a in range(9):
+        for i in range(2):
+            conv = sum((u[j] - w0[j]) * grad[i][j] for j in range(2))
+            visc = sum(mu * (grad[i][j] + grad[j][i]) * sympy.diff(phi[a], (x, y)[j]) for j in range(2))
+            ref = _integrate(sympy, rho * conv * phi[a] + visc, x, y, sympy_h)
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-12 * (1.0 + abs(ref)), (a, i, R[0, 2 * a + i], ref)
+    assert np.abs(R[0, 18:36]).max() < 1e-12                                    # A rows: grad d = 0
+    div = c[1] + c[5]
+    for b in range(4):
+        ref = -div * _integrate(sympy, psi[b], x, y, sympy_h)
+        assert abs(R[0, 36 + b] - ref) <= 1e-13 * (1.0 + abs(ref))
+
+
+@pytest.mark.parametrize("speed", [1e-4, 5.0])
+def test_supg_term_closed_form(c0, speed):
+    """Undeformed element, constant velocity U0 from rest (u_n = 0), p = 0,
+    f = 0: the strong residual is rho U0 / dt, the SUPG test function
+    rho U0.grad phi_a and tau = min(1/(4 lambda nu), 1/(sqrt(lambda) |U0|))
+    with lambda of the square element in closed form; both branches of the
+    minimum (slow and fast flow)."""
+    p, pr = c0
+    lev, one = _fluid_element(pr)
+    h = lev.h
+    P = NL.Params(p, force=0.0)
+    sh = sympy_rational(h)
+    sympy, x, y, phi, X, psi = _sym_q2(sh)
+    # lambda_k of the square element (bubble eigenproblem, closed form)
+    b = 16 * (x / sh) * (1 - x / sh) * (y / sh) * (1 - y / sh)
+    H = [[sympy.diff(b, u_, v_) for v_ in (x, y)] for u_ in (x, y)]
+    lap = H[0][0] + H[1][1]
+    K = np.array([[_integrate(sympy, lap ** 2 * (1 if i == j else 0) + 2 * lap * H[i][j]
+                              + H[i][0] * H[j][0] + H[i][1] * H[j][1], x, y, sh) for j in range(2)]
+                  for i in range(2)])
+    Mb = _integrate(sympy, sympy.diff(b, x) ** 2 + sympy.diff(b, y) ** 2, x, y, sh)
+    lam = np.linalg.eigvalsh(K).max() / Mb
+    nu = P.mu_f / P.rho_f
+    U0 = speed * np.array([0.6, 0.8])
+    tau = min(1.0 / (4.0 * lam * nu), 1.0 / (math.sqrt(lam) * np.linalg.norm(U0)))
+    Ul = np.zeros((1, NL.NLOC))
+    for a in range(9):
+        Ul[0, 18 + 2 * a:18 + 2 * a + 2] = U0
+    fq = np.zeros((1, 9, 2))
+    R = NL.element_residual(lev, P, Ul, np.zeros((1, NL.NLOC)), None, fq, fq, one, NL.shape_tables())
+    rho = P.rho_f
+    for a in range(9):
+        ip = _integrate(sympy, phi[a], x, y, sh)
+        ig = _integrate(sympy, U0[0] * sympy.diff(phi[a], x) + U0[1] * sympy.diff(phi[a], y), x, y, sh)
+        for i in range(2):
+            ref = rho * U0[i] / P.dt * ip + tau * (rho * U0[i] / P.dt) * rho * ig
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-10 * (abs(ref) + rho * abs(U0[i]) / P.dt * abs(ip)), \
+                (speed, a, i, R[0, 2 * a + i], ref)
+
+
+def test_body_force_crank_nicolson_closed_form(c0):
+    """At rest (u = u_n = 0, d = d_n = 0, p = 0) the fluid momentum rows hold
+    only the body force, averaged over the two time levels: -rho/2 (f_new +
+    f_old)_i int phi_a (the SUPG test function vanishes with u = w_m = 0)."""
+    p, pr = c0
+    lev, one = _fluid_element(pr)
+    P = NL.Params(p, force=0.0)
+    sh = sympy_rational(lev.h)
+    sympy, x, y, phi, X, psi = _sym_q2(sh)
+    fn, fo = np.array([1.5, -0.5]), np.array([-0.25, 2.0])
+    fqn = np.broadcast_to(fn, (1, 9, 2)).copy()
+    fqo = np.broadcast_to(fo, (1, 9, 2)).copy()
+    Z = np.zeros((1, NL.NLOC))
+    R = NL.element_residual(lev, P, Z, Z, None, fqn, fqo, one, NL.shape_tables())
+    for a in range(9):
+        ip = _integrate(sympy, phi[a], x, y, sh)
+        for i in range(2):
+            ref = -0.5 * P.rho_f * (fn[i] + fo[i]) * ip
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-13 * (1.0 + abs(ref))
