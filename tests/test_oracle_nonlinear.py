@@ -282,3 +282,48 @@ def test_body_force_crank_nicolson_closed_form(c0):
         for i in range(2):
             ref = -0.5 * P.rho_f * (fn[i] + fo[i]) * ip
             assert abs(R[0, 2 * a + i] - ref) <= 1e-13 * (1.0 + abs(ref))
+
+
+def test_mooney_rivlin_homogeneous_deformation_closed_form(c0):
+    """A solid element under the homogeneous deformation F = [[s1, g], [0, s2]]
+    from rest (d_n = 0: P_el(F_n) = 0 in the rest-state convention), u = u_n =
+    0, constant pressure p0: momentum row (a, i) = sum_J T_iJ int d_J phi_a with
+    the constant stress T = 1/2 P_el(F) - p0 J F^{-T}, P_el = J sigma_el F^{-T}
+    (the first Piola-Kirchhoff stress), sigma_el = 2 C1 (B - I) - 2 C2 (B^{-1} -
+    I), B = F F^T -- the law's two invariant terms, which a rigid rotation
+    cannot tell apart, and the transposes a shear exposes; V rows -(J - 1)
+    int psi_b; K rows -M_L d / dt."""
+    p, pr = c0
+    lev = pr.levels[-1]
+    m = pr.nl[-1].maps
+    e = int(np.flatnonzero(lev.material == 1)[0])
+    one = NL.ElementMaps.__new__(NL.ElementMaps)
+    one.solid, one.cols, one.rows = m.solid[[e]], m.cols[[e]], m.rows[[e]]
+    P = NL.Params(p, force=0.0)
+    sh = sympy_rational(lev.h)
+    sympy, x, y, phi, X, psi = _sym_q2(sh)
+    s1, s2, g, p0 = 1.03, 0.98, 0.07, 0.37
+    F = np.array([[s1, g], [0.0, s2]])
+    Ul = np.zeros((1, NL.NLOC))
+    for a in range(9):
+        Xa = np.array([float(X[a][0]), float(X[a][1])])
+        Ul[0, 2 * a:2 * a + 2] = (F - np.eye(2)) @ Xa
+    Ul[0, 36:40] = p0
+    fq = np.zeros((1, 9, 2))
+    R = NL.element_residual(lev, P, Ul, np.zeros((1, NL.NLOC)), np.zeros((1, 9)), fq, fq, one, NL.shape_tables())
+    J = np.linalg.det(F)
+    FiT = np.linalg.inv(F).T
+    B = F @ F.T
+    sig = 2 * P.C1 * (B - np.eye(2)) - 2 * P.C2 * (np.linalg.inv(B) - np.eye(2))
+    T = 0.5 * J * sig @ FiT - p0 * J * FiT
+    for a in range(9):
+        dphi = [_integrate(sympy, sympy.diff(phi[a], v), x, y, sh) for v in (x, y)]
+        for i in range(2):
+            ref = T[i, 0] * dphi[0] + T[i, 1] * dphi[1]
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-12 * (1.0 + np.abs(T).max() * lev.h), (a, i, R[0, 2 * a + i], ref)
+        lump = _integrate(sympy, phi[a], x, y, sh)
+        for i in range(2):
+            assert abs(R[0, 18 + 2 * a + i] + lump * Ul[0, 2 * a + i] / P.dt) <= 1e-12 * (1 + abs(Ul[0, 2 * a + i]) / P.dt)
+    for b in range(4):
+        ref = -(J - 1.0) * _integrate(sympy, psi[b], x, y, sh)
+        assert abs(R[0, 36 + b] - ref) <= 1e-13
