@@ -327,3 +327,41 @@ def test_mooney_rivlin_homogeneous_deformation_closed_form(c0):
     for b in range(4):
         ref = -(J - 1.0) * _integrate(sympy, psi[b], x, y, sh)
         assert abs(R[0, 36 + b] - ref) <= 1e-13
+
+
+def test_fluid_on_deformed_element_closed_form(c0):
+    """Fluid element moved by the homogeneous deformation F = [[s1, g], [0,
+    s2]] (d = d_n: no mesh velocity), a velocity u = G X linear in the
+    reference coordinates with u_n = u, p = 0, f = 0, tau = 0: with the spatial
+    gradient Gx = G F^{-1} (constant) and J = det F, momentum row (a, i) =
+    int J [rho (u . Gx^T)_i phi_a + (mu (Gx + Gx^T) F^{-T})_iK d_K phi_a] dX
+    and continuity row b = -J tr(Gx) int psi_b (the ALE map of gradients and
+    volumes, Sec. 2.2)."""
+    p, pr = c0
+    lev, one = _fluid_element(pr)
+    P = NL.Params(p, force=0.0)
+    sh = sympy_rational(lev.h)
+    sympy, x, y, phi, X, psi = _sym_q2(sh)
+    F = np.array([[1.04, 0.06], [0.0, 0.97]])
+    G = np.array([[0.4, -1.1], [0.8, 0.3]])
+    Ul = np.zeros((1, NL.NLOC))
+    for a in range(9):
+        Xa = np.array([float(X[a][0]), float(X[a][1])])
+        Ul[0, 2 * a:2 * a + 2] = (F - np.eye(2)) @ Xa
+        Ul[0, 18 + 2 * a:18 + 2 * a + 2] = G @ Xa
+    fq = np.zeros((1, 9, 2))
+    R = NL.element_residual(lev, P, Ul, Ul.copy(), np.zeros((1, 9)), fq, fq, one, NL.shape_tables())
+    J = np.linalg.det(F)
+    Fi = np.linalg.inv(F)
+    Gx = G @ Fi
+    T = P.mu_f * (Gx + Gx.T) @ Fi.T
+    uX = [G[i, 0] * x + G[i, 1] * y for i in range(2)]
+    conv = [sum(uX[j] * Gx[i, j] for j in range(2)) for i in range(2)]
+    for a in range(9):
+        for i in range(2):
+            ref = J * _integrate(sympy, P.rho_f * conv[i] * phi[a] + T[i, 0] * sympy.diff(phi[a], x)
+                                 + T[i, 1] * sympy.diff(phi[a], y), x, y, sh)
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-12 * (1.0 + abs(ref)), (a, i, R[0, 2 * a + i], ref)
+    for b in range(4):
+        ref = -J * np.trace(Gx) * _integrate(sympy, psi[b], x, y, sh)
+        assert abs(R[0, 36 + b] - ref) <= 1e-13 * (1.0 + abs(ref))
