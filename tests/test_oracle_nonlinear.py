@@ -365,3 +365,85 @@ def test_fluid_on_deformed_element_closed_form(c0):
     for b in range(4):
         ref = -J * np.trace(Gx) * _integrate(sympy, psi[b], x, y, sh)
         assert abs(R[0, 36 + b] - ref) <= 1e-13 * (1.0 + abs(ref))
+
+
+def test_supg_strong_residual_viscous_and_pressure_terms(c0):
+    """Undeformed element, slow quadratic velocity u (tau in its 1/(4 lambda
+    nu) branch: constant), u_n = 0, bilinear pressure p, f = 0: momentum row
+    (a, i) = int [rho u_i / dt phi_a + 1/2 (rho (u.grad u)_i phi_a + mu (grad u +
+    grad u^T) : grad (phi_a e_i)) - p d_i phi_a] + tau int r_i rho (u.grad phi_a)
+    (Crank-Nicolson: the old state contributes nothing from rest; pressure
+    and strong residual at the new level)
+    with the strong residual r = rho u / dt + rho u.grad u + grad p - mu
+    div(grad u + grad u^T) -- derivatives by sympy, integrals by the
+    3-point Gauss rule of the method (the SUPG integrand's degree exceeds what
+    the rule integrates exactly)."""
+    p, pr = c0
+    lev, one = _fluid_element(pr)
+    P = NL.Params(p, force=0.0)
+    sh = sympy_rational(lev.h)
+    sympy, x, y, phi, X, psi = _sym_q2(sh)
+    # |u| below 4 sqrt(lambda) nu (~4.7 here): tau takes its constant branch;
+    # the viscous and pressure parts of r are a few per cent of it
+    u = [0.3 + 2.0 * x - 1.5 * y + 40.0 * x * y - 30.0 * x ** 2,
+         -0.2 + 1.0 * x + 0.5 * y + 25.0 * y ** 2 - 35.0 * x * y]
+    pf = 0.01 * (0.6 - 2.0 * x / sh + 1.3 * y / sh + 0.9 * x * y / sh ** 2)
+    Ul = np.zeros((1, NL.NLOC))
+    for a in range(9):
+        for i in range(2):
+            Ul[0, 18 + 2 * a + i] = float(u[i].subs({x: X[a][0], y: X[a][1]}))
+    for b in range(4):
+        Ul[0, 36 + b] = float(pf.subs({x: sh * (b % 2), y: sh * (b // 2)}))
+    fq = np.zeros((1, 9, 2))
+    R = NL.element_residual(lev, P, Ul, np.zeros((1, NL.NLOC)), None, fq, fq, one, NL.shape_tables())
+    tau, lam = NL.tau_local(float(sh), P, np.zeros((1, 9, 2)), Ul[:, 18:36].reshape(1, 9, 2), NL.shape_tables())
+    assert np.allclose(tau, 1.0 / (4.0 * lam[0] * P.mu_f / P.rho_f), rtol=1e-14)     # the constant branch
+    t = 1.0 / (4.0 * lam[0] * P.mu_f / P.rho_f)
+    rho, mu, dt = P.rho_f, P.mu_f, P.dt
+    gu = [[sympy.diff(u[i], v) for v in (x, y)] for i in range(2)]
+    conv = [u[0] * gu[i][0] + u[1] * gu[i][1] for i in range(2)]
+    gp = [sympy.diff(pf, x), sympy.diff(pf, y)]
+    divs = [sum(sympy.diff(gu[i][j] + gu[j][i], (x, y)[j]) for j in range(2)) for i in range(2)]
+    r = [rho * u[i] / dt + rho * conv[i] + gp[i] - mu * divs[i] for i in range(2)]
+    gx = [0.5 - 0.5 * math.sqrt(0.6), 0.5, 0.5 + 0.5 * math.sqrt(0.6)]
+    gw = [5 / 18, 8 / 18, 5 / 18]
+    hf = float(sh)
+    for a in range(9):
+        dphi = [sympy.diff(phi[a], v) for v in (x, y)]
+        for i in range(2):
+            integrand = (rho * u[i] / dt * phi[a]
+                         + 0.5 * (rho * conv[i] * phi[a] + sum(mu * (gu[i][j] + gu[j][i]) * dphi[j] for j in range(2)))
+                         - pf * dphi[i]
+                         + t * r[i] * rho * (u[0] * dphi[0] + u[1] * dphi[1]))
+            fn = sympy.lambdify((x, y), integrand, "math")
+            ref = sum(gw[k] * gw[l] * hf * hf * fn(gx[k] * hf, gx[l] * hf) for k in range(3) for l in range(3))
+            assert abs(R[0, 2 * a + i] - ref) <= 1e-11 * (1.0 + abs(ref)), (a, i, R[0, 2 * a + i], ref)
+
+
+def test_injection_maps_coinciding_nodes(c0):
+    """The coarse state takes each coarse dof's value from the fine dof of the
+    same field and component at the same point (Q2 nodes and Q1 vertices of
+    a coarse level are nodes of the finer one); fixed coarse dofs are zero."""
+    p, pr = c0
+    for l in range(1, len(pr.levels)):
+        fine, coarse = pr.levels[l], pr.levels[l - 1]
+        inj = pr.inj[l]
+        def coords(lev, dof):
+            q2 = lev.dof_field[dof] < 2                 # Q2 node (d, u) or Q1 vertex (p)
+            node = lev.dof_node[dof]
+            m = np.where(q2, 2 * lev.n + 1, lev.n + 1)
+            step = np.where(q2, 0.5 * lev.h, lev.h)
+            return np.stack([(node % m) * step, (node // m) * step], -1)
+        has = inj >= 0
+        cd = np.flatnonzero(has)
+        fd = inj[has]
+        assert np.array_equal(coarse.dof_field[cd], fine.dof_field[fd])
+        assert np.array_equal(coarse.dof_comp[cd], fine.dof_comp[fd])
+        np.testing.assert_allclose(coords(coarse, cd), coords(fine, fd), atol=1e-15)
+        # every coarse d/u dof has a fine partner; pressure copies may not
+        assert np.all(has[coarse.dof_field < 2])
+        U = np.random.default_rng(l).standard_normal(fine.n_dofs)
+        Uc = NL.inject(U, inj, coarse)
+        assert np.all(Uc[coarse.fixed] == 0.0)
+        free = has & ~coarse.fixed
+        assert np.array_equal(Uc[free], U[inj[free]])
