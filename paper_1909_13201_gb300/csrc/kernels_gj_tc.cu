@@ -225,26 +225,40 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                 if (bad && lane == 0) sflag[0] = 1;
             }
             __syncthreads();
-            for (int j0 = 0; j0 < n; j0 += PANEL) {
-                // thread: column j = j0 + lane, rows t = warp + 8 q (q < 4)
-                constexpr int QN = PANEL * PANEL / TC_THREADS;
-                float acc[QN];
+            // thread: rows t = warp + 8 q (q < 4) of Rp, columns j = g0 + 32 c +
+            // lane (c < CG) of a group of CG 32-column chunks: per panel row u
+            // 4 + CG shared-memory loads feed 4 CG FMAs
+            constexpr int QN = PANEL * PANEL / TC_THREADS;
+            constexpr int CG = 6;
+            for (int g0 = 0; g0 < n; g0 += CG * 32) {
+                float acc[QN][CG];
 #pragma unroll
-                for (int q = 0; q < QN; ++q) acc[q] = 0.f;
-                const int jj = j0 + lane;
-                if (jj < n) {
-                    for (int u = 0; u < kw; ++u) {
-                        const float m = Ms[(size_t)(lb + u) * ldm + jj];
+                for (int q = 0; q < QN; ++q)
 #pragma unroll
-                        for (int q = 0; q < QN; ++q) acc[q] = fmaf(Dm[(warp + 8 * q) * 33 + u], m, acc[q]);
+                    for (int c = 0; c < CG; ++c) acc[q][c] = 0.f;
+                for (int u = 0; u < kw; ++u) {
+                    float dm[QN];
+#pragma unroll
+                    for (int q = 0; q < QN; ++q) dm[q] = Dm[(warp + 8 * q) * 33 + u];
+                    const float *mrow = Ms + (size_t)(lb + u) * ldm;
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        const int j = g0 + 32 * c + lane;
+                        const float m = j < n ? mrow[j] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < QN; ++q) acc[q][c] = fmaf(dm[q], m, acc[q][c]);
                     }
                 }
                 __syncthreads();
 #pragma unroll
                 for (int q = 0; q < QN; ++q) {
                     const int t = warp + 8 * q;
-                    if (t < kw && jj < n)
-                        Ms[(size_t)(lb + t) * ldm + jj] = (jj >= k0 && jj < k0 + kw) ? Dm[t * 33 + (jj - k0)] : acc[q];
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        const int j = g0 + 32 * c + lane;
+                        if (t < kw && j < n)
+                            Ms[(size_t)(lb + t) * ldm + j] = (j >= k0 && j < k0 + kw) ? Dm[t * 33 + (j - k0)] : acc[q][c];
+                    }
                 }
                 __syncthreads();
             }
