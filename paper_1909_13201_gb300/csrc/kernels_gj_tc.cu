@@ -186,17 +186,41 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     for (int p = 0; p < npanels; ++p) {
         const int k0 = p * PANEL, kw = min(PANEL, n - k0);
         const int owner = k0 / R;
+        const bool own = rank == owner;
+        const int lb = k0 - r0;                         // first panel row (local, owner)
+        // ---- F = -M[rows, K] (0 on the owner's panel rows) into the A operand,
+        //      then M[rows, K] = 0.  Neither touches the panel rows, so it runs
+        //      beside the panel step: in the owner by warps 1..7 while warp 0
+        //      inverts the diagonal block, in the other CTAs while they wait
+        //      for the owner's operand
+        auto build_f = [&](int t0, int stride) {
+            for (int e = t0; e < P.tiles * 128 * PANEL; e += stride) {
+                const int t = (e & 3) | (((e >> 5) & 7) << 2), li = ((e >> 2) & 7) | ((e >> 8) << 3);
+                float v = 0.f;
+                if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) v = -Ms[(size_t)li * ldm + k0 + t];
+                *reinterpret_cast<float *>(Fs + (size_t)(li >> 7) * 16384 + cm_off(li & 127, t)) = TC ? to_tf32(v) : v;
+            }
+        };
+        auto zero_k = [&](int t0, int stride) {
+            for (int e = t0; e < nr * kw; e += stride) {
+                const int li = e / kw, t = e - li * kw;
+                if (!(own && li >= lb && li < lb + kw)) Ms[(size_t)li * ldm + k0 + t] = 0.f;
+            }
+        };
         // ---- 1. owner: Dinv = D^{-1} (D = M[K, K], one warp, padded with the
         //         identity to 32 x 32), then Rp = Dinv M[K, :] in place, with
         //         the panel columns of Rp equal to Dinv
-        if (rank == owner) {
-            const int lb = k0 - r0;                     // first panel row (local)
+        if (own) {
             for (int e = tid; e < PANEL * PANEL; e += blockDim.x) {
                 const int t = e / PANEL, u = e - t * PANEL;
                 Dm[t * 33 + u] = (t < kw && u < kw) ? Ms[(size_t)(lb + t) * ldm + k0 + u] : (t == u ? 1.f : 0.f);
             }
             __syncthreads();
-            if (warp == 0) {
+            if (warp != 0) {
+                build_f(tid - 32, TC_THREADS - 32);
+                asm volatile("bar.sync 1, %0;" ::"r"(TC_THREADS - 32) : "memory");   // warps 1..7
+                zero_k(tid - 32, TC_THREADS - 32);
+            } else {
                 // lane j holds column j of D; row t of the pivot step and the
                 // multipliers D[u][t] come from lane t by shuffles
                 float d[PANEL];
@@ -269,6 +293,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                 const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
                 *reinterpret_cast<float *>(Bs + cm_off(j, t)) = TC ? to_tf32(v) : v;
             }
+        } else {
+            build_f(tid, TC_THREADS);
+            __syncthreads();
+            zero_k(tid, TC_THREADS);
         }
         if (C > 1) {
             cluster.sync();
@@ -280,22 +308,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
         }
         __syncthreads();
-        // ---- 3. F = -M[rows, K] (0 on the panel rows), zero M[rows, K]
-        const bool own = rank == owner;
-        const int lb = k0 - r0;
-        for (int e = tid; e < P.tiles * 128 * PANEL; e += blockDim.x) {
-            const int t = (e & 3) | (((e >> 5) & 7) << 2), li = ((e >> 2) & 7) | ((e >> 8) << 3);
-            float v = 0.f;
-            if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) {
-                v = -Ms[(size_t)li * ldm + k0 + t];
-            }
-            *reinterpret_cast<float *>(Fs + (size_t)(li >> 7) * 16384 + cm_off(li & 127, t)) = TC ? to_tf32(v) : v;
-        }
-        __syncthreads();
-        for (int e = tid; e < nr * kw; e += blockDim.x) {
-            const int li = e / kw, t = e - li * kw;
-            if (!(own && li >= lb && li < lb + kw)) Ms[(size_t)li * ldm + k0 + t] = 0.f;
-        }
         if (TC) {
             // ---- 4a. tensor cores: D = F x Rp, then M += D
             asm volatile("fence.proxy.async.shared::cta;");
