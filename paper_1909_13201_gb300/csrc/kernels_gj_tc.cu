@@ -149,19 +149,35 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
         }
         __syncthreads();
-        for (int li = warp; li < nr; li += TC_THREADS / 32) {
-            const int g = sidx[r0 + li];
-            const int a = P.row_ptr[g], b = P.row_ptr[g + 1];
-            float *mrow = Ms + (size_t)li * ldm;
-            for (int k = a + lane; k < b; k += 64) {
-                const bool two = k + 32 < b;
-                const int c0 = P.col[k];
-                const float v0 = (float)P.val[k];
-                const int c1 = two ? P.col[k + 32] : -1;
-                const float v1 = two ? (float)P.val[k + 32] : 0.f;
-    #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int c = u ? c1 : c0;
+        // two rows per warp at a time (rows li and li + 8): their row bounds,
+        // then up to 64 entries of each, are loaded before any is used
+        constexpr int NW = TC_THREADS / 32;
+        for (int li0 = warp; li0 < nr; li0 += 2 * NW) {
+            int a[2], b[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int li = li0 + r * NW;
+                a[r] = b[r] = 0;
+                if (li < nr) {
+                    const int g = sidx[r0 + li];
+                    a[r] = P.row_ptr[g];
+                    b[r] = P.row_ptr[g + 1];
+                }
+            }
+            const int len = max(b[0] - a[0], b[1] - a[1]);
+            for (int off = lane; off < len; off += 64) {
+                int cc[4];
+                float vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = u >> 1, k = a[r] + off + 32 * (u & 1);
+                    const bool in = k < b[r];
+                    cc[u] = in ? P.col[k] : -1;
+                    vv[u] = in ? (float)P.val[k] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = cc[u];
                     if (c < 0) continue;
                     uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
                     int pos = -1;
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                         if (kk == -1) break;
                         h = (h + 1) & (HT - 1);
                     }
-                    if (pos >= 0) mrow[pos] = u ? v1 : v0;
+                    if (pos >= 0) Ms[(size_t)(li0 + (u >> 1) * NW) * ldm + pos] = vv[u];
                 }
             }
         }
