@@ -6,12 +6,16 @@
 // The block's rows live in shared memory (float32, row-major), split over a
 // thread-block cluster of C CTAs when they do not fit one CTA.  Columns are
 // eliminated in panels of 32:
-//   1. the CTA owning the panel's 32 rows inverts D = M[K, K] (one warp,
-//      Gauss-Jordan on 32 x 32 in registers, lane j holding column j) and forms
-//      Rp = D^{-1} M[K, :] with the panel columns replaced by D^{-1};
+//   1. the CTA owning the panel's 32 rows forms Rp = D^{-1} M[K, :] (D =
+//      M[K, K]) with the panel columns replaced by D^{-1}: unblocked Gauss-
+//      Jordan restricted to the 32 panel rows, the rows held in registers by
+//      all eight warps (4 rows x NCH 32-column chunks per thread), one pivot
+//      row and one multiplier column published through shared memory per
+//      step;
 //   2. Rp is written, transposed and rounded to TF32, into the owner's
 //      operand buffer; after a cluster barrier the other CTAs copy it over
-//      distributed shared memory;
+//      distributed shared memory and arrive on the owner's copy barrier (an
+//      mbarrier the owner waits on before it writes its next operand);
 //   3. every CTA builds F = -M[rows, K] (zero on the panel rows), zeroes
 //      M[rows, K], and one thread issues D_tmem = F x Rp (M = 128 rows per
 //      MMA, N <= 256 columns, K = 8 per instruction, 4 instructions);
@@ -44,7 +48,10 @@ namespace {
 constexpr int TC_THREADS = 256;
 constexpr int PANEL = 32;
 constexpr int CM_SBO = 1024, CM_LBO = 128;
-constexpr size_t MISC_BYTES = 64 + PANEL * 33 * 4 + 64;   // mbarrier, TMEM slot, flags, Dm
+constexpr int NCH_MAX = 16;       // 32-column chunks of a panel row held in registers (n <= 512)
+// mbarrier, TMEM slot, flags; the published pivot rows [2][NCH_MAX * 32] and
+// multiplier columns [2][PANEL] of the panel step
+constexpr size_t MISC_BYTES = 64 + 2 * NCH_MAX * 32 * 4 + 2 * PANEL * 4 + 64;
 constexpr int HT = 1024;          // slots of the gather's dof -> position table (> 2 x the largest block)
 
 struct GJTCParams {
@@ -86,7 +93,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-template <int C, bool TC>
+// column of chunk c, lane l in the panel step of panel columns [k0, k0 + 32):
+// chunk 0 holds the panel columns, chunks 1.. the others in increasing order
+__device__ __forceinline__ int panel_col(int c, int l, int k0) {
+    if (c == 0) return k0 + l;
+    const int jo = 32 * (c - 1) + l;
+    return jo < k0 ? jo : jo + PANEL;
+}
+
+template <int C, bool TC, int NCH>
 __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -105,8 +120,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 8);
     int *sflag = reinterpret_cast<int *>(misc + 12);    // [0] bad pivot, [1] wait timeout
-    float *Dm = reinterpret_cast<float *>(misc + 64);   // [PANEL][33] panel diagonal block / its inverse
+    uint64_t *cbar = reinterpret_cast<uint64_t *>(misc + 24);   // peers' copies of this CTA's operand done
+    float *prow = reinterpret_cast<float *>(misc + 64);            // [2][NCH_MAX * 32] pivot rows
+    float *pmul = prow + 2 * NCH_MAX * 32;                         // [2][PANEL] multiplier columns
     int32_t *sidx = reinterpret_cast<int32_t *>(misc + MISC_BYTES);   // [n] block indices (sorted)
+    int32_t *rb = sidx + ((n + 3) & ~3);                           // [2 R] CSR bounds of the local rows
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
     if (TC && warp == 0) {
@@ -118,6 +136,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
         sflag[0] = 0;
         sflag[1] = 0;
         if (TC) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        if (C > 1) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(cbar)), "r"(C - 1));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     // gather the local rows (float64 CSR -> float32): a warp per row, lanes
     // over its entries (independent global loads), each column's position in
@@ -138,6 +160,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
         for (int t = tid; t < nr * ldm; t += blockDim.x) Ms[t] = 0.f;
         for (int t = tid; t < HT; t += blockDim.x) hkey[t] = -1;
         for (int t = tid; t < n; t += blockDim.x) sidx[t] = P.blk_idx[s0 + t];
+        // the CSR bounds of every local row at once (one round trip)
+        for (int t = tid; t < nr; t += blockDim.x) {
+            const int g = P.blk_idx[s0 + r0 + t];
+            rb[2 * t] = P.row_ptr[g];
+            rb[2 * t + 1] = P.row_ptr[g + 1];
+        }
         __syncthreads();
         for (int t = tid; t < n; t += blockDim.x) {
             const int key = sidx[t];
@@ -149,34 +177,34 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
         }
         __syncthreads();
-        // two rows per warp at a time (rows li and li + 8): their row bounds,
-        // then up to 64 entries of each, are loaded before any is used
-        constexpr int NW = TC_THREADS / 32;
-        for (int li0 = warp; li0 < nr; li0 += 2 * NW) {
-            int a[2], b[2];
+        // four rows per warp at a time (rows li0 + 8 r), up to 64 entries of
+        // each: 8 column indices and 8 values per lane loaded before any is used
+        constexpr int NW = TC_THREADS / 32, RG = 4;
+        for (int li0 = warp; li0 < nr; li0 += RG * NW) {
+            int a[RG], b[RG];
+            int len = 0;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < RG; ++r) {
                 const int li = li0 + r * NW;
                 a[r] = b[r] = 0;
                 if (li < nr) {
-                    const int g = sidx[r0 + li];
-                    a[r] = P.row_ptr[g];
-                    b[r] = P.row_ptr[g + 1];
+                    a[r] = rb[2 * li];
+                    b[r] = rb[2 * li + 1];
                 }
+                len = max(len, b[r] - a[r]);
             }
-            const int len = max(b[0] - a[0], b[1] - a[1]);
             for (int off = lane; off < len; off += 64) {
-                int cc[4];
-                float vv[4];
+                int cc[2 * RG];
+                float vv[2 * RG];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2 * RG; ++u) {
                     const int r = u >> 1, k = a[r] + off + 32 * (u & 1);
                     const bool in = k < b[r];
                     cc[u] = in ? P.col[k] : -1;
                     vv[u] = in ? (float)P.val[k] : 0.f;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2 * RG; ++u) {
                     const int c = cc[u];
                     if (c < 0) continue;
                     uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
@@ -199,124 +227,153 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     if (C > 1) cluster.sync();
 
     const int npanels = (n + PANEL - 1) / PANEL;
+    constexpr int QN = PANEL / (TC_THREADS / 32);       // consecutive panel rows per thread in the panel step
+    static_assert(QN == 4, "the panel step moves 4 rows per thread as float4");
+    int owned = 0;                                      // panels this CTA has owned so far
     for (int p = 0; p < npanels; ++p) {
         const int k0 = p * PANEL, kw = min(PANEL, n - k0);
         const int owner = k0 / R;
         const bool own = rank == owner;
         const int lb = k0 - r0;                         // first panel row (local, owner)
         // ---- F = -M[rows, K] (0 on the owner's panel rows) into the A operand,
-        //      then M[rows, K] = 0.  Neither touches the panel rows, so it runs
-        //      beside the panel step: in the owner by warps 1..7 while warp 0
-        //      inverts the diagonal block, in the other CTAs while they wait
-        //      for the owner's operand
-        auto build_f = [&](int t0, int stride) {
-            for (int e = t0; e < P.tiles * 128 * PANEL; e += stride) {
-                const int t = (e & 3) | (((e >> 5) & 7) << 2), li = ((e >> 2) & 7) | ((e >> 8) << 3);
-                float v = 0.f;
-                if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) v = -Ms[(size_t)li * ldm + k0 + t];
-                *reinterpret_cast<float *>(Fs + (size_t)(li >> 7) * 16384 + cm_off(li & 127, t)) = TC ? to_tf32(v) : v;
+        //      then M[rows, K] = 0.  Neither touches the panel rows: the owner
+        //      builds F before the first barrier of its panel step and zeroes
+        //      after it, the other CTAs do both while they wait for the owner's
+        //      operand.  Thread order of F walks each 8 x 16-byte core matrix
+        //      contiguously.
+        auto build_f = [&]() {
+            constexpr int NE = 128 * PANEL / TC_THREADS;
+            for (int tile = 0; tile < P.tiles; ++tile) {
+#pragma unroll 4
+                for (int i = 0; i < NE; ++i) {
+                    const int e = tid + i * TC_THREADS;
+                    const int t = (e & 3) | (((e >> 5) & 7) << 2);
+                    const int lr = ((e >> 2) & 7) | ((e >> 8) << 3), li = tile * 128 + lr;
+                    float v = 0.f;
+                    if (li < nr && t < kw && !(own && li >= lb && li < lb + kw)) v = -Ms[(size_t)li * ldm + k0 + t];
+                    *reinterpret_cast<float *>(Fs + (size_t)tile * 16384 + cm_off(lr, t)) = TC ? to_tf32(v) : v;
+                }
             }
         };
-        auto zero_k = [&](int t0, int stride) {
-            for (int e = t0; e < nr * kw; e += stride) {
-                const int li = e / kw, t = e - li * kw;
-                if (!(own && li >= lb && li < lb + kw)) Ms[(size_t)li * ldm + k0 + t] = 0.f;
-            }
+        auto zero_k = [&]() {
+            if (lane < kw)
+                for (int li = warp; li < nr; li += TC_THREADS / 32)
+                    if (!(own && li >= lb && li < lb + kw)) Ms[(size_t)li * ldm + k0 + lane] = 0.f;
         };
-        // ---- 1. owner: Dinv = D^{-1} (D = M[K, K], one warp, padded with the
-        //         identity to 32 x 32), then Rp = Dinv M[K, :] in place, with
-        //         the panel columns of Rp equal to Dinv
+        // ---- 1. owner: Gauss-Jordan on the panel rows M[K, :] (steps t < kw,
+        //         pivot M[k0 + t, k0 + t]); column k0 + t takes the identity
+        //         column before its step, so the panel columns end as D^{-1}.
+        //         Thread: rows u = 4 warp + q (q < 4), chunks c < NCH at columns
+        //         panel_col(c, lane).  Before step t the warp holding row t
+        //         publishes it scaled by 1 / pivot (the pivot's entry replaced by
+        //         1 / pivot) and lane t of every warp its multipliers M[u, k0 + t]
+        //         (double-buffered: one barrier per step); step t is then one
+        //         FMA per held entry.
         if (own) {
-            for (int e = tid; e < PANEL * PANEL; e += blockDim.x) {
-                const int t = e / PANEL, u = e - t * PANEL;
-                Dm[t * 33 + u] = (t < kw && u < kw) ? Ms[(size_t)(lb + t) * ldm + k0 + u] : (t == u ? 1.f : 0.f);
-            }
-            __syncthreads();
-            if (warp != 0) {
-                build_f(tid - 32, TC_THREADS - 32);
-                asm volatile("bar.sync 1, %0;" ::"r"(TC_THREADS - 32) : "memory");   // warps 1..7
-                zero_k(tid - 32, TC_THREADS - 32);
-            } else {
-                // lane j holds column j of D; row t of the pivot step and the
-                // multipliers D[u][t] come from lane t by shuffles
-                float d[PANEL];
+            float acc[QN][NCH];
 #pragma unroll
-                for (int u = 0; u < PANEL; ++u) d[u] = Dm[u * 33 + lane];
-                bool bad = false;
+            for (int q = 0; q < QN; ++q) {
+                const int u = QN * warp + q;
 #pragma unroll
-                for (int t = 0; t < PANEL; ++t) {
-                    float piv = __shfl_sync(0xffffffffu, d[t], t);
-                    if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
-                        bad = true;
-                        piv = 1.f;
-                    }
-                    const float ip = 1.f / piv;
-                    const float rt = (lane == t) ? ip : d[t] * ip;
-#pragma unroll
-                    for (int u = 0; u < PANEL; ++u) {
-                        if (u == t) continue;
-                        const float f = __shfl_sync(0xffffffffu, d[u], t);
-                        d[u] = (lane == t) ? -f * ip : fmaf(-f, rt, d[u]);
-                    }
-                    d[t] = rt;
+                for (int c = 0; c < NCH; ++c) {
+                    const int j = panel_col(c, lane, k0);
+                    acc[q][c] = (u < kw && j < n) ? Ms[(size_t)(lb + u) * ldm + j] : 0.f;
                 }
-#pragma unroll
-                for (int u = 0; u < PANEL; ++u) Dm[u * 33 + lane] = d[u];
-                if (bad && lane == 0) sflag[0] = 1;
             }
+            build_f();
+            bool bad = false;
+            if (warp == 0) {
+                float piv = __shfl_sync(0xffffffffu, acc[0][0], 0);
+                if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
+                    bad = true;
+                    piv = 1.f;
+                }
+                const float ip = 1.f / piv;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) prow[c * 32 + lane] = (c == 0 && lane == 0) ? ip : acc[0][c] * ip;
+            }
+            if (lane == 0)
+                *reinterpret_cast<float4 *>(pmul + QN * warp) = make_float4(acc[0][0], acc[1][0], acc[2][0], acc[3][0]);
             __syncthreads();
-            // thread: rows t = warp + 8 q (q < 4) of Rp, columns j = g0 + 32 c +
-            // lane (c < CG) of a group of CG 32-column chunks: per panel row u
-            // 4 + CG shared-memory loads feed 4 CG FMAs
-            constexpr int QN = PANEL * PANEL / TC_THREADS;
-            constexpr int CG = 6;
-            for (int g0 = 0; g0 < n; g0 += CG * 32) {
-                float acc[QN][CG];
+            zero_k();
 #pragma unroll
-                for (int q = 0; q < QN; ++q)
+            for (int t = 0; t < PANEL; ++t) {
+                if (t < kw) {
+                    const float *pr = prow + (t & 1) * NCH_MAX * 32;
+                    const float4 f4 = *reinterpret_cast<const float4 *>(pmul + (t & 1) * PANEL + QN * warp);
+                    const float f[QN] = {f4.x, f4.y, f4.z, f4.w};
+                    float sv[NCH];
 #pragma unroll
-                    for (int c = 0; c < CG; ++c) acc[q][c] = 0.f;
-                for (int u = 0; u < kw; ++u) {
-                    float dm[QN];
+                    for (int c = 0; c < NCH; ++c) sv[c] = pr[c * 32 + lane];
 #pragma unroll
-                    for (int q = 0; q < QN; ++q) dm[q] = Dm[(warp + 8 * q) * 33 + u];
-                    const float *mrow = Ms + (size_t)(lb + u) * ldm;
+                    for (int q = 0; q < QN; ++q) {
+                        acc[q][0] = fmaf(-f[q], sv[0], lane == t ? 0.f : acc[q][0]);
 #pragma unroll
-                    for (int c = 0; c < CG; ++c) {
-                        const int j = g0 + 32 * c + lane;
-                        const float m = j < n ? mrow[j] : 0.f;
+                        for (int c = 1; c < NCH; ++c) acc[q][c] = fmaf(-f[q], sv[c], acc[q][c]);
+                    }
+                    if (warp == t / QN)
 #pragma unroll
-                        for (int q = 0; q < QN; ++q) acc[q][c] = fmaf(dm[q], m, acc[q][c]);
+                        for (int c = 0; c < NCH; ++c) acc[t % QN][c] = sv[c];
+                    const int t1 = t + 1;
+                    if (t1 < kw) {
+                        float *nrow = prow + (t1 & 1) * NCH_MAX * 32;
+                        if (warp == t1 / QN) {
+                            float piv = __shfl_sync(0xffffffffu, acc[t1 % QN][0], t1 % 32);
+                            if (!(fabsf(piv) > 1e-30f) || !isfinite(piv)) {
+                                bad = true;
+                                piv = 1.f;
+                            }
+                            const float ip = 1.f / piv;
+#pragma unroll
+                            for (int c = 0; c < NCH; ++c)
+                                nrow[c * 32 + lane] = (c == 0 && lane == t1) ? ip : acc[t1 % QN][c] * ip;
+                        }
+                        if (lane == t1)
+                            *reinterpret_cast<float4 *>(pmul + (t1 & 1) * PANEL + QN * warp) =
+                                make_float4(acc[0][0], acc[1][0], acc[2][0], acc[3][0]);
+                        __syncthreads();
                     }
                 }
-                __syncthreads();
+            }
+            if (bad) sflag[0] = 1;
+            // ---- 2. the other CTAs finished copying this CTA's previous
+            //         operand (bounded wait on the copy barrier's phase), then
+            //         Rp back into the panel rows and Rp^T (TF32, zero-padded to
+            //         32 x npad) into the B buffer, 4 rows per 16-byte store
+            if (C > 1 && owned > 0 && !sflag[1]) {     // after a timed-out wait no further waits
+                uint32_t done = 0;
+                for (int it = 0; it < (1 << 20) && !done; ++it) {
+                    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 q, [%1], %2;\n"
+                                 "selp.u32 %0, 1, 0, q;\n}"
+                                 : "=r"(done)
+                                 : "r"(smem_u32(cbar)), "r"((uint32_t)((owned - 1) & 1))
+                                 : "memory");
+                }
+                if (!done) sflag[1] = 1;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int j = panel_col(c, lane, k0);
+                float w[QN];
 #pragma unroll
                 for (int q = 0; q < QN; ++q) {
-                    const int t = warp + 8 * q;
-#pragma unroll
-                    for (int c = 0; c < CG; ++c) {
-                        const int j = g0 + 32 * c + lane;
-                        if (t < kw && j < n)
-                            Ms[(size_t)(lb + t) * ldm + j] = (j >= k0 && j < k0 + kw) ? Dm[t * 33 + (j - k0)] : acc[q][c];
-                    }
+                    const int u = QN * warp + q;
+                    const bool live = u < kw && j < n;
+                    if (live) Ms[(size_t)(lb + u) * ldm + j] = acc[q][c];
+                    w[q] = live ? (TC ? to_tf32(acc[q][c]) : acc[q][c]) : 0.f;
                 }
-                __syncthreads();
+                if (j < npad) *reinterpret_cast<float4 *>(Bs + cm_off(j, QN * warp)) = make_float4(w[0], w[1], w[2], w[3]);
             }
-            // ---- 2. Rp^T (TF32) into the owner's B buffer, zero-padded; the
-            //         thread order walks each 8 x 16-byte core matrix contiguously
-            for (int e = tid; e < npad * PANEL; e += blockDim.x) {
-                const int t = (e & 3) | (((e >> 5) & 7) << 2), j = ((e >> 2) & 7) | ((e >> 8) << 3);
-                const float v = (j < n && t < kw) ? Ms[(size_t)(lb + t) * ldm + j] : 0.f;
-                *reinterpret_cast<float *>(Bs + cm_off(j, t)) = TC ? to_tf32(v) : v;
-            }
+            ++owned;
         } else {
-            build_f(tid, TC_THREADS);
+            build_f();
             __syncthreads();
-            zero_k(tid, TC_THREADS);
+            zero_k();
         }
         if (C > 1) {
             cluster.sync();
-            // the other CTAs copy the owner's operand (16-byte DSMEM reads, in parallel)
+            // the other CTAs copy the owner's operand (16-byte DSMEM reads, in
+            // parallel), then one thread each arrives on the owner's copy barrier
             if (rank != owner) {
                 const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(Bs, owner));
                 float4 *dstp = reinterpret_cast<float4 *>(Bs);
@@ -324,6 +381,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
         }
         __syncthreads();
+        if (C > 1 && rank != owner && tid == 0) {
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(cbar)), "r"(owner));
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+        }
         if (TC) {
             // ---- 4a. tensor cores: D = F x Rp, then M += D
             asm volatile("fence.proxy.async.shared::cta;");
@@ -405,8 +467,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
             __syncthreads();
         }
-        // peers finished reading their B buffers before the next owner writes them
-        if (C > 1) cluster.sync();
     }
     if (tid == 0) {
         if (sflag[0]) atomicExch(P.flags, 1);
@@ -444,7 +504,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
     if (C > 1) cluster.sync();
 }
 
-template <int C, bool TC>
+template <int C, bool TC, int NCH>
 fsi_status launch_tc(const GJTCParams &P, int64_t n_blocks, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(n_blocks * C));
@@ -458,10 +518,29 @@ fsi_status launch_tc(const GJTCParams &P, int64_t n_blocks, size_t smem, cudaStr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    FSI_CUDA(cudaFuncSetAttribute(block_gj_tc_kernel<C, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FSI_CUDA(cudaLaunchKernelEx(&cfg, block_gj_tc_kernel<C, TC>, P));
+    FSI_CUDA(cudaFuncSetAttribute(block_gj_tc_kernel<C, TC, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FSI_CUDA(cudaLaunchKernelEx(&cfg, block_gj_tc_kernel<C, TC, NCH>, P));
     count_launch();
     return FSI_OK;
+}
+
+// The kernel for blocks of up to n dofs in clusters of C CTAs: a panel row
+// of n columns takes NCH = ceil(n / 32) register chunks, rounded up to 6, 12
+// or 16.  Instantiated for the (NCH, C) pairs gj_tc_plan yields for n <= 512:
+// (6, 1) n <= 128, (6, 2) up to 176, (6, 4) up to 192, (12, 4) up to 384
+// except (12, 8) for 240..256, (16, 8) up to 512.
+template <bool TC>
+fsi_status launch_gj(const GJTCParams &P, int n, int C, int64_t n_blocks, size_t smem, cudaStream_t s) {
+    const int nch = n <= 6 * 32 ? 6 : n <= 12 * 32 ? 12 : 16;
+    if (nch == 6 && C == 1) return launch_tc<1, TC, 6>(P, n_blocks, smem, s);
+    if (nch == 6 && C == 2) return launch_tc<2, TC, 6>(P, n_blocks, smem, s);
+    if (nch == 6 && C == 4) return launch_tc<4, TC, 6>(P, n_blocks, smem, s);
+    if (nch == 12 && C == 4) return launch_tc<4, TC, 12>(P, n_blocks, smem, s);
+    if (nch == 12 && C == 8) return launch_tc<8, TC, 12>(P, n_blocks, smem, s);
+    if (nch == 16 && C == 8) return launch_tc<8, TC, 16>(P, n_blocks, smem, s);
+    set_error("no block inversion kernel for blocks of " + std::to_string(n) + " dofs in clusters of " +
+              std::to_string(C));
+    return FSI_ERR_ARG;
 }
 
 }  // namespace
@@ -546,20 +625,7 @@ fsi_status launch_block_invert_tc(const DevCSR &A, const LevelDev &lev, int stor
     P.off_misc = P.off_b + (((size_t)P.npad * 128 + 1023) & ~(size_t)1023);
     P.flags = flags;
     P.dense = nullptr;
-#define FSI_TC_CASE(CC)                                                                       \
-    case CC:                                                                                  \
-        return tensor ? launch_tc<CC, true>(P, lev.n_blocks, smem, s)                         \
-                      : launch_tc<CC, false>(P, lev.n_blocks, smem, s);
-    switch (C) {
-        FSI_TC_CASE(1)
-        FSI_TC_CASE(2)
-        FSI_TC_CASE(4)
-        FSI_TC_CASE(8)
-        default:
-            set_error("bad cluster size");
-            return FSI_ERR_ARG;
-    }
-#undef FSI_TC_CASE
+    return tensor ? launch_gj<true>(P, n, C, lev.n_blocks, smem, s) : launch_gj<false>(P, n, C, lev.n_blocks, smem, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,19 +783,7 @@ fsi_status invert_dense(const float *in, float *out, int64_t nb, int N, bool ten
     P.off_misc = P.off_b + (((size_t)P.npad * 128 + 1023) & ~(size_t)1023);
     P.flags = flags;
     P.dense = in;
-#define FSI_TC_CASE(CC)                                                                   \
-    case CC:                                                                              \
-        return tensor ? launch_tc<CC, true>(P, nb, smem, s) : launch_tc<CC, false>(P, nb, smem, s);
-    switch (C) {
-        FSI_TC_CASE(1)
-        FSI_TC_CASE(2)
-        FSI_TC_CASE(4)
-        FSI_TC_CASE(8)
-        default:
-            set_error("bad cluster size");
-            return FSI_ERR_ARG;
-    }
-#undef FSI_TC_CASE
+    return tensor ? launch_gj<true>(P, N, C, nb, smem, s) : launch_gj<false>(P, N, C, nb, smem, s);
 }
 }  // namespace
 

@@ -463,7 +463,7 @@ def test_repeatable_smoother_and_solve(prec, variant):
 
 
 FACTOR_CASES = {
-    "bulge48": lambda: I.make_channel_2d(48, 4, 3, 4242, bulge=True),     # 171-dof blocks, one CTA
+    "bulge48": lambda: I.make_channel_2d(48, 4, 3, 4242, bulge=True),     # 171-dof blocks, 2-CTA cluster
     "valve8": lambda: I.make_valve_3d(8, 3, 1, 777),                      # 376-dof blocks, 4-CTA cluster
 }
 

@@ -11,9 +11,11 @@ size.
   reference formed from every block that overlaps them, one block at a time;
   the lumped K_u^s Jacobi rows on a sample;
 - the solves bench.py times (FP16 inverses from tensor-core factors, additive
-  smoother and the multiplicative sweep on the finest level): converged, and
-  the true residual of the oracle's operator, evaluated on the host in
-  extended precision, within 1.05 rtol;
+  smoother and the multiplicative sweep on the finest level): converged; the
+  true residual of the operator the library solved with (read back), in
+  extended precision on the host, within 1.05 rtol; that operator equal to
+  the oracle's assembled one to rounding; the oracle's residual within those
+  two;
 - iteration counts within +-1 of the oracle's on the same storage emulation
   and the solution against the oracle's float64 solution at sampled
   unknowns, both from tests/golden/full_size_256.json, which
@@ -123,14 +125,15 @@ def test_full_size_fp16_smoother_sampled_blocks(full):
     np.testing.assert_allclose(y[k], ref_k, rtol=1e-6, atol=0)
 
 
-def _residual_ld(A, x, b):
-    """||b - A x|| evaluated in extended precision (numpy longdouble: 64-bit
-    significand on x86, 113-bit on Arm): on these row-scaled systems
-    || |A| |x| || ~ 3e6 ||b||, so a float64 evaluation alone is uncertain by
-    ~1e-9 ||b||; the extended sum removes the host's share of that."""
-    Al = A.astype(np.longdouble)
-    r = b.astype(np.longdouble) - Al @ x.astype(np.longdouble)
-    return float(np.sqrt(np.sum(r * r)))
+def _matvec_ld(A, x):
+    """A x in extended precision (numpy longdouble: 64-bit significand on
+    x86, 113-bit on Arm): on these row-scaled systems || |A| |x| || ~ 3e6
+    ||b||, so a float64 product alone is uncertain by ~1e-9 ||b||."""
+    return A.astype(np.longdouble) @ x.astype(np.longdouble)
+
+
+def _norm_ld(v):
+    return float(np.sqrt(np.sum(v * v)))
 
 
 @pytest.fixture(scope="module")
@@ -142,17 +145,38 @@ def golden():
 
 @pytest.mark.parametrize("mult_levels", [0, 1])
 def test_full_size_solve_true_residual(full, golden, mult_levels):
-    """The solves bench.py times (FP16 inverses from tensor-core factors):
-    x solves the oracle's assembled system, ||b - A x|| <= 1.05 rtol ||b||
-    (the solve stops on its own float64 true residual <= rtol; 5 % covers the
-    float64 summation order of that on-device evaluation), and the iteration
-    count stays within one of the oracle's on the same storage emulation."""
+    """The solves bench.py times (FP16 inverses from tensor-core factors).
+
+    - ||b - A_lib x|| <= 1.05 rtol ||b|| for the operator A_lib the library
+      solved with (read back from the device), evaluated exactly enough on the
+      host: the solve stops on its own float64 true residual <= rtol, and 5 %
+      covers the rounding of that on-device evaluation;
+    - A_lib equals the oracle's assembled A to rounding: ||(A_lib - A) x|| <=
+      4 u || |A| |x| || (u = 2^-53; both sum the same element contributions
+      in different orders);
+    - hence ||b - A x|| <= 1.05 rtol ||b|| + ||(A_lib - A) x||.  On this
+      system || |A| |x| || ~ 3e6 ||b||, so a last-bit difference of the two
+      assemblies moves the residual by a few tenths of rtol: the oracle's
+      residual is held to rtol up to that measured term, not to 1.05 rtol
+      alone;
+    - the iteration count within one of the oracle's on the same storage
+      emulation."""
     p, lev, A, s, b = full
     s.setup_smoothers(precision=binding.FSI_MIXED_HALF, mult_levels=mult_levels)
     x, st = s.solve(_cuda(b), rtol=RTOL)
     assert st["converged"] and st["rel_residual"] <= RTOL
     xr = x.cpu().numpy()
-    assert _residual_ld(A, xr, b) <= 1.05 * RTOL * np.linalg.norm(b), (mult_levels, st)
+    ptr, col, val = s.matrix(p.n_levels - 1)
+    A_lib = sp.csr_matrix((val, col, ptr), shape=A.shape)
+    bl = b.astype(np.longdouble)
+    y_lib, y_or = _matvec_ld(A_lib, xr), _matvec_ld(A, xr)
+    nb = float(np.linalg.norm(b))
+    r_lib, r_or, dax = _norm_ld(bl - y_lib), _norm_ld(bl - y_or), _norm_ld(y_lib - y_or)
+    absax = float(np.linalg.norm(abs(A) @ np.abs(xr)))
+    info = (mult_levels, st["iterations"], r_lib / nb, r_or / nb, dax / nb, absax / nb)
+    assert r_lib <= 1.05 * RTOL * nb, info
+    assert dax <= 4 * (np.finfo(np.float64).eps / 2) * absax, info
+    assert r_or <= 1.05 * RTOL * nb + dax, info
     key = "iterations_half_mult_fine" if mult_levels else "iterations_half_additive"
     assert abs(st["iterations"] - golden[key]) <= 1, (st["iterations"], golden[key])
 
