@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             }
         }
         __syncthreads();
-        // four rows per warp at a time (rows li0 + 8 r), up to 64 entries of
-        // each: 8 column indices and 8 values per lane loaded before any is used
-        constexpr int NW = TC_THREADS / 32, RG = 4;
+        // four rows per warp at a time (rows li0 + 8 r), up to 128 entries of
+        // each: 16 column indices and 16 values per lane loaded before any is
+        // used
+        constexpr int NW = TC_THREADS / 32, RG = 4, SUBC = 4;
         for (int li0 = warp; li0 < nr; li0 += RG * NW) {
             int a[RG], b[RG];
             int len = 0;
@@ -193,18 +194,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                 }
                 len = max(len, b[r] - a[r]);
             }
-            for (int off = lane; off < len; off += 64) {
-                int cc[2 * RG];
-                float vv[2 * RG];
+            for (int off = lane; off < len; off += 32 * SUBC) {
+                int cc[SUBC * RG];
+                float vv[SUBC * RG];
 #pragma unroll
-                for (int u = 0; u < 2 * RG; ++u) {
-                    const int r = u >> 1, k = a[r] + off + 32 * (u & 1);
+                for (int u = 0; u < SUBC * RG; ++u) {
+                    const int r = u / SUBC, k = a[r] + off + 32 * (u % SUBC);
                     const bool in = k < b[r];
                     cc[u] = in ? P.col[k] : -1;
                     vv[u] = in ? (float)P.val[k] : 0.f;
                 }
 #pragma unroll
-                for (int u = 0; u < 2 * RG; ++u) {
+                for (int u = 0; u < SUBC * RG; ++u) {
                     const int c = cc[u];
                     if (c < 0) continue;
                     uint32_t h = ((uint32_t)c * 0x9E3779B1u) >> 22;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                         if (kk == -1) break;
                         h = (h + 1) & (HT - 1);
                     }
-                    if (pos >= 0) Ms[(size_t)(li0 + (u >> 1) * NW) * ldm + pos] = vv[u];
+                    if (pos >= 0) Ms[(size_t)(li0 + (u / SUBC) * NW) * ldm + pos] = vv[u];
                 }
             }
         }
@@ -236,10 +237,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
         const bool own = rank == owner;
         const int lb = k0 - r0;                         // first panel row (local, owner)
         // ---- F = -M[rows, K] (0 on the owner's panel rows) into the A operand,
-        //      then M[rows, K] = 0.  Neither touches the panel rows: the owner
-        //      builds F before the first barrier of its panel step and zeroes
-        //      after it, the other CTAs do both while they wait for the owner's
-        //      operand.  Thread order of F walks each 8 x 16-byte core matrix
+        //      then M[rows, K] = 0.  Neither touches the panel rows: the other
+        //      CTAs do both while they wait for the owner's operand, the owner
+        //      after the cluster barrier that releases them.  Thread order of F walks each 8 x 16-byte core matrix
         //      contiguously.
         auto build_f = [&]() {
             constexpr int NE = 128 * PANEL / TC_THREADS;
@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
                     acc[q][c] = (u < kw && j < n) ? Ms[(size_t)(lb + u) * ldm + j] : 0.f;
                 }
             }
-            build_f();
             bool bad = false;
             if (warp == 0) {
                 float piv = __shfl_sync(0xffffffffu, acc[0][0], 0);
@@ -295,7 +294,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             if (lane == 0)
                 *reinterpret_cast<float4 *>(pmul + QN * warp) = make_float4(acc[0][0], acc[1][0], acc[2][0], acc[3][0]);
             __syncthreads();
-            zero_k();
 #pragma unroll
             for (int t = 0; t < PANEL; ++t) {
                 if (t < kw) {
@@ -385,6 +383,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
             uint32_t remote;
             asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(cbar)), "r"(owner));
             asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+        }
+        // after the last operand copy no CTA touches another's shared memory:
+        // arrive on the cluster barrier now, wait for it only before exit
+        if (C > 1 && p == npanels - 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        // the owner builds its A operand once the other CTAs are released
+        if (own) {
+            build_f();
+            __syncthreads();
+            zero_k();
         }
         if (TC) {
             // ---- 4a. tensor cores: D = F x Rp, then M += D
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
         for (int li = warp; li < nr; li += TC_THREADS / 32) {
             float m = 0.f;
             for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(Ms[(size_t)li * ldm + j]));
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));   // m >= 0
             const float sc = m > 0.f ? m : 1.f;
             if (lane == 0) P.scale[s0 + r0 + li] = sc;
             const float isc = 1.f / sc;
@@ -501,7 +508,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) block_gj_tc_kernel(GJTCParams P
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
     }
-    if (C > 1) cluster.sync();
+    if (C > 1) {
+        if (npanels == 0) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
 }
 
 template <int C, bool TC, int NCH>
