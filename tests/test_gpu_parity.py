@@ -464,6 +464,7 @@ def test_repeatable_smoother_and_solve(prec, variant):
 
 FACTOR_CASES = {
     "bulge48": lambda: I.make_channel_2d(48, 4, 3, 4242, bulge=True),     # 171-dof blocks, 2-CTA cluster
+    "bulge48_b4": lambda: I.make_channel_2d(48, 4, 4, 4242, bulge=True),  # 258-dof blocks, 4-CTA cluster
     "valve8": lambda: I.make_valve_3d(8, 3, 1, 777),                      # 376-dof blocks, 4-CTA cluster
 }
 
@@ -625,6 +626,36 @@ def test_as_3d_split_inversion():
     _, st8 = s.solve(_cuda(b), rtol=1e-8)
     assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
 
+
+
+def test_as_2d_wide_blocks_eight_cta_clusters():
+    """Monolithic AS blocks of a 4 x 4 pressure-vertex group in 2D (~506
+    dofs): the tensor-core and float32 Gauss-Jordan kernels in 8-CTA clusters
+    with 16 register chunks per panel row.  Block sets equal the oracle's;
+    with float32 factors the solve reaches the direct solution and needs the
+    oracle's float32-storage emulation's iteration count +-1; with TF32
+    factors it reaches the direct solution."""
+    p = I.make_channel_2d(24, 3, 4, 7)
+    H = gmg.Hierarchy(p, monolithic=True)
+    l = len(H.A) - 1
+    s = binding.FSISolver(p)
+    s.setup_smoothers(precision=binding.FSI_MIXED, factor=binding.FSI_FACTOR_FP32, variant=binding.FSI_SMOOTHER_AS)
+    assert 384 < s.sizes(l)["max_block"] <= 512
+    ptr, idx = s.blocks(l)
+    for j, ref in enumerate(H.smoothers[l].blocks):
+        np.testing.assert_array_equal(idx[ptr[j]:ptr[j + 1]], ref)
+    b = _rhs(p, H, 44)
+    xd = _direct(H.fine, b)
+    x, st = s.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+    Hm = gmg.Hierarchy(p, monolithic=True, mixed=True)
+    _, ost = ofg.solve(Hm, b, rtol=1e-8)
+    _, st8 = s.solve(_cuda(b), rtol=1e-8)
+    assert abs(st8["iterations"] - ost["iterations"]) <= 1, (st8["iterations"], ost["iterations"])
+    st_ = binding.FSISolver(p)
+    st_.setup_smoothers(precision=binding.FSI_MIXED, factor=binding.FSI_FACTOR_TF32, variant=binding.FSI_SMOOTHER_AS)
+    x, st = st_.solve(_cuda(b), rtol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
 
 
 @pytest.mark.parametrize("prec", [binding.FSI_MIXED, binding.FSI_MIXED_HALF])
