@@ -49,7 +49,7 @@ constexpr int TC_THREADS = 256;
 constexpr int PANEL = 32;
 constexpr int CM_SBO = 1024, CM_LBO = 128;
 constexpr int NCH_MAX = 16;       // 32-column chunks of a panel row held in registers (n <= 512)
-// mbarrier, TMEM slot, flags; the published pivot rows [2][NCH_MAX * 32] and
+// mbarriers, TMEM slot, flags; the published pivot rows [2][NCH_MAX * 32] and
 // multiplier columns [2][PANEL] of the panel step
 constexpr size_t MISC_BYTES = 64 + 2 * NCH_MAX * 32 * 4 + 2 * PANEL * 4 + 64;
 constexpr int HT = 1024;          // slots of the gather's dof -> position table (> 2 x the largest block)
