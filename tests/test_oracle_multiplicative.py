@@ -57,10 +57,11 @@ def test_blocks_of_a_pass_are_uncoupled(mk, b):
             assert not cross.any(), (key, int(cross.sum()))
 
 
-def _closed_form(S, A, lev, transpose=False):
+def _closed_form(S, A, lev, transpose=False, block_inverse=None):
     """Dense M (or M^T) of the sweep from its textbook form: for a field F with
     corrections B_1..B_m (in sweep order, B_j = R_j^T A_jj^{-1} R_j),
-    M_F = (I - (I - B_m A_FF) ... (I - B_1 A_FF)) A_FF^{-1}."""
+    M_F = (I - (I - B_m A_FF) ... (I - B_1 A_FF)) A_FF^{-1}.  block_inverse(j,
+    A_jj) replaces the exact inverse of block j (default numpy inv)."""
     n = lev.n_dofs
     Ad = A.toarray()
     d, u = _field_masks(lev)
@@ -81,7 +82,8 @@ def _closed_form(S, A, lev, transpose=False):
                 continue
             idx = pos[S.blocks[j]]
             Bj = np.zeros((F.size, F.size))
-            Bj[np.ix_(idx, idx)] = np.linalg.inv(AFF[np.ix_(idx, idx)])
+            Ajj = AFF[np.ix_(idx, idx)]
+            Bj[np.ix_(idx, idx)] = np.linalg.inv(Ajj) if block_inverse is None else block_inverse(j, Ajj)
             corr.append(Bj)
         E = np.eye(F.size)
         for Bj in corr:
@@ -131,6 +133,57 @@ def test_sweep_adjoint_identity_mixed_half():
         rhs = float(np.dot(r1, S.apply_transpose(r2).astype(np.float64)))
         tol = 1e-12 if not kw else 1e-5
         assert abs(lhs - rhs) <= tol * (abs(lhs) + abs(rhs)), (kw, lhs, rhs)
+
+
+class _HalfScaleDropped(fsasm.FSASM):
+    """Planted mistake: the float16 rows applied without their row scale."""
+
+    def _solve(self, j, v, transpose=False):
+        m16, scale = self.lu[j]
+        m = m16.astype(np.float32)
+        return m.T @ v if transpose else m @ v
+
+
+@pytest.mark.parametrize("mk,b", [
+    (lambda: I.make_channel_2d(8, 2, 2, 11, bulge=True), 2),
+    (lambda: I.make_channel_2d(8, 2, 1, 12), 1),
+])
+def test_half_sweep_equals_closed_form_of_its_stored_inverses(mk, b):
+    """The float16-storage sweep (the emulation behind the headline's stored
+    iteration count) equals the closed form built from its own stored
+    inverses diag(s) m16 (dequantized in float64) up to its float32
+    arithmetic, and differs from the exact-inverse closed form at float16
+    level: the tolerance separates the two, and a sweep that drops the row
+    scale fails it."""
+    p = mk()
+    lev = mesh.build_levels(p)[-1]
+    A = assemble(p, lev)
+    S = fsasm.FSASM(A, lev, b, multiplicative=True, half=True)
+
+    def stored(j, Ajj):
+        m16, scale = S.lu[j]
+        return scale.astype(np.float64)[:, None] * m16.astype(np.float64)
+
+    Mh = _closed_form(S, A, lev, block_inverse=stored)
+    M = _closed_form(S, A, lev)
+    bad = _HalfScaleDropped(A, lev, b, multiplicative=True, half=True)
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        r = rng.standard_normal(lev.n_dofs).astype(np.float32).astype(np.float64)
+        for tr in (False, True):
+            y = (S.apply_transpose(r) if tr else S.apply(r)).astype(np.float64)
+            ref = (Mh.T if tr else Mh) @ r
+            exact = (M.T if tr else M) @ r
+            nr = np.linalg.norm(ref)
+            # float32 arithmetic of the sweep: a few u = 2^-24 (measured
+            # 4e-8 to 9e-8), allowed 1e-6
+            assert np.linalg.norm(y - ref) <= 1e-6 * nr, (tr, np.linalg.norm(y - ref) / nr)
+            # the stored inverses are visibly not the exact ones: float16
+            # rounding (2^-11 per stored entry, averaging in the products;
+            # measured 1.6e-5 to 1.1e-4) stays above 4x that tolerance
+            assert np.linalg.norm(exact - ref) > 4e-6 * nr
+        yb = bad.apply(r).astype(np.float64)
+        assert np.linalg.norm(yb - Mh @ r) > 1e-2 * np.linalg.norm(Mh @ r)
 
 
 @pytest.mark.parametrize("mult_levels", [1, 99])
