@@ -98,8 +98,12 @@ typedef struct {
                                  *     [d^f] and a fluid [u^f, p^f] block, Jacobi on K_u^s;
                                  *   FSI_SMOOTHER_AS (1): the monolithic additive Schwarz method
                                  *     the paper compares against: one block of all fields per
-                                 *     pressure group.  Blocks of more than ~500 dofs (3D) are
-                                 *     beyond the inversion kernels: FSI_ERR_ARG. */
+                                 *     pressure group.  Blocks beyond one thread-block cluster
+                                 *     of the float32 factorisation (above 507 dofs: 3D) are
+                                 *     inverted by a 2 x 2 split over the two field systems,
+                                 *     which needs FSI_MIXED (float32 inverses); the float64
+                                 *     factorisation refuses blocks its 8-CTA cluster cannot
+                                 *     hold (441 dofs and more).  Both: FSI_ERR_ARG. */
     int mult_levels;            /* locally multiplicative Schwarz (Sec. 3.2, multiplicative update
                                  * formula; the paper's AS1/AS2 are multiplicative within a
                                  * process) on the mult_levels finest levels, additive below;
